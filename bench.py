@@ -1,0 +1,308 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched safety filter on the N=16 robots 3D workload.
+
+A step is one sf_project call: K=200 iterations of f_FP over S=1024 sampled
+trajectories of one scene (16 robots, 3D, T=100, Bernstein order 10, sample
+init, rho=0.1), inputs resident in HBM. Metric: SF-projected samples/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--form fused|plain]
+
+Prints one JSON line (rank 0). Under torchrun each rank runs its own
+1024-sample batch (weak scaling, no collective on the data path); the timed
+region is bracketed by a barrier and a synchronize, and the slowest rank's
+time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import swarm_inputs as si  # noqa: E402
+
+RHO = 0.1
+METRIC = "SF-projected samples/s (16 robots 3D, residual<=1e-3), chosen vs plain form"
+UNIT = "samples/s"
+FP32_LANES_PER_SM = 128
+
+
+def ops_per_sample_iter(N: int, T: int, dim: int, nv: int = 11, use_v: bool = True, use_a: bool = True):
+    """Algorithmic float32 lane operations of one iteration of one sample
+    (an FMA counts once; rsqrt counts once)."""
+    blocks = 1 + int(use_v) + int(use_a)
+    contractions = 2 * blocks * T * nv * dim * N          # states and F^T of the residual
+    c_pair = 19 if dim == 3 else 14
+    c_ball = 9 if dim == 3 else 7
+    pairs = N * (N - 1) // 2 * T * c_pair                   # alpha/beta/d steps + accumulation
+    balls = (int(use_v) + int(use_a)) * N * T * c_ball      # velocity / acceleration blocks
+    solve = dim * (N * 2 * nv * nv + 2 * nv * nv) + dim * N * nv * 5  # lambda step and xi step
+    return contractions + pairs + balls + solve
+
+
+def workload_spec():
+    return si.config_n16_3d()
+
+
+def workload_name(spec):
+    return (f"{spec.dim}D N={spec.n_robots} robots, S={spec.n_samples} samples, T={spec.T}, "
+            f"K={spec.K}, Bernstein order {spec.order}, sample init, rho={RHO}, robot radius "
+            f"{spec.radius} m, |v|<={spec.v_max}, |a|<={spec.a_max}")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_gpu(args):
+    import torch
+    import paper_2501_19042_gb300 as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    P.build()
+    spec = workload_spec()
+    sc = si.scene(spec, 1 + rank)
+    S, K = spec.n_samples, spec.K
+    f = P.SafetyFilter(dim=spec.dim, T=spec.T, rho=RHO, coll_a=spec.coll, v_max=spec.v_max, a_max=spec.a_max,
+                       max_robots=spec.n_robots, t_final=spec.t_final, device=dev.index)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    xb, st, gl = t(sc.xi_bar), t(sc.start), t(sc.goal)
+    stream = torch.cuda.current_stream(dev)
+    out = f.project(xb, st, gl, K, form=args.form)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        f.project(xb, st, gl, K, form=args.form, out=out)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clk = ClockSampler(dev.index)
+    clk.start()
+    barrier()
+    torch.cuda.synchronize()
+    n_launch0 = f.launch_count()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()                       # L2 flushed between timed steps, outside the events
+        starts[i].record(stream)
+        f.project(xb, st, gl, K, form=args.form, out=out)
+        stops[i].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t0
+    launches = f.launch_count() - n_launch0
+    clocks = clk.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, stops)]
+    ms = float(np.mean(step_ms))
+    if dist is not None:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    f.sync_status()
+
+    # residual condition of the metric
+    med_res = float(out.residual.median())
+
+    # end to end through sf_project_host: pinned host inputs, copies inside the call
+    hx = torch.tensor(sc.xi_bar, dtype=torch.float32).contiguous().pin_memory()
+    hs = torch.tensor(sc.start, dtype=torch.float32).contiguous().pin_memory()
+    hg = torch.tensor(sc.goal, dtype=torch.float32).contiguous().pin_memory()
+    hout = f.project_host(hx, hs, hg, K, form=args.form)
+    e2e_steps = max(3, min(args.steps, 10))
+    barrier()
+    t1 = time.perf_counter()
+    for _ in range(e2e_steps):
+        f.project_host(hx, hs, hg, K, form=args.form, out=hout)
+    barrier()
+    e2e_s = (time.perf_counter() - t1) / e2e_steps
+    if dist is not None:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    h2d = (hx.numel() + hs.numel() + hg.numel()) * 4
+    d2h = (2 * hx.numel() + S) * 4
+
+    if rank == 0:
+        peaks = measured_peaks()
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+        max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        peak_tops = sm_count * FP32_LANES_PER_SM * max_mhz * 1e6 / 1e12
+        ops = ops_per_sample_iter(spec.n_robots, spec.T, spec.dim) * S * K
+        kernel_ms = ms   # a step is one launch of the fused kernel
+        achieved = ops / (kernel_ms * 1e-3) / 1e12
+        value = world * S / (ms * 1e-3)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded swarm generator)",
+            "impl": "gb300", "form": args.form,
+            "config": {"workload": workload_name(spec), "global_batch": world * S, "per_gpu_samples": S,
+                       "parallelism": f"independent sample batches on {world} GPU(s)",
+                       "l2": "flushed between timed steps by a 256 MiB write outside the events"},
+            "median_final_residual": med_res,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                         "frac": achieved / peak_tops, "traffic": None,
+                         "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x {max_mhz:.0f} MHz "
+                                        "(max SM clock of MEASURED_PEAKS.json)",
+                         "kernel": "fused_fwd_kernel" if args.form == "fused" else "plain form (several kernels)"},
+            "e2e": {"value": world * S / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "api": "sf_project_host"},
+            "gpu_launches": int(launches),
+            "wall_s_timed": wall,
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(spec, sc, args.cpu_samples)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(spec, sc, n_samples):
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    pb = oracle.Problem(dim=spec.dim, n_robots=spec.n_robots, T=spec.T, order=spec.order, t_final=spec.t_final,
+                        rho=RHO, coll_a=spec.coll, coll_b=spec.coll, v_max=spec.v_max, a_max=spec.a_max)
+    xb = sc.xi_bar[:n_samples]
+    t0 = time.perf_counter()
+    oracle.run_batch(pb, sc.start, sc.goal, xb, K=spec.K, n_threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n_samples / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {n_samples} of the {spec.n_samples} samples, K={spec.K}, FP64 C oracle, "
+                      f"{dt:.1f} s wall on {cores} threads"}
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle on the machine's host cores."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    spec = workload_spec()
+    sc = si.scene(spec, 1)
+    cores = os.cpu_count() or 1
+    n = args.cpu_samples
+    pb = oracle.Problem(dim=spec.dim, n_robots=spec.n_robots, T=spec.T, order=spec.order, t_final=spec.t_final,
+                        rho=RHO, coll_a=spec.coll, coll_b=spec.coll, v_max=spec.v_max, a_max=spec.a_max)
+    for _ in range(args.warmup):
+        oracle.run_batch(pb, sc.start, sc.goal, sc.xi_bar[:cores], K=5, n_threads=cores)
+    times = []
+    for i in range(args.steps):
+        xb = sc.xi_bar[(i * n) % spec.n_samples:][:n]
+        t0 = time.perf_counter()
+        oracle.run_batch(pb, sc.start, sc.goal, xb, K=spec.K, n_threads=cores)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    value = n / (ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded swarm generator)", "impl": "reference",
+        "config": {"workload": workload_name(spec), "global_batch": n,
+                   "parallelism": f"{cores} host threads", "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n} samples of the {spec.n_samples}-sample workload per step, K={spec.K}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--form", default="fused", choices=["fused", "plain"])
+    ap.add_argument("--cpu-samples", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * sf.h — C ABI of the GB300-native batched safety filter (SF) of Swarm-Gen,
+ * arXiv 2501.19042 (Sec. III-C and Appendix, "Custom SF optimizer").
+ *
+ * The library projects many sampled joint swarm trajectories onto the
+ * feasible set of Eq. (sf_form): boundary conditions A xi = b
+ * (Eq. boundary_con), velocity / acceleration bounds, and collision avoidance
+ * between every pair of robots at every time step (Eq. inter_robot_con). It
+ * runs the paper's fixed-point iteration f_FP (Eq. fixed_point), whose steps
+ * are the alpha / beta / d closed forms, the multiplier update and the
+ * equality-constrained xi step of the Appendix.
+ *
+ * Conventions
+ *  - Every call returns an sf_status; no C++ exception crosses the ABI.
+ *    sf_last_error() gives a human-readable message for the last failure on a
+ *    handle.
+ *  - Sizes and shapes are validated on the host before any launch.
+ *  - Device pointers are CUDA device memory owned by the caller; the library
+ *    never frees them. The handle owns only its precomputed basis matrices and
+ *    solve operators.
+ *  - Compute calls are asynchronous on the caller's stream (passed as a
+ *    cudaStream_t cast to void*; NULL is the legacy default stream). No
+ *    implicit host synchronisation, except where a function says so.
+ *  - Device-side errors (a bounded wait that ran out, non-finite values) are
+ *    latched in a device word; sf_sync_status() synchronises the stream and
+ *    returns them.
+ *  - Layouts (row-major, float32 unless stated):
+ *      coefficients (xi_bar, xi0, lambda0, xi_out, lambda_out, gradients):
+ *        per sample [dim][N][nvar], nvar = order + 1 (the paper's xi vector,
+ *        Sec. II-B: all robots' x coefficients, then y, then z); samples of a
+ *        scene are contiguous and scenes follow each other.
+ *      start, goal: [sum_s N_s][dim];  start_va, goal_va: [sum_s N_s][2][dim]
+ *        holding (velocity, acceleration).
+ *      per-sample scalars (residual_out): [sum_s S_s];
+ *      residual_hist: [K][sum_s S_s].
+ */
+#ifndef GB300_SWARM_SF_H
+#define GB300_SWARM_SF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SF_ABI_VERSION 1
+#define SF_MAX_SCENES 4096   /* scenes in one sf_batch */
+#define SF_MAX_ROBOTS 32     /* N per scene */
+#define SF_MAX_T 1024        /* time steps */
+
+typedef enum {
+  SF_OK = 0,
+  SF_ERR_INVALID_ARG = 1,   /* bad size, shape, pointer or value */
+  SF_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  SF_ERR_OOM = 3,           /* handle-owned allocation failed */
+  SF_ERR_TIMEOUT = 4,       /* a bounded device wait ran out */
+  SF_ERR_NONFINITE = 5,     /* a non-finite value reached the output */
+  SF_ERR_UNSUPPORTED = 6,   /* valid request this build does not implement */
+  SF_ERR_WORKSPACE = 7      /* workspace missing or too small */
+} sf_status;
+
+/* Arithmetic of the contractions (coefficients -> states, and F^T of the
+ * residual). The projections, residuals and multiplier updates are float32 in
+ * every mode; the one-time factorisation of the KKT matrix is float64. */
+typedef enum {
+  SF_PREC_FP32 = 0,  /* float32 everywhere */
+  SF_PREC_BF16 = 1,  /* tensor-core bf16 products, float32 accumulation */
+  SF_PREC_FP16 = 2   /* tensor-core fp16 products, float32 accumulation */
+} sf_precision;
+
+/* How the iteration is laid out on the GPU. */
+typedef enum {
+  SF_FORM_FUSED = 0, /* one persistent launch: state resident on chip for all K iterations */
+  SF_FORM_PLAIN = 1  /* one launch per step per iteration, time-domain arrays in HBM (workspace) */
+} sf_form;
+
+/* Problem constants shared by every scene of a handle (paper Sec. II and the
+ * Appendix). */
+typedef struct {
+  int dim;             /* 2 or 3 */
+  int order;           /* Bernstein order of Eq. (poly); nvar = order + 1; this build: 10 */
+  int T;               /* time steps on tau_j = j/(T-1); 2..SF_MAX_T */
+  double t_final;      /* horizon H in seconds, > 0 */
+  double rho;          /* weight of Eq. (aug_lag), > 0 */
+  double coll_a;       /* collision semi-axes (a, a, b) of M_a, Eq. (inter_robot_con); > 0 */
+  double coll_b;
+  double v_max;        /* velocity bound (norm); <= 0 disables the block */
+  double a_max;        /* acceleration bound (norm); <= 0 disables the block */
+  int use_workspace;   /* Eq. (workspace_con); must be 0 in this build */
+  double ws_center[3];
+  double ws_a, ws_b;
+  int max_robots;      /* largest N of any scene used with the handle, 1..SF_MAX_ROBOTS */
+  int precision;       /* sf_precision */
+  int checkpoint_every;/* k of the checkpointed backward; 0 = no gradient support */
+} sf_problem;
+
+/* A batch of scenes. Scene s has N_s robots and S_s samples. */
+typedef struct {
+  int n_scenes;              /* 1..SF_MAX_SCENES */
+  const int *n_robots;       /* HOST [n_scenes], each 1..max_robots */
+  const int *n_samples;      /* HOST [n_scenes], each >= 0 */
+  const float *start;        /* device [sum N_s][dim] start positions (b_0, Eq. boundary_con) */
+  const float *goal;         /* device [sum N_s][dim] goal positions (b_H) */
+  const float *start_va;     /* device [sum N_s][2][dim] start velocity, acceleration; NULL = 0 */
+  const float *goal_va;      /* device [sum N_s][2][dim] goal velocity, acceleration; NULL = 0 */
+  const float *xi_bar;       /* device coefficients of the sampled trajectories (Eq. sf_form) */
+} sf_batch;
+
+typedef struct sf_handle sf_handle;
+
+/* Creates a handle on CUDA device `device`: computes on the GPU, in float64,
+ * the Bernstein matrices of Eq. (poly) and, for every N in 1..max_robots, the
+ * solution operators of the xi step (the KKT matrix of the Appendix is
+ * input-independent, so its factorisation is pre-stored). Synchronises the
+ * device once. *out is NULL on failure. */
+sf_status sf_create(const sf_problem *problem, int device, sf_handle **out);
+
+/* Frees the handle and its device memory. NULL is a no-op. */
+void sf_destroy(sf_handle *h);
+
+/* Last error message of the handle (static storage until the next call on it). */
+const char *sf_last_error(const sf_handle *h);
+
+/* Device workspace, in bytes, that sf_project needs for `batch` in `form`
+ * with `K` iterations. The fused form needs 0 unless residual_hist or
+ * checkpoints are requested; the plain form holds its time-domain arrays
+ * here. Returns 0 and sets the error on invalid input. */
+size_t sf_workspace_bytes(const sf_handle *h, const sf_batch *batch, int form, int K);
+
+/* Bytes of the checkpoint buffer sf_project writes for sf_project_backward:
+ * (xi, lambda) of every sample every checkpoint_every iterations. */
+size_t sf_checkpoint_bytes(const sf_handle *h, const sf_batch *batch, int K);
+
+/* Runs K >= 1 iterations of f_FP on every sample of the batch.
+ *   xi0, lambda0   device initial iterate, same layout as xi_bar; NULL gives
+ *                  the sample init xi0 = xi_bar, lambda0 = 0.
+ *   xi_out, lambda_out   device, the K-th iterate (required).
+ *   residual_out   device [sum S_s]: ||r_p||_2 of Eq. (primal_residual) after
+ *                  iteration K, i.e. ||F xi^K - e(xi^{K-1})||_2 (required).
+ *   residual_hist  device [K][sum S_s] or NULL: ||F xi^k - e(xi^k)||_2 at the
+ *                  start of iteration k (the projection residual).
+ *   workspace      device, sf_workspace_bytes() bytes (may be NULL when 0).
+ *   checkpoints    device, sf_checkpoint_bytes() bytes, or NULL for no gradient.
+ * The output buffers must not overlap the inputs. */
+sf_status sf_project(sf_handle *h, void *stream, const sf_batch *batch, int K, int form,
+                     const float *xi0, const float *lambda0, float *xi_out, float *lambda_out,
+                     float *residual_out, float *residual_hist, void *workspace,
+                     size_t workspace_bytes, void *checkpoints);
+
+/* Device staging bytes sf_project_host needs for `batch` (whose pointers are
+ * host pointers in that call): the inputs, the outputs and, for the plain
+ * form, its workspace. */
+size_t sf_host_staging_bytes(const sf_handle *h, const sf_batch *batch, int form, int K);
+
+/* sf_project on HOST buffers: copies the batch (and xi0 / lambda0 when not
+ * NULL) into `staging` (device, sf_host_staging_bytes() bytes), runs the
+ * same launches as sf_project, copies xi, lambda and the residuals back into
+ * the host arrays, and synchronises `stream` before returning. Pinned host
+ * memory gives asynchronous copies; pageable memory works but copies
+ * synchronously. */
+sf_status sf_project_host(sf_handle *h, void *stream, const sf_batch *batch, int K, int form,
+                          const float *xi0, const float *lambda0, float *xi_out,
+                          float *lambda_out, float *residual_out, void *staging,
+                          size_t staging_bytes);
+
+/* Number of kernels the handle has launched so far (all calls, all streams).
+ * Lets a caller count the library's launches inside a timed region. */
+unsigned long long sf_launch_count(const sf_handle *h);
+
+/* Synchronises `stream` and returns any device-side error latched by earlier
+ * calls on the handle (SF_ERR_TIMEOUT, SF_ERR_NONFINITE), clearing it. */
+sf_status sf_sync_status(sf_handle *h, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

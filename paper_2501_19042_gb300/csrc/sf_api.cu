@@ -1,0 +1,441 @@
+// Host side of the C ABI declared in include/sf.h: argument validation,
+// handle lifetime, work decomposition of a batch into launches, and the
+// device-status word.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sf_internal.cuh"
+
+struct sf_handle {
+  sf_problem pb;
+  int device = 0;
+  int num_sms = 0;
+  size_t max_smem_optin = 0;
+  float* basis = nullptr;   // [T][BASIS_ROW]
+  float* ops = nullptr;     // [max_robots + 1][OPS_STRIDE]
+  int* status = nullptr;    // device status word
+  unsigned long long launches = 0;
+  std::string err;
+};
+
+namespace {
+
+using namespace sf;
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+sf_status fail(sf_handle* h, sf_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+sf_status cuda_fail(sf_handle* h, cudaError_t e, const char* where) {
+  return fail(h, SF_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+int nmax_bucket(int N) { return N <= 8 ? 8 : (N <= 16 ? 16 : 32); }
+
+ProblemConsts consts(const sf_problem& pb, int K) {
+  ProblemConsts c;
+  c.dim = pb.dim;
+  c.T = pb.T;
+  c.K = K;
+  c.rho = (float)pb.rho;
+  c.inv_a2 = (float)(1.0 / (pb.coll_a * pb.coll_a));
+  c.inv_b2 = (float)(1.0 / (pb.coll_b * pb.coll_b));
+  c.tie = (float)(pb.dim == 3 ? pb.coll_b : pb.coll_a);
+  c.use_v = pb.v_max > 0.0;
+  c.use_a = pb.a_max > 0.0;
+  c.v_max = (float)(c.use_v ? pb.v_max : 0.0);
+  c.a_max = (float)(c.use_a ? pb.a_max : 0.0);
+  return c;
+}
+
+sf_status check_batch(sf_handle* h, const sf_batch* b, long long* tot_robots, long long* tot_samples) {
+  if (!b) return fail(h, SF_ERR_INVALID_ARG, "batch is NULL");
+  if (b->n_scenes < 1 || b->n_scenes > SF_MAX_SCENES)
+    return fail(h, SF_ERR_INVALID_ARG, "n_scenes out of range");
+  if (!b->n_robots || !b->n_samples) return fail(h, SF_ERR_INVALID_ARG, "n_robots / n_samples is NULL");
+  long long R = 0, S = 0;
+  for (int s = 0; s < b->n_scenes; ++s) {
+    const int N = b->n_robots[s], Ss = b->n_samples[s];
+    if (N < 1 || N > h->pb.max_robots)
+      return fail(h, SF_ERR_INVALID_ARG, "scene " + std::to_string(s) + ": n_robots outside 1..max_robots");
+    if (Ss < 0) return fail(h, SF_ERR_INVALID_ARG, "scene " + std::to_string(s) + ": negative n_samples");
+    R += N;
+    S += Ss;
+  }
+  if (!b->start || !b->goal) return fail(h, SF_ERR_INVALID_ARG, "start / goal is NULL");
+  if (S > 0 && !b->xi_bar) return fail(h, SF_ERR_INVALID_ARG, "xi_bar is NULL");
+  if (S > (1LL << 30)) return fail(h, SF_ERR_INVALID_ARG, "too many samples");
+  *tot_robots = R;
+  *tot_samples = S;
+  return SF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sf_status sf_create(const sf_problem* pb, int device, sf_handle** out) {
+  if (!out) return SF_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!pb) return SF_ERR_INVALID_ARG;
+  if (pb->dim != 2 && pb->dim != 3) return SF_ERR_INVALID_ARG;
+  if (pb->order != 10) return SF_ERR_UNSUPPORTED;  // kernels are built for nvar = 11
+  if (pb->T < 2 || pb->T > SF_MAX_T) return SF_ERR_INVALID_ARG;
+  if (!finite_pos(pb->t_final) || !finite_pos(pb->rho) || !finite_pos(pb->coll_a) ||
+      !finite_pos(pb->coll_b))
+    return SF_ERR_INVALID_ARG;
+  if (!std::isfinite(pb->v_max) || !std::isfinite(pb->a_max)) return SF_ERR_INVALID_ARG;
+  if (pb->max_robots < 1 || pb->max_robots > SF_MAX_ROBOTS) return SF_ERR_INVALID_ARG;
+  if (pb->precision < SF_PREC_FP32 || pb->precision > SF_PREC_FP16) return SF_ERR_INVALID_ARG;
+  if (pb->checkpoint_every < 0) return SF_ERR_INVALID_ARG;
+  if (pb->use_workspace) return SF_ERR_UNSUPPORTED;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return SF_ERR_CUDA;
+
+  sf_handle* h = new (std::nothrow) sf_handle();
+  if (!h) return SF_ERR_OOM;
+  h->pb = *pb;
+  h->device = device;
+  DeviceGuard g(device);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete h; return SF_ERR_CUDA; }
+  h->num_sms = prop.multiProcessorCount;
+  h->max_smem_optin = prop.sharedMemPerBlockOptin;
+  double* scratch = nullptr;
+  const size_t nscr = precompute_scratch_doubles(pb->T, pb->order, pb->max_robots);
+  cudaError_t e = cudaMalloc(&h->basis, sizeof(float) * (size_t)pb->T * BASIS_ROW);
+  if (e == cudaSuccess) e = cudaMalloc(&h->ops, sizeof(float) * (size_t)(pb->max_robots + 1) * OPS_STRIDE);
+  if (e == cudaSuccess) e = cudaMalloc(&h->status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&scratch, sizeof(double) * nscr);
+  if (e != cudaSuccess) {
+    cudaFree(scratch);
+    sf_destroy(h);
+    return SF_ERR_OOM;
+  }
+  cudaStream_t st;
+  e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) {
+    e = cudaMemsetAsync(h->status, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+      e = launch_precompute(pb->T, pb->order, pb->t_final, pb->rho, pb->v_max > 0, pb->a_max > 0,
+                            pb->max_robots, h->basis, h->ops, scratch, st);
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  cudaFree(scratch);
+  if (e != cudaSuccess) {
+    sf_destroy(h);
+    return e == cudaErrorInvalidValue ? SF_ERR_INVALID_ARG : SF_ERR_CUDA;
+  }
+  *out = h;
+  return SF_OK;
+}
+
+void sf_destroy(sf_handle* h) {
+  if (!h) return;
+  DeviceGuard g(h->device);
+  cudaFree(h->basis);
+  cudaFree(h->ops);
+  cudaFree(h->status);
+  delete h;
+}
+
+const char* sf_last_error(const sf_handle* h) { return h ? h->err.c_str() : "NULL handle"; }
+
+size_t sf_workspace_bytes(const sf_handle* hc, const sf_batch* b, int form, int K) {
+  sf_handle* h = const_cast<sf_handle*>(hc);
+  if (!h) return 0;
+  long long R = 0, S = 0;
+  if (check_batch(h, b, &R, &S) != SF_OK) return 0;
+  if (K < 1) return 0;
+  if (form == SF_FORM_FUSED) return 0;
+  if (form != SF_FORM_PLAIN) return 0;
+  size_t best = 0;
+  for (int s = 0; s < b->n_scenes; ++s)
+    best = std::max(best, plain_workspace_floats(h->pb.dim, b->n_robots[s], b->n_samples[s], h->pb.T));
+  return best * sizeof(float) + 256;
+}
+
+size_t sf_checkpoint_bytes(const sf_handle* hc, const sf_batch* b, int K) {
+  sf_handle* h = const_cast<sf_handle*>(hc);
+  if (!h || h->pb.checkpoint_every <= 0 || K < 1) return 0;
+  long long R = 0, S = 0;
+  if (check_batch(h, b, &R, &S) != SF_OK) return 0;
+  const long long nck = (K + h->pb.checkpoint_every - 1) / h->pb.checkpoint_every;
+  long long coefs = 0;
+  for (int s = 0; s < b->n_scenes; ++s) coefs += (long long)b->n_samples[s] * h->pb.dim * b->n_robots[s] * NV;
+  return (size_t)(nck * 2 * coefs) * sizeof(float);
+}
+
+sf_status sf_project(sf_handle* h, void* stream, const sf_batch* b, int K, int form, const float* xi0,
+                     const float* lam0, float* xi_out, float* lam_out, float* resid_out,
+                     float* resid_hist, void* workspace, size_t workspace_bytes, void* checkpoints) {
+  if (!h) return SF_ERR_INVALID_ARG;
+  long long R = 0, S = 0;
+  sf_status s0 = check_batch(h, b, &R, &S);
+  if (s0 != SF_OK) return s0;
+  if (K < 1) return fail(h, SF_ERR_INVALID_ARG, "K must be >= 1");
+  if (S > 0 && (!xi_out || !lam_out || !resid_out))
+    return fail(h, SF_ERR_INVALID_ARG, "xi_out / lambda_out / residual_out is NULL");
+  if (form != SF_FORM_FUSED && form != SF_FORM_PLAIN) return fail(h, SF_ERR_INVALID_ARG, "unknown form");
+  if (h->pb.precision != SF_PREC_FP32)
+    return fail(h, SF_ERR_UNSUPPORTED, "only SF_PREC_FP32 is built into this library");
+  if (checkpoints) return fail(h, SF_ERR_UNSUPPORTED, "checkpointed forward not built");
+  if (S == 0) return SF_OK;
+  DeviceGuard g(h->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int dim = h->pb.dim, T = h->pb.T;
+  const ProblemConsts pc = consts(h->pb, K);
+
+  if (form == SF_FORM_PLAIN) {
+    const size_t need = sf_workspace_bytes(h, b, form, K);
+    if (!workspace || workspace_bytes < need)
+      return fail(h, SF_ERR_WORKSPACE, "plain form needs " + std::to_string(need) + " workspace bytes");
+    long long roff = 0, soff = 0, coff = 0;
+    float* ws = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(workspace) + 255) & ~uintptr_t(255));
+    for (int sc = 0; sc < b->n_scenes; ++sc) {
+      const int N = b->n_robots[sc], Ss = b->n_samples[sc];
+      const size_t n = (size_t)Ss * dim * N * NV;
+      const size_t xs = (size_t)Ss * 3 * dim * N * (size_t)T;
+      PlainArgs a;
+      a.pc = pc;
+      a.basis = reinterpret_cast<const float4*>(h->basis);
+      a.ops = h->ops;
+      a.N = N;
+      a.S = Ss;
+      a.start = b->start + roff * dim;
+      a.goal = b->goal + roff * dim;
+      a.start_va = b->start_va ? b->start_va + roff * 2 * dim : nullptr;
+      a.goal_va = b->goal_va ? b->goal_va + roff * 2 * dim : nullptr;
+      a.xi_bar = b->xi_bar + coff;
+      a.xi = xi_out + coff;
+      a.lam = lam_out + coff;
+      a.resid_out = resid_out + soff;
+      a.hist = resid_hist ? resid_hist + soff : nullptr;
+      a.hist_stride = (int)S;
+      a.beta = ws;
+      a.X = ws + (size_t)dim * N * NP;
+      a.Q = a.X + xs;
+      a.g = a.Q + xs;
+      a.xprev = a.g + n;
+      a.r2 = a.xprev + n;
+      a.status = h->status;
+      cudaError_t e = launch_plain(a, xi0 ? xi0 + coff : nullptr, lam0 ? lam0 + coff : nullptr, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "plain form launch");
+      if (Ss > 0) h->launches += 2 + 4ULL * K + 3;
+      roff += N;
+      soff += Ss;
+      coff += (long long)n;
+    }
+    return SF_OK;
+  }
+
+  // ---- fused form: scenes grouped by robot-count bucket, one launch per group
+  struct Item { int scene; long long roff, soff, coff; };
+  std::vector<Item> items[3];
+  {
+    long long roff = 0, soff = 0, coff = 0;
+    for (int sc = 0; sc < b->n_scenes; ++sc) {
+      const int N = b->n_robots[sc], Ss = b->n_samples[sc];
+      const int bk = nmax_bucket(N) == 8 ? 0 : (nmax_bucket(N) == 16 ? 1 : 2);
+      if (Ss > 0) items[bk].push_back({sc, roff, soff, coff});
+      roff += N;
+      soff += Ss;
+      coff += (long long)Ss * dim * N * NV;
+    }
+  }
+  const int maxw = fused_max_warps();
+  const int TB = (T + 31) / 32;
+  for (int bk = 0; bk < 3; ++bk) {
+    const int nmax = 8 << bk;
+    for (size_t first = 0; first < items[bk].size(); first += MAX_SCENES_PER_LAUNCH) {
+      const size_t last = std::min(items[bk].size(), first + (size_t)MAX_SCENES_PER_LAUNCH);
+      long long tot = 0;
+      for (size_t q = first; q < last; ++q) tot += b->n_samples[items[bk][q].scene];
+      // samples per CTA: spread the group over one wave of CTAs, bounded by shared memory
+      int gcap = 1;
+      while (gcap < 64 && fused_smem_bytes(dim, nmax, T, gcap + 1) <= h->max_smem_optin) ++gcap;
+      if (fused_smem_bytes(dim, nmax, T, 1) > h->max_smem_optin)
+        return fail(h, SF_ERR_UNSUPPORTED, "T too large for the fused form");
+      int G = (int)std::min<long long>(gcap, std::max<long long>(1, (tot + h->num_sms - 1) / h->num_sms));
+      FusedArgs a;
+      std::memset(&a, 0, sizeof(a));
+      a.pc = pc;
+      a.basis = reinterpret_cast<const float4*>(h->basis);
+      a.ops = h->ops;
+      a.start = b->start;
+      a.goal = b->goal;
+      a.start_va = b->start_va;
+      a.goal_va = b->goal_va;
+      a.xi_bar = b->xi_bar;
+      a.xi0 = xi0;
+      a.lam0 = lam0;
+      a.xi_out = xi_out;
+      a.lam_out = lam_out;
+      a.resid_out = resid_out;
+      a.hist = resid_hist;
+      a.total_samples = (int)S;
+      a.status = h->status;
+      int ctas = 0, gmax = 1;
+      a.n_scenes = (int)(last - first);
+      for (size_t q = first; q < last; ++q) {
+        const Item& it = items[bk][q];
+        SceneDesc& d = a.sc[q - first];
+        d.N = b->n_robots[it.scene];
+        d.S = b->n_samples[it.scene];
+        d.G = std::min(G, d.S);
+        d.cta_begin = ctas;
+        d.robot_off = (int)it.roff;
+        d.sample_off = (int)it.soff;
+        d.coef_off = it.coff;
+        ctas += (d.S + d.G - 1) / d.G;
+        gmax = std::max(gmax, d.G);
+      }
+      FusedLaunch l;
+      l.nmax = nmax;
+      l.gmax = gmax;
+      l.n_ctas = ctas;
+      const int units = gmax * TB;
+      const int rounds = (units + maxw - 1) / maxw;
+      l.warps = std::max(1, (units + rounds - 1) / rounds);
+      if (nmax == 32) l.warps = std::min(l.warps, 12);
+      l.smem = fused_smem_bytes(dim, nmax, T, gmax);
+      cudaError_t e = launch_fused(a, l, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "fused form launch");
+      h->launches += 1;
+    }
+  }
+  return SF_OK;
+}
+
+unsigned long long sf_launch_count(const sf_handle* h) { return h ? h->launches : 0ULL; }
+
+namespace {
+struct HostPlan {
+  size_t off_start, off_goal, off_sva, off_gva, off_xib, off_xi0, off_lam0, off_xi, off_lam, off_res,
+      off_ws, total;
+  long long R, S, coefs;
+  size_t ws;
+};
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+sf_status host_plan(sf_handle* h, const sf_batch* b, int form, int K, HostPlan* p) {
+  sf_status s = check_batch(h, b, &p->R, &p->S);
+  if (s != SF_OK) return s;
+  if (K < 1) return fail(h, SF_ERR_INVALID_ARG, "K must be >= 1");
+  const int dim = h->pb.dim;
+  p->coefs = 0;
+  for (int sc = 0; sc < b->n_scenes; ++sc) p->coefs += (long long)b->n_samples[sc] * dim * b->n_robots[sc] * NV;
+  p->ws = sf_workspace_bytes(h, b, form, K);
+  size_t o = 0;
+  const size_t pos = sizeof(float) * (size_t)p->R * dim, va = 2 * pos, cf = sizeof(float) * (size_t)p->coefs;
+  p->off_start = o; o = align256(o + pos);
+  p->off_goal = o; o = align256(o + pos);
+  p->off_sva = o; o = align256(o + va);
+  p->off_gva = o; o = align256(o + va);
+  p->off_xib = o; o = align256(o + cf);
+  p->off_xi0 = o; o = align256(o + cf);
+  p->off_lam0 = o; o = align256(o + cf);
+  p->off_xi = o; o = align256(o + cf);
+  p->off_lam = o; o = align256(o + cf);
+  p->off_res = o; o = align256(o + sizeof(float) * (size_t)p->S);
+  p->off_ws = o; o = align256(o + p->ws);
+  p->total = o + 256;
+  return SF_OK;
+}
+}  // namespace
+
+size_t sf_host_staging_bytes(const sf_handle* hc, const sf_batch* b, int form, int K) {
+  sf_handle* h = const_cast<sf_handle*>(hc);
+  if (!h) return 0;
+  HostPlan p;
+  if (host_plan(h, b, form, K, &p) != SF_OK) return 0;
+  return p.total;
+}
+
+sf_status sf_project_host(sf_handle* h, void* stream, const sf_batch* b, int K, int form, const float* xi0,
+                          const float* lam0, float* xi_out, float* lam_out, float* resid_out,
+                          void* staging, size_t staging_bytes) {
+  if (!h) return SF_ERR_INVALID_ARG;
+  HostPlan p;
+  sf_status s = host_plan(h, b, form, K, &p);
+  if (s != SF_OK) return s;
+  if (p.S > 0 && (!xi_out || !lam_out || !resid_out))
+    return fail(h, SF_ERR_INVALID_ARG, "xi_out / lambda_out / residual_out is NULL");
+  if (!staging || staging_bytes < p.total)
+    return fail(h, SF_ERR_WORKSPACE, "staging needs " + std::to_string(p.total) + " bytes");
+  DeviceGuard g(h->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(staging) + 255) & ~uintptr_t(255));
+  const int dim = h->pb.dim;
+  const size_t pos = sizeof(float) * (size_t)p.R * dim, cf = sizeof(float) * (size_t)p.coefs;
+  auto h2d = [&](size_t off, const void* src, size_t n) -> cudaError_t {
+    return (src && n) ? cudaMemcpyAsync(base + off, src, n, cudaMemcpyHostToDevice, st) : cudaSuccess;
+  };
+  cudaError_t e = h2d(p.off_start, b->start, pos);
+  if (e == cudaSuccess) e = h2d(p.off_goal, b->goal, pos);
+  if (e == cudaSuccess) e = h2d(p.off_sva, b->start_va, 2 * pos);
+  if (e == cudaSuccess) e = h2d(p.off_gva, b->goal_va, 2 * pos);
+  if (e == cudaSuccess) e = h2d(p.off_xib, b->xi_bar, cf);
+  if (e == cudaSuccess) e = h2d(p.off_xi0, xi0, cf);
+  if (e == cudaSuccess) e = h2d(p.off_lam0, lam0, cf);
+  if (e != cudaSuccess) return cuda_fail(h, e, "host-to-device copy");
+  sf_batch db = *b;
+  db.start = reinterpret_cast<const float*>(base + p.off_start);
+  db.goal = reinterpret_cast<const float*>(base + p.off_goal);
+  db.start_va = b->start_va ? reinterpret_cast<const float*>(base + p.off_sva) : nullptr;
+  db.goal_va = b->goal_va ? reinterpret_cast<const float*>(base + p.off_gva) : nullptr;
+  db.xi_bar = reinterpret_cast<const float*>(base + p.off_xib);
+  float* dxi = reinterpret_cast<float*>(base + p.off_xi);
+  float* dlam = reinterpret_cast<float*>(base + p.off_lam);
+  float* dres = reinterpret_cast<float*>(base + p.off_res);
+  s = sf_project(h, stream, &db, K, form, xi0 ? reinterpret_cast<const float*>(base + p.off_xi0) : nullptr,
+                 lam0 ? reinterpret_cast<const float*>(base + p.off_lam0) : nullptr, dxi, dlam, dres, nullptr,
+                 p.ws ? base + p.off_ws : nullptr, p.ws, nullptr);
+  if (s != SF_OK) return s;
+  e = cudaMemcpyAsync(xi_out, dxi, cf, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(lam_out, dlam, cf, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(resid_out, dres, sizeof(float) * (size_t)p.S, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "device-to-host copy");
+  return SF_OK;
+}
+
+sf_status sf_sync_status(sf_handle* h, void* stream) {
+  if (!h) return SF_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "stream synchronize");
+  int word = 0;
+  e = cudaMemcpy(&word, h->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "status read");
+  if (word) {
+    cudaMemset(h->status, 0, sizeof(int));
+    if (word & ST_TIMEOUT) return fail(h, SF_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (word & ST_NONFINITE) return fail(h, SF_ERR_NONFINITE, "non-finite value in the output");
+  }
+  return SF_OK;
+}
+
+}  // extern "C"

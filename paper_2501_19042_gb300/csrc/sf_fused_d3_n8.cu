@@ -1,0 +1,8 @@
+// Fused forward kernel instantiated for dim = 3, up to 8 robots.
+#include "sf_fused_kernel.cuh"
+
+namespace sf {
+cudaError_t launch_fused_d3_n8(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st) {
+  return fused_impl::launch_t<3, 8, 448>(a, l, st);
+}
+}  // namespace sf

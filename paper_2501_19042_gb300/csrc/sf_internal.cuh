@@ -1,0 +1,170 @@
+// Internal declarations of the GB300 safety-filter library: data layouts on
+// the device, launch descriptors and the per-element closed forms shared by
+// the fused, plain and adjoint kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sf.h"
+
+namespace sf {
+
+// Coefficients per robot-axis in the kernels: Bernstein order 10 (nvar = 11),
+// stored padded to 12 floats so that a row is three float4.
+constexpr int NV = 11;
+constexpr int NP = 12;
+
+// Basis table: per time step t, 36 floats = P[t][0..11], Pd[t][0..11],
+// Pdd[t][0..11] (entry 11 of each row is 0).
+constexpr int BASIS_ROW = 3 * NP;
+
+// xi-step operators for one value of N (all float32, [k][m], m padded to 12):
+//   W1 = S_dev rho H_dev, S1 = S_dev, DW = W_mean - W_dev, DS = S_mean - S_dev,
+//   R0 = R_mean, R1 = R_dev ([k][q], q < 6, padded to 8).
+// The xi step then is, per robot i and axis (Appendix, xi step, with the
+// mean / deviation split of I + rho F^T F):
+//   c_i' = W1 c_i + S1 r_i + DW cbar + DS rbar + beta_i,
+//   beta_i = R1 b_i + (R0 - R1) bbar,   r = rho g + lambda' + xi_bar.
+constexpr int OPS_W1 = 0;
+constexpr int OPS_S1 = 1 * NV * NP;
+constexpr int OPS_DW = 2 * NV * NP;
+constexpr int OPS_DS = 3 * NV * NP;
+constexpr int OPS_R0 = 4 * NV * NP;
+constexpr int OPS_R1 = 4 * NV * NP + NV * 8;
+constexpr int OPS_STRIDE = 4 * NV * NP + 2 * NV * 8;  // floats per N
+
+// Scenes per launch descriptor (kernel parameter space).
+constexpr int MAX_SCENES_PER_LAUNCH = 192;
+
+struct SceneDesc {
+  int N;           // robots
+  int S;           // samples
+  int G;           // samples per CTA (fused) / unused (plain)
+  int cta_begin;   // first CTA of this scene in the launch
+  int robot_off;   // row offset into start / goal
+  int sample_off;  // global index of the scene's first sample
+  long long coef_off;  // float offset of the scene's first sample in coefficient arrays
+};
+
+// Bounded-wait / status words latched on the device.
+enum : int { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
+
+struct ProblemConsts {
+  int dim, T, K;
+  float rho;
+  float inv_a2, inv_b2;  // 1/a^2, 1/b^2 of the collision spheroid
+  float tie;             // e of a pair at delta = 0: (0,0,b) in 3D, (a,0) in 2D
+  float v_max, a_max;
+  int use_v, use_a;
+};
+
+struct FusedArgs {
+  ProblemConsts pc;
+  int n_scenes;
+  const float4* basis;     // [T][9] float4
+  const float* ops;        // [max_robots + 1][OPS_STRIDE]
+  const float* start;      // [sum N][dim]
+  const float* goal;
+  const float* start_va;   // [sum N][2][dim] or null
+  const float* goal_va;
+  const float* xi_bar;
+  const float* xi0;        // or null (sample init)
+  const float* lam0;       // or null (zero)
+  float* xi_out;
+  float* lam_out;
+  float* resid_out;        // [total samples]
+  float* hist;             // [K][total samples] or null
+  int total_samples;
+  int* status;
+  SceneDesc sc[MAX_SCENES_PER_LAUNCH];
+};
+
+// ---- per-element closed forms (Appendix, alpha / beta / d steps) ----------
+//
+// Pair block: with scaled distance s2 = (dx^2 + dy^2)/a^2 + dz^2/b^2, the
+// alpha / beta / d closed forms give e = delta when s2 >= 1 and
+// e = delta / sqrt(s2) otherwise (d clipped to 1); at delta = 0 the tie-break
+// alpha = beta = 0 gives e = (0, 0, b) (3D) or (a, 0) (2D). Returned is
+// q = e - delta and its squared norm is added to res2.
+template <int DIM>
+__device__ __forceinline__ void pair_residual(const float* pi, const float* pj, float* q,
+                                              const ProblemConsts& pc, float& res2) {
+  float d[DIM];
+#pragma unroll
+  for (int x = 0; x < DIM; ++x) d[x] = pi[x] - pj[x];
+  float s2;
+  if (DIM == 3)
+    s2 = fmaf(d[2] * d[2], pc.inv_b2, (d[0] * d[0] + d[1] * d[1]) * pc.inv_a2);
+  else
+    s2 = (d[0] * d[0] + d[1] * d[1]) * pc.inv_a2;
+  const bool zero = (s2 == 0.0f);
+  float s = fmaxf(rsqrtf(s2) - 1.0f, 0.0f);
+  s = zero ? 0.0f : s;
+#pragma unroll
+  for (int x = 0; x < DIM; ++x) q[x] = s * d[x];
+  if (zero) q[DIM == 3 ? 2 : 0] = pc.tie;
+#pragma unroll
+  for (int x = 0; x < DIM; ++x) res2 = fmaf(q[x], q[x], res2);
+}
+
+// Velocity / acceleration block (polar form with centre 0, d in [0, 1]): the
+// Euclidean ball projection. q = e - v = -max(0, 1 - r/||v||) v; at v = 0, q = 0.
+template <int DIM>
+__device__ __forceinline__ void ball_residual(const float* v, float r, float* q, float& res2) {
+  float n2 = 0.0f;
+#pragma unroll
+  for (int x = 0; x < DIM; ++x) n2 = fmaf(v[x], v[x], n2);
+  const float s = fmaxf(fmaf(-r, rsqrtf(n2), 1.0f), 0.0f);
+#pragma unroll
+  for (int x = 0; x < DIM; ++x) {
+    q[x] = -s * v[x];
+    res2 = fmaf(q[x], q[x], res2);
+  }
+}
+
+// ---- host-side launchers (defined in the .cu files) ------------------------
+cudaError_t launch_precompute(int T, int order, double t_final, double rho, int use_v, int use_a,
+                              int max_robots, float* basis32, float* ops32, double* scratch64,
+                              cudaStream_t st);
+size_t precompute_scratch_doubles(int T, int order, int max_robots);
+
+struct FusedLaunch {
+  int nmax;     // 8, 16 or 32
+  int warps;    // warps per CTA
+  int gmax;     // largest samples-per-CTA of the scenes in this launch
+  int n_ctas;
+  size_t smem;  // dynamic shared memory bytes
+};
+size_t fused_smem_bytes(int dim, int nmax, int T, int gmax);
+cudaError_t launch_fused(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st);
+int fused_max_warps();
+
+struct PlainArgs {
+  ProblemConsts pc;
+  const float4* basis;
+  const float* ops;
+  int N, S;
+  const float* start;     // [N][dim] of this scene
+  const float* goal;
+  const float* start_va;
+  const float* goal_va;
+  const float* xi_bar;    // [S][dim][N][NV] for this scene
+  float* xi;              // iterate (xi_out), [S][dim][N][NV]
+  float* lam;             // multiplier (lambda_out)
+  float* resid_out;       // [S]
+  float* hist;            // [K][total] pointer already offset to this scene, or null
+  int hist_stride;        // total samples
+  // workspace (all float)
+  float* beta;            // [dim][N][NP]
+  float* X;               // states p, v, a: [S][3][dim][N][T]
+  float* Q;               // residuals E, qv, qa: [S][3][dim][N][T]
+  float* g;               // F^T q: [S][dim][N][NV]
+  float* xprev;           // [S][dim][N][NV]
+  float* r2;              // [S]
+  int* status;
+};
+size_t plain_workspace_floats(int dim, int N, int S, int T);
+cudaError_t launch_plain(const PlainArgs& a, const float* xi0, const float* lam0, cudaStream_t st);
+
+}  // namespace sf

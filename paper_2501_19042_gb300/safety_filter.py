@@ -1,0 +1,190 @@
+"""Python front end of the GB300 safety filter (argument marshalling only).
+
+Every step of the solver runs in the CUDA library behind ``include/sf.h``;
+this module allocates device tensors with PyTorch, passes raw pointers and
+the caller's CUDA stream, and turns status codes into exceptions.
+
+Shapes (float32, contiguous):
+  single scene:  xi_bar [S, dim, N, nvar], start / goal [N, dim]
+  many scenes:   xi_bar flat [sum_s S_s * dim * N_s * nvar], start / goal
+                 [sum_s N_s, dim], with ``n_robots`` / ``n_samples`` lists.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import torch
+
+from . import _native as nat
+
+NVAR = 11
+
+
+@dataclass
+class ProjectResult:
+    xi: torch.Tensor
+    lam: torch.Tensor
+    residual: torch.Tensor
+    hist: torch.Tensor | None = None
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class SafetyFilter:
+    """Handle over ``sf_create`` / ``sf_project`` / ``sf_destroy``."""
+
+    def __init__(self, dim: int = 3, T: int = 100, rho: float = 0.1, coll_a: float = 0.5,
+                 coll_b: float | None = None, v_max: float = 2.0, a_max: float = 3.0,
+                 max_robots: int = 32, order: int = 10, t_final: float = 5.0,
+                 precision: str = "fp32", checkpoint_every: int = 0, device=None):
+        self._lib = nat.load()
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = torch.device("cuda", device if isinstance(device, int) else torch.device(device).index or 0)
+        pb = nat.SfProblem()
+        pb.dim, pb.order, pb.T, pb.t_final, pb.rho = dim, order, T, t_final, rho
+        pb.coll_a = coll_a
+        pb.coll_b = coll_a if coll_b is None else coll_b
+        pb.v_max, pb.a_max = v_max, a_max
+        pb.use_workspace = 0
+        pb.max_robots = max_robots
+        pb.precision = nat.PREC[precision]
+        pb.checkpoint_every = checkpoint_every
+        self.pb = pb
+        self.dim, self.T, self.order = dim, T, order
+        self.nvar = order + 1
+        h = C.c_void_p()
+        code = self._lib.sf_create(C.byref(pb), self.device.index, C.byref(h))
+        if code != nat.SF_OK:
+            raise nat.SfError(code, "sf_create failed")
+        self._h = h
+        self._ws = None
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._lib.sf_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- batch marshalling ---------------------------------------------------------
+    def _batch(self, xi_bar, start, goal, n_robots, n_samples, start_va, goal_va):
+        if n_robots is None:
+            S, dim, N, nv = xi_bar.shape
+            if dim != self.dim or nv != self.nvar:
+                raise ValueError(f"xi_bar must be [S, {self.dim}, N, {self.nvar}]")
+            n_robots, n_samples = [N], [S]
+        nr = (C.c_int * len(n_robots))(*[int(v) for v in n_robots])
+        ns = (C.c_int * len(n_samples))(*[int(v) for v in n_samples])
+        for name, t in (("xi_bar", xi_bar), ("start", start), ("goal", goal), ("start_va", start_va),
+                        ("goal_va", goal_va)):
+            if t is not None:
+                if t.dtype != torch.float32 or not t.is_contiguous():
+                    raise ValueError(f"{name} must be a contiguous float32 tensor")
+                if t.device != self.device:
+                    raise ValueError(f"{name} must live on {self.device}")
+        tot_r = sum(int(v) for v in n_robots)
+        tot_c = sum(int(s) * self.dim * int(n) * self.nvar for n, s in zip(n_robots, n_samples))
+        if start.numel() != tot_r * self.dim or goal.numel() != tot_r * self.dim:
+            raise ValueError("start / goal size does not match n_robots")
+        if xi_bar.numel() != tot_c:
+            raise ValueError("xi_bar size does not match n_robots / n_samples")
+        b = nat.SfBatch()
+        b.n_scenes = len(n_robots)
+        b.n_robots, b.n_samples = nr, ns
+        b.start, b.goal = start.data_ptr(), goal.data_ptr()
+        b.start_va = start_va.data_ptr() if start_va is not None else None
+        b.goal_va = goal_va.data_ptr() if goal_va is not None else None
+        b.xi_bar = xi_bar.data_ptr()
+        keep = (nr, ns)
+        return b, keep, tot_c, sum(int(s) for s in n_samples)
+
+    def workspace_bytes(self, xi_bar, start, goal, K, form="fused", n_robots=None, n_samples=None):
+        b, _keep, _, _ = self._batch(xi_bar, start, goal, n_robots, n_samples, None, None)
+        return int(self._lib.sf_workspace_bytes(self._h, C.byref(b), nat.FORM[form], int(K)))
+
+    def _workspace(self, nbytes):
+        if nbytes == 0:
+            return None
+        if self._ws is None or self._ws.numel() < nbytes:
+            self._ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def project(self, xi_bar, start, goal, K: int, n_robots=None, n_samples=None, xi0=None, lam0=None,
+                start_va=None, goal_va=None, form: str = "fused", hist: bool = False,
+                out: ProjectResult | None = None, stream=None) -> ProjectResult:
+        """K iterations of the SF on device tensors, asynchronously on ``stream``
+        (default: the current PyTorch stream)."""
+        b, keep, ncoef, nsamp = self._batch(xi_bar, start, goal, n_robots, n_samples, start_va, goal_va)
+        for name, t in (("xi0", xi0), ("lam0", lam0)):
+            if t is not None and (t.numel() != ncoef or t.dtype != torch.float32 or not t.is_contiguous()):
+                raise ValueError(f"{name} must match xi_bar")
+        if out is None:
+            out = ProjectResult(
+                xi=torch.empty_like(xi_bar), lam=torch.empty_like(xi_bar),
+                residual=torch.empty(nsamp, dtype=torch.float32, device=self.device),
+                hist=torch.empty((K, nsamp), dtype=torch.float32, device=self.device) if hist else None)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        wsb = int(self._lib.sf_workspace_bytes(self._h, C.byref(b), nat.FORM[form], int(K)))
+        ws = self._workspace(wsb)
+        code = self._lib.sf_project(self._h, C.c_void_p(stream.cuda_stream), C.byref(b), int(K),
+                                    nat.FORM[form], _ptr(xi0), _ptr(lam0), _ptr(out.xi), _ptr(out.lam),
+                                    _ptr(out.residual), _ptr(out.hist), _ptr(ws), C.c_size_t(wsb), None)
+        del keep
+        nat.check(self._lib, self._h, code)
+        return out
+
+    def project_host(self, xi_bar, start, goal, K: int, n_robots=None, n_samples=None, xi0=None,
+                     lam0=None, start_va=None, goal_va=None, form: str = "fused", out=None, stream=None):
+        """``sf_project_host``: host (preferably pinned) float32 tensors in and out;
+        the host-to-device and device-to-host copies happen inside the call, which
+        returns after synchronising the stream."""
+        if n_robots is None:
+            S, _, N, _ = xi_bar.shape
+            n_robots, n_samples = [N], [S]
+        nr = (C.c_int * len(n_robots))(*[int(v) for v in n_robots])
+        ns = (C.c_int * len(n_samples))(*[int(v) for v in n_samples])
+        for t in (xi_bar, start, goal, start_va, goal_va, xi0, lam0):
+            if t is not None and (t.device.type != "cpu" or t.dtype != torch.float32 or not t.is_contiguous()):
+                raise ValueError("host tensors must be contiguous float32 on the CPU")
+        b = nat.SfBatch()
+        b.n_scenes = len(n_robots)
+        b.n_robots, b.n_samples = nr, ns
+        b.start, b.goal = start.data_ptr(), goal.data_ptr()
+        b.start_va = start_va.data_ptr() if start_va is not None else None
+        b.goal_va = goal_va.data_ptr() if goal_va is not None else None
+        b.xi_bar = xi_bar.data_ptr()
+        nsamp = sum(int(v) for v in n_samples)
+        if out is None:
+            pin = torch.cuda.is_available()
+            out = ProjectResult(xi=torch.empty(xi_bar.shape, pin_memory=pin),
+                                lam=torch.empty(xi_bar.shape, pin_memory=pin),
+                                residual=torch.empty(nsamp, pin_memory=pin))
+        nb = int(self._lib.sf_host_staging_bytes(self._h, C.byref(b), nat.FORM[form], int(K)))
+        if nb == 0:
+            nat.check(self._lib, self._h, 1)
+        stg = self._workspace(nb)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        code = self._lib.sf_project_host(self._h, C.c_void_p(stream.cuda_stream), C.byref(b), int(K),
+                                         nat.FORM[form], _ptr(xi0), _ptr(lam0), _ptr(out.xi),
+                                         _ptr(out.lam), _ptr(out.residual), _ptr(stg), C.c_size_t(nb))
+        nat.check(self._lib, self._h, code)
+        return out
+
+    def launch_count(self) -> int:
+        return int(self._lib.sf_launch_count(self._h))
+
+    def sync_status(self, stream=None):
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        nat.check(self._lib, self._h, self._lib.sf_sync_status(self._h, C.c_void_p(stream.cuda_stream)))
