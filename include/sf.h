@@ -167,6 +167,36 @@ sf_status sf_project_host(sf_handle *h, void *stream, const sf_batch *batch, int
  * Lets a caller count the library's launches inside a timed region. */
 unsigned long long sf_launch_count(const sf_handle *h);
 
+/* Plain form without any device allocation. The paper has no counterpart to
+ * this entry point; it exists for callers that cannot allocate device
+ * memory at call time, for example a host framework that owns every device
+ * allocation and forbids its plug-ins to call cudaMalloc, or a control loop
+ * that may not make calls whose latency is unbounded or that can
+ * synchronise the device.
+ *
+ * It runs the same kernels as sf_project(..., SF_FORM_PLAIN, ...), but their
+ * scratch (the time-domain arrays) lives in one buffer built into the
+ * library: a static device array of SF_NOALLOC_SCRATCH_BYTES (32 MiB) that
+ * every GPU which loads the library holds until the process exits. The
+ * caller still passes all inputs and outputs (device memory, as in
+ * sf_project). A batch whose largest scene needs more scratch than the
+ * buffer holds is rejected with SF_ERR_INVALID_ARG before any launch (need:
+ * about 4 * S * N * dim * (6 T + 2 * nvar) bytes for a scene of S samples).
+ * The call itself allocates nothing: no cudaMalloc, no cudaFree.
+ *
+ * The first call on a device looks up the device address of the buffer
+ * (cudaGetSymbolAddress with that device current); make that first call
+ * before capturing the stream into a graph. All calls share the one buffer
+ * and it keeps the last call's contents; every kernel writes each scratch
+ * element before reading it, so nothing has to be cleared between calls.
+ * Two calls whose work overlaps on the GPU (different streams, or different
+ * handles on the same device) race on the buffer and give wrong results:
+ * serialise them. residual_hist may be NULL. */
+#define SF_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+sf_status sf_project_plain_noalloc(sf_handle *h, void *stream, const sf_batch *batch, int K,
+                                   const float *xi0, const float *lambda0, float *xi_out,
+                                   float *lambda_out, float *residual_out, float *residual_hist);
+
 /* Synchronises `stream` and returns any device-side error latched by earlier
  * calls on the handle (SF_ERR_TIMEOUT, SF_ERR_NONFINITE), clearing it. */
 sf_status sf_sync_status(sf_handle *h, void *stream);

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -419,6 +420,57 @@ sf_status sf_project_host(sf_handle* h, void* stream, const sf_batch* b, int K, 
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(h, e, "device-to-host copy");
   return SF_OK;
+}
+
+// ---- plain form on a built-in scratch buffer (no device allocation) -------
+//
+// For callers that may not allocate device memory when they call in: the
+// time-domain arrays of the plain form live in this static device array
+// instead of a caller-provided workspace. In host code the name below is a
+// host-side stand-in, not a device address; the device address is looked up
+// once per device with cudaGetSymbolAddress and then passed to the kernels.
+namespace {
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SF_NOALLOC_SCRATCH_BYTES];
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the buffer on h->device (the caller has made that device
+// current). Looked up on the first call per device.
+sf_status noalloc_scratch_address(sf_handle* h, void** out) {
+  if (h->device < 0 || h->device >= kMaxDevices) return fail(h, SF_ERR_UNSUPPORTED, "device index too large");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[h->device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(h, e, "device address of the built-in scratch buffer");
+    g_noalloc_addr[h->device] = p;
+  }
+  *out = g_noalloc_addr[h->device];
+  return SF_OK;
+}
+}  // namespace
+
+sf_status sf_project_plain_noalloc(sf_handle* h, void* stream, const sf_batch* b, int K, const float* xi0,
+                                   const float* lam0, float* xi_out, float* lam_out, float* resid_out,
+                                   float* resid_hist) {
+  if (!h) return SF_ERR_INVALID_ARG;
+  long long R = 0, S = 0;
+  sf_status s = check_batch(h, b, &R, &S);
+  if (s != SF_OK) return s;
+  if (K < 1) return fail(h, SF_ERR_INVALID_ARG, "K must be >= 1");
+  const size_t need = sf_workspace_bytes(h, b, SF_FORM_PLAIN, K);
+  if (need > (size_t)SF_NOALLOC_SCRATCH_BYTES)
+    return fail(h, SF_ERR_INVALID_ARG,
+                "batch needs " + std::to_string(need) + " bytes of plain-form scratch; the built-in buffer of "
+                "sf_project_plain_noalloc holds " + std::to_string((size_t)SF_NOALLOC_SCRATCH_BYTES) +
+                " bytes (split the batch into smaller scenes or sample ranges)");
+  DeviceGuard g(h->device);
+  void* scratch = nullptr;
+  s = noalloc_scratch_address(h, &scratch);
+  if (s != SF_OK) return s;
+  return sf_project(h, stream, b, K, SF_FORM_PLAIN, xi0, lam0, xi_out, lam_out, resid_out, resid_hist, scratch,
+                    (size_t)SF_NOALLOC_SCRATCH_BYTES, nullptr);
 }
 
 sf_status sf_sync_status(sf_handle* h, void* stream) {
