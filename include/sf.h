@@ -167,6 +167,16 @@ sf_status sf_project_host(sf_handle *h, void *stream, const sf_batch *batch, int
  * Lets a caller count the library's launches inside a timed region. */
 unsigned long long sf_launch_count(const sf_handle *h);
 
+/* Launch shape of the fused form: samples per CTA (G), warps per CTA, time
+ * steps per chunk (tc). Values <= 0 leave that choice to the library's cost
+ * model. Applies to later sf_project calls on the handle; a shape that does
+ * not fit in shared memory makes them fail with SF_ERR_UNSUPPORTED. */
+sf_status sf_set_launch_shape(sf_handle *h, int samples_per_cta, int warps, int time_chunk);
+
+/* Shape of the last fused launch of the handle: out[0..3] = G, warps, tc and
+ * the number of time ranges of the contraction phase. */
+sf_status sf_get_launch_shape(const sf_handle *h, int *out4);
+
 /* Plain form without any device allocation. The paper has no counterpart to
  * this entry point; it exists for callers that cannot allocate device
  * memory at call time, for example a host framework that owns every device

@@ -22,7 +22,8 @@ FORM = {"fused": 0, "plain": 1}
 # every function include/sf.h declares
 EXPORTS = ("sf_create", "sf_destroy", "sf_last_error", "sf_workspace_bytes", "sf_checkpoint_bytes",
            "sf_project", "sf_host_staging_bytes", "sf_project_host", "sf_launch_count",
-           "sf_project_plain_noalloc", "sf_sync_status")
+           "sf_project_plain_noalloc", "sf_set_launch_shape", "sf_get_launch_shape",
+           "sf_sync_status")
 
 
 class SfProblem(C.Structure):
@@ -88,6 +89,10 @@ def load(path: str = LIB_PATH):
         lib.sf_project_plain_noalloc.argtypes = [vp, vp, C.POINTER(SfBatch), C.c_int, vp, vp, vp, vp,
                                                  vp, vp]
         lib.sf_project_plain_noalloc.restype = C.c_int
+        lib.sf_set_launch_shape.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+        lib.sf_set_launch_shape.restype = C.c_int
+        lib.sf_get_launch_shape.argtypes = [vp, C.POINTER(C.c_int)]
+        lib.sf_get_launch_shape.restype = C.c_int
         lib.sf_sync_status.argtypes = [vp, vp]
         lib.sf_sync_status.restype = C.c_int
         _lib = lib

@@ -20,6 +20,8 @@ struct sf_handle {
   float* ops = nullptr;     // [max_robots + 1][OPS_STRIDE]
   int* status = nullptr;    // device status word
   unsigned long long launches = 0;
+  int force_G = 0, force_warps = 0, force_tc = 0;  // launch-shape overrides (tuning)
+  int last_plan[4] = {0, 0, 0, 0};                 // G, warps, tc, nq of the last fused launch
   std::string err;
 };
 
@@ -264,20 +266,18 @@ sf_status sf_project(sf_handle* h, void* stream, const sf_batch* b, int K, int f
       coff += (long long)Ss * dim * N * NV;
     }
   }
-  const int maxw = fused_max_warps();
-  const int TB = (T + 31) / 32;
   for (int bk = 0; bk < 3; ++bk) {
     const int nmax = 8 << bk;
     for (size_t first = 0; first < items[bk].size(); first += MAX_SCENES_PER_LAUNCH) {
       const size_t last = std::min(items[bk].size(), first + (size_t)MAX_SCENES_PER_LAUNCH);
-      long long tot = 0;
-      for (size_t q = first; q < last; ++q) tot += b->n_samples[items[bk][q].scene];
-      // samples per CTA: spread the group over one wave of CTAs, bounded by shared memory
-      int gcap = 1;
-      while (gcap < 64 && fused_smem_bytes(dim, nmax, T, gcap + 1) <= h->max_smem_optin) ++gcap;
-      if (fused_smem_bytes(dim, nmax, T, 1) > h->max_smem_optin)
-        return fail(h, SF_ERR_UNSUPPORTED, "T too large for the fused form");
-      int G = (int)std::min<long long>(gcap, std::max<long long>(1, (tot + h->num_sms - 1) / h->num_sms));
+      std::vector<int> nr, ns;
+      for (size_t q = first; q < last; ++q) {
+        nr.push_back(b->n_robots[items[bk][q].scene]);
+        ns.push_back(b->n_samples[items[bk][q].scene]);
+      }
+      const FusedPlan plan = plan_fused(dim, nmax, T, nr.data(), ns.data(), (int)nr.size(), h->num_sms,
+                                        h->max_smem_optin, h->force_G, h->force_warps, h->force_tc);
+      if (plan.G == 0) return fail(h, SF_ERR_UNSUPPORTED, "no fused launch shape fits in shared memory");
       FusedArgs a;
       std::memset(&a, 0, sizeof(a));
       a.pc = pc;
@@ -296,6 +296,8 @@ sf_status sf_project(sf_handle* h, void* stream, const sf_batch* b, int K, int f
       a.hist = resid_hist;
       a.total_samples = (int)S;
       a.status = h->status;
+      a.tc = plan.tc;
+      a.nq = plan.nq;
       int ctas = 0, gmax = 1;
       a.n_scenes = (int)(last - first);
       for (size_t q = first; q < last; ++q) {
@@ -303,7 +305,7 @@ sf_status sf_project(sf_handle* h, void* stream, const sf_batch* b, int K, int f
         SceneDesc& d = a.sc[q - first];
         d.N = b->n_robots[it.scene];
         d.S = b->n_samples[it.scene];
-        d.G = std::min(G, d.S);
+        d.G = std::min(plan.G, d.S);
         d.cta_begin = ctas;
         d.robot_off = (int)it.roff;
         d.sample_off = (int)it.soff;
@@ -315,11 +317,14 @@ sf_status sf_project(sf_handle* h, void* stream, const sf_batch* b, int K, int f
       l.nmax = nmax;
       l.gmax = gmax;
       l.n_ctas = ctas;
-      const int units = gmax * TB;
-      const int rounds = (units + maxw - 1) / maxw;
-      l.warps = std::max(1, (units + rounds - 1) / rounds);
-      if (nmax == 32) l.warps = std::min(l.warps, 12);
-      l.smem = fused_smem_bytes(dim, nmax, T, gmax);
+      l.warps = plan.warps;
+      l.tc = plan.tc;
+      l.nq = plan.nq;
+      l.smem = fused_smem_bytes(dim, nmax, T, gmax, plan.tc, plan.nq);
+      h->last_plan[0] = plan.G;
+      h->last_plan[1] = plan.warps;
+      h->last_plan[2] = plan.tc;
+      h->last_plan[3] = plan.nq;
       cudaError_t e = launch_fused(a, l, st);
       if (e != cudaSuccess) return cuda_fail(h, e, "fused form launch");
       h->launches += 1;
@@ -329,6 +334,21 @@ sf_status sf_project(sf_handle* h, void* stream, const sf_batch* b, int K, int f
 }
 
 unsigned long long sf_launch_count(const sf_handle* h) { return h ? h->launches : 0ULL; }
+
+sf_status sf_set_launch_shape(sf_handle* h, int G, int warps, int tc) {
+  if (!h) return SF_ERR_INVALID_ARG;
+  if (G > 64 || warps > 32 || tc > SF_MAX_T) return fail(h, SF_ERR_INVALID_ARG, "launch shape out of range");
+  h->force_G = G > 0 ? G : 0;
+  h->force_warps = warps > 0 ? warps : 0;
+  h->force_tc = tc > 0 ? tc : 0;
+  return SF_OK;
+}
+
+sf_status sf_get_launch_shape(const sf_handle* h, int* out4) {
+  if (!h || !out4) return SF_ERR_INVALID_ARG;
+  for (int q = 0; q < 4; ++q) out4[q] = h->last_plan[q];
+  return SF_OK;
+}
 
 namespace {
 struct HostPlan {

@@ -1,7 +1,10 @@
 // Dispatch of the fused forward kernel over (dim, robot-count bucket); the
 // kernel template lives in sf_fused_kernel.cuh and each instantiation is
 // compiled in its own translation unit (sf_fused_d*_n*.cu).
-#include "sf_internal.cuh"
+#include <algorithm>
+#include <cmath>
+
+#include "sf_fused_kernel.cuh"
 
 namespace sf {
 
@@ -9,14 +12,60 @@ namespace sf {
 SF_DECL(2, 8) SF_DECL(2, 16) SF_DECL(2, 32) SF_DECL(3, 8) SF_DECL(3, 16) SF_DECL(3, 32)
 #undef SF_DECL
 
-int fused_max_warps() { return 14; }
+int fused_max_warps(int nmax) { return nmax == 32 ? 8 : 12; }
 
-size_t fused_smem_bytes(int dim, int nmax, int T, int gmax) {
-  const int RS = dim * NP;
-  const int TB = (T + 31) / 32;
-  const int SB = (4 + TB) * nmax * RS + 2 * dim * NP + ((TB + 3) / 4) * 4;
-  const int head = 4 * NV * NP + nmax * RS;
-  return sizeof(float) * ((size_t)head + (size_t)gmax * SB);
+size_t fused_smem_bytes(int dim, int nmax, int T, int gmax, int tc, int nq) {
+  const fused_impl::Lay L(dim, nmax, T, tc, nq);
+  return sizeof(float) * ((size_t)L.head + (size_t)gmax * L.SB);
+}
+
+// Cost model: instruction slots of the pair phase (per (sample, t) lane) and
+// of the contraction phase (per (sample, robot, t)), padded to whole rounds
+// of the CTA's threads, over an issue rate that saturates at 4 warp
+// instructions per cycle; plus a charge per block-wide barrier. The CTA count
+// over the SM count gives the number of waves.
+FusedPlan plan_fused(int dim, int nmax, int T, const int* nr, const int* ns, int n_scenes, int num_sms,
+                     size_t smem_cap, int force_G, int force_warps, int force_tc) {
+  FusedPlan best;
+  best.G = 0;
+  best.cost = INFINITY;
+  long long tot = 0;
+  int Nbig = 1;
+  for (int q = 0; q < n_scenes; ++q) {
+    tot += ns[q];
+    Nbig = std::max(Nbig, nr[q]);
+  }
+  const int maxw = fused_max_warps(nmax);
+  const double cA = 0.5 * Nbig * (Nbig - 1) * 14.0 + 45.0 * Nbig;
+  const double cB = 200.0;
+  const int gmax_try = (int)std::min<long long>(64, std::max<long long>(1, tot));
+  for (int G = 1; G <= gmax_try; ++G) {
+    if (force_G > 0 && G != force_G) continue;
+    long long ctas = 0;
+    for (int q = 0; q < n_scenes; ++q) ctas += (ns[q] + std::min(G, std::max(ns[q], 1)) - 1) / std::min(G, std::max(ns[q], 1));
+    const double waves = std::ceil((double)ctas / num_sms);
+    for (int nch = 1; nch <= 6; ++nch) {
+      const int tc = (T + nch - 1) / nch;
+      if (force_tc > 0 && tc != force_tc) continue;
+      for (int w = 4; w <= maxw; ++w) {
+        if (force_warps > 0 && w != force_warps) continue;
+        const int nthr = 32 * w;
+        const int nq = std::max(1, std::min(tc, nthr / std::max(1, G * Nbig)));
+        const size_t smem = fused_smem_bytes(dim, nmax, T, G, tc, nq);
+        if (smem > smem_cap) continue;
+        const int real_nch = (T + tc - 1) / tc;
+        const double rate = std::min(4.0, w / 2.0);
+        const double a_rounds = std::ceil((double)G * tc / nthr);
+        const double b_rounds = std::ceil((double)nq * G * Nbig / nthr);
+        const double tq = std::ceil((double)tc / nq);
+        const double per_iter = real_nch * (a_rounds * w * cA + b_rounds * w * tq * cB) / rate +
+                                (2.0 * real_nch + 2.0) * 400.0 + 24.0 * G * Nbig * dim * 4.0 / rate;
+        const double cost = waves * per_iter;
+        if (cost < best.cost) best = FusedPlan{G, w, tc, nq, smem, cost};
+      }
+    }
+  }
+  return best;
 }
 
 cudaError_t launch_fused(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st) {

@@ -3,6 +3,6 @@
 
 namespace sf {
 cudaError_t launch_fused_d2_n16(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st) {
-  return fused_impl::launch_t<2, 16, 448>(a, l, st);
+  return fused_impl::launch_t<2, 16, 384>(a, l, st);
 }
 }  // namespace sf

@@ -3,6 +3,6 @@
 
 namespace sf {
 cudaError_t launch_fused_d2_n8(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st) {
-  return fused_impl::launch_t<2, 8, 448>(a, l, st);
+  return fused_impl::launch_t<2, 8, 384>(a, l, st);
 }
 }  // namespace sf

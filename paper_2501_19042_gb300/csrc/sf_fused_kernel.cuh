@@ -1,24 +1,29 @@
 // Fused forward of the safety filter: one launch runs all K iterations of
 // f_FP (Appendix, AM steps) for many samples, with every sample's
-// coefficient-space state (xi, lambda, xi_bar) resident in shared memory.
+// coefficient-space state (xi, lambda) resident in shared memory.
 //
-// CTA = G samples of one scene. Per iteration:
-//  * time phase, one warp per (sample, block of 32 time steps), lane = t:
-//      positions p_i(t) = P[t] c_i for all robots (recomputed from the
-//      resident coefficients, never stored), every pair (i < j) projected by
-//      the alpha / beta / d closed forms, q = e - delta accumulated per robot
-//      in registers (E_i += q, E_j -= q, blocks of 8 robots); then per robot
-//      the velocity / acceleration ball projections and the transposed
-//      contraction  g_i = sum_t P[t] E_i(t) + Pd[t] qv_i(t) + Pdd[t] qa_i(t)
-//      (F^T of the residual, Eq. lambda_step), reduced over the 32 lanes by a
-//      shuffle reduce-scatter and written per time block;
-//  * solve phase: lambda' = lambda + rho g  (lambda step, minus-sign reading),
-//      r = rho g + lambda' + xi_bar, robot means, and the xi step
-//      c_i' = W1 c_i + S1 r_i + DW cbar + DS rbar + beta_i with the
-//      pre-stored operators of the KKT system.
-// After the last iteration one more time pass evaluates
+// CTA = G samples of one scene. The time axis is processed in chunks of TC
+// steps. Per iteration and chunk:
+//  * pair phase — one thread per (sample, t), the (sample, t) pairs of the
+//    chunk laid out flat over the CTA's lanes: positions p_i(t) = P[t] c_i of
+//    all robots, then every pair (i < j) by the alpha / beta / d closed forms,
+//    q = e - delta accumulated per robot in registers (E_i += q, E_j -= q).
+//    A pair that is inactive on all 32 lanes of a warp is skipped after its
+//    distance test. E_i(t) goes to a shared-memory chunk buffer.
+//  * contraction phase — one thread per (sample, robot, range of t): the
+//    robot's coefficients in registers, velocity / acceleration and their
+//    ball projections, and the transposed contraction
+//      g_i += P[t] E_i(t) + Pd[t] qv_i(t) + Pdd[t] qa_i(t)
+//    (F^T of the residual, Eq. lambda_step) kept in registers and added to a
+//    per-range partial.
+// Then the solve phase: lambda' = lambda + rho g (minus-sign reading),
+// r = rho g + lambda' + xi_bar, robot means, and the xi step
+//   c_i' = W1 c_i + S1 r_i + DW cbar + DS rbar + beta_i
+// with the operators pre-stored from the KKT system.
+// After the last iteration one more pass evaluates
 //   ||r_p|| = ||F xi^K - e(xi^{K-1})||  (Eq. primal_residual)
-// as  F(xi^K - xi^{K-1}) - q(xi^{K-1})  per row.
+// row by row as F(xi^K - xi^{K-1}) - q(xi^{K-1}).
+// Every reduction is done in a fixed order: results are bit-reproducible.
 #pragma once
 #include "sf_internal.cuh"
 
@@ -27,42 +32,42 @@ namespace fused_impl {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-template <int DIM, int NMAX>
-struct Layout {
-  static constexpr int RS = DIM * NP;  // floats per robot row [ax][12]
-  int TB;                              // time blocks of 32
-  int SB;                              // floats per sample block
-  __host__ __device__ Layout(int T) {
-    TB = (T + 31) / 32;
-    SB = (4 + TB) * NMAX * RS + 2 * DIM * NP + ((TB + 3) / 4) * 4;
+// Shared-memory layout (floats). Head: basis [T][36], operators, beta.
+// Per sample: C, LAM [NMAX][DIM][12]; PG [NQ][NMAX][DIM][12] (partials of
+// F^T q, later r); MC, MR [DIM][12] (robot means); EB [TC][EP] (E of the
+// chunk, EP = NMAX*DIM + 1; also holds xi^{K-1} after the last iteration);
+// RS2 [T] (pair residual per t); RSB [NQ][NMAX] (ball residual partials).
+struct Lay {
+  int RS, EP, TC, NQ, T, nmax, dim;
+  int C, LAM, PG, MC, MR, EB, RS2, RSB, SB;
+  int head;
+  __host__ __device__ Lay(int dim_, int nmax_, int T_, int TC_, int NQ_) {
+    dim = dim_; nmax = nmax_; T = T_; TC = TC_; NQ = NQ_;
+    RS = dim * NP;
+    EP = nmax * dim + 1;
+    C = 0;
+    LAM = C + nmax * RS;
+    PG = LAM + nmax * RS;
+    MC = PG + NQ * nmax * RS;
+    MR = MC + dim * NP;
+    EB = MR + dim * NP;
+    int eb = TC * EP;
+    if (eb < nmax * RS) eb = nmax * RS;
+    RS2 = EB + ((eb + 3) / 4) * 4;
+    RSB = RS2 + T;
+    SB = ((RSB + NQ * nmax + 3) / 4) * 4;
+    head = T * BASIS_ROW + 4 * NV * NP + nmax * RS;
   }
-  // offsets inside a sample block
-  __host__ __device__ int C() const { return 0; }
-  __host__ __device__ int LAM() const { return NMAX * RS; }
-  __host__ __device__ int XIB() const { return 2 * NMAX * RS; }
-  __host__ __device__ int CPREV() const { return 3 * NMAX * RS; }
-  __host__ __device__ int GP(int tb) const { return (4 + tb) * NMAX * RS; }
-  __host__ __device__ int MC() const { return (4 + TB) * NMAX * RS; }
-  __host__ __device__ int MR() const { return (4 + TB) * NMAX * RS + DIM * NP; }
-  __host__ __device__ int RESP() const { return (4 + TB) * NMAX * RS + 2 * DIM * NP; }
-  static constexpr int head_floats() { return 4 * NV * NP + NMAX * RS; }  // OPS + BETA
 };
 
-__device__ __forceinline__ void load_row(const float4* __restrict__ basis, int t, int which, bool valid,
-                                         float (&r)[NV]) {
-  float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a, c = a;
-  if (valid) {
-    const float4* p = basis + (size_t)t * 9 + which * 3;
-    a = __ldg(p);
-    b = __ldg(p + 1);
-    c = __ldg(p + 2);
-  }
+__device__ __forceinline__ void row_from(const float* __restrict__ src, float (&r)[NV]) {
+  const float4* p = reinterpret_cast<const float4*>(src);
+  const float4 a = p[0], b = p[1], c = p[2];
   r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w;
   r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
   r[8] = c.x; r[9] = c.y; r[10] = c.z;
 }
 
-// dot of a basis row with one 12-float coefficient row in shared memory
 __device__ __forceinline__ float dot_row(const float (&r)[NV], const float* crow) {
   const float4* c4 = reinterpret_cast<const float4*>(crow);
   const float4 a = c4[0], b = c4[1], c = c4[2];
@@ -74,178 +79,238 @@ __device__ __forceinline__ float dot_row(const float (&r)[NV], const float* crow
   return s;
 }
 
+__device__ __forceinline__ float dot_reg(const float (&r)[NV], const float (&c)[NV]) {
+  float s = r[0] * c[0];
+#pragma unroll
+  for (int k = 1; k < NV; ++k) s = fmaf(r[k], c[k], s);
+  return s;
+}
+
 template <int DIM>
 __device__ __forceinline__ void state(const float (&r)[NV], const float* Crow, float (&p)[DIM]) {
 #pragma unroll
   for (int x = 0; x < DIM; ++x) p[x] = dot_row(r, Crow + x * NP);
 }
 
+// One pair row (i < j): q = e(delta) - delta with delta = p_i - p_j, added to
+// E_i and subtracted from E_j. The scaled distance s2 >= 1 means the row is
+// inactive (e = delta); a warp skips the rest when no lane is active.
 template <int DIM>
-__device__ __forceinline__ void state_diff(const float (&r)[NV], const float* Crow, const float* Prow,
-                                           float (&p)[DIM]) {
+__device__ __forceinline__ void pair_update(const float (&pi)[DIM], const float (&pj)[DIM], float (&Ei)[DIM],
+                                            float (&Ej)[DIM], bool valid, const ProblemConsts& pc,
+                                            float& res2) {
+  float d[DIM];
 #pragma unroll
-  for (int x = 0; x < DIM; ++x) p[x] = dot_row(r, Crow + x * NP) - dot_row(r, Prow + x * NP);
-}
-
-// Reduce-scatter over the 32 lanes: afterwards v[0] on lane l holds the sum
-// over all lanes of the input v[l].
-__device__ __forceinline__ void reduce_scatter32(float (&v)[32], int lane) {
+  for (int x = 0; x < DIM; ++x) d[x] = pi[x] - pj[x];
+  float s2;
+  if (DIM == 3)
+    s2 = fmaf(d[2] * d[2], pc.inv_b2, (d[0] * d[0] + d[1] * d[1]) * pc.inv_a2);
+  else
+    s2 = (d[0] * d[0] + d[1] * d[1]) * pc.inv_a2;
+  s2 = valid ? s2 : 2.0f;
+  if (__any_sync(FULL, s2 < 1.0f)) {
+    const bool zero = (s2 == 0.0f);
+    float f = fmaxf(rsqrtf(s2) - 1.0f, 0.0f);
+    f = zero ? 0.0f : f;
+    float q[DIM];
 #pragma unroll
-  for (int n = 16; n >= 1; n >>= 1) {
-    const bool up = (lane & n) != 0;
+    for (int x = 0; x < DIM; ++x) q[x] = f * d[x];
+    if (zero) q[DIM == 3 ? 2 : 0] = pc.tie;
 #pragma unroll
-    for (int j = 0; j < n; ++j) {
-      const float send = up ? v[j] : v[j + n];
-      const float keep = up ? v[j + n] : v[j];
-      v[j] = keep + __shfl_xor_sync(FULL, send, n);
+    for (int x = 0; x < DIM; ++x) {
+      Ei[x] += q[x];
+      Ej[x] -= q[x];
+      res2 = fmaf(q[x], q[x], res2);
     }
   }
 }
 
-__device__ __forceinline__ float warp_sum(float x) {
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
-  return x;
-}
-
-// One (sample, time block) unit of an iteration. Writes this block's part of
-// g = F^T (e - F xi) to GP ([NMAX][DIM][NP]) and its squared projection
-// residual to *resp.
+// Pair phase of one chunk [t0, t0 + TCc).
 template <int DIM, int NMAX>
-__device__ void time_unit(const float* __restrict__ C, const float4* __restrict__ basis, int T, int t,
-                          int N, const ProblemConsts& pc, float* __restrict__ GP, float* resp, int lane) {
+__device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G, int N, int t0, int TCc,
+                           const ProblemConsts& pc, bool want_res, int warp, int nwarps, int lane) {
   constexpr int RS = DIM * NP;
-  const bool valid = t < T;
-  float Pr[NV];
-  load_row(basis, t, 0, valid, Pr);
-  float E[NMAX][DIM];
+  const int nA = G * TCc;
+  for (int base = warp * 32; base < nA; base += nwarps * 32) {
+    const int u = base + lane;
+    const bool valid = u < nA;
+    const int s = valid ? u / TCc : 0;
+    const int tl = valid ? u - s * TCc : 0;
+    const int t = t0 + tl;
+    float* blk = SAMP + (size_t)s * L.SB;
+    const float* Cs = blk + L.C;
+    float Pr[NV];
+    row_from(BASIS + (size_t)t * BASIS_ROW, Pr);
+    float E[NMAX][DIM];
 #pragma unroll
-  for (int i = 0; i < NMAX; ++i)
+    for (int i = 0; i < NMAX; ++i)
 #pragma unroll
-    for (int x = 0; x < DIM; ++x) E[i][x] = 0.0f;
-  float res2 = 0.0f;
-
-  // all pairs (i < j), robots in blocks of 8: positions of the block in
-  // registers, the later robots one at a time
+      for (int x = 0; x < DIM; ++x) E[i][x] = 0.0f;
+    float res2 = 0.0f;
+    if (NMAX <= 16) {
+      float p[NMAX][DIM];
 #pragma unroll
-  for (int I0 = 0; I0 < NMAX; I0 += 8) {
-    if (I0 < N) {
-      float pI[8][DIM];
+      for (int i = 0; i < NMAX; ++i) {
+        if (i < N) state<DIM>(Pr, Cs + i * RS, p[i]);
+        else
 #pragma unroll
-      for (int a = 0; a < 8; ++a) state<DIM>(Pr, C + (I0 + a) * RS, pI[a]);
-#pragma unroll
-      for (int a = 0; a < 8; ++a)
-#pragma unroll
-        for (int b = a + 1; b < 8; ++b) {
-          if (I0 + b < N) {
-            float q[DIM];
-            pair_residual<DIM>(pI[a], pI[b], q, pc, res2);
-#pragma unroll
-            for (int x = 0; x < DIM; ++x) { E[I0 + a][x] += q[x]; E[I0 + b][x] -= q[x]; }
-          }
-        }
-#pragma unroll
-      for (int j = I0 + 8; j < NMAX; ++j) {
-        if (j < N) {
-          float pj[DIM];
-          state<DIM>(Pr, C + j * RS, pj);
-#pragma unroll
-          for (int a = 0; a < 8; ++a) {
-            float q[DIM];
-            pair_residual<DIM>(pI[a], pj, q, pc, res2);
-#pragma unroll
-            for (int x = 0; x < DIM; ++x) { E[I0 + a][x] += q[x]; E[j][x] -= q[x]; }
-          }
-        }
-      }
-    }
-  }
-
-  float Pd[NV], Pdd[NV];
-  load_row(basis, t, 1, valid, Pd);
-  load_row(basis, t, 2, valid, Pdd);
-#pragma unroll
-  for (int i = 0; i < NMAX; ++i) {
-    if (i < N) {
-      float qv[DIM], qa[DIM];
-#pragma unroll
-      for (int x = 0; x < DIM; ++x) { qv[x] = 0.0f; qa[x] = 0.0f; }
-      if (pc.use_v) {
-        float v[DIM];
-        state<DIM>(Pd, C + i * RS, v);
-        ball_residual<DIM>(v, pc.v_max, qv, res2);
-      }
-      if (pc.use_a) {
-        float a[DIM];
-        state<DIM>(Pdd, C + i * RS, a);
-        ball_residual<DIM>(a, pc.a_max, qa, res2);
-      }
-      float h[32];
-      float hlast = 0.0f;
-#pragma unroll
-      for (int x = 0; x < DIM; ++x)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-          const float val = fmaf(Pr[k], E[i][x], fmaf(Pd[k], qv[x], Pdd[k] * qa[x]));
-          const int idx = x * NV + k;
-          if (idx < 32) h[idx] = val; else hlast = val;
-        }
-#pragma unroll
-      for (int idx = DIM * NV; idx < 32; ++idx) h[idx] = 0.0f;
-      reduce_scatter32(h, lane);
-      float* g = GP + i * RS;
-      if (lane < DIM * NV && lane < 32) g[(lane / NV) * NP + lane % NV] = h[0];
-      if (DIM * NV > 32) {
-        hlast = warp_sum(hlast);
-        if (lane == 0) g[(32 / NV) * NP + 32 % NV] = hlast;
-      }
-    }
-  }
-  res2 = valid ? res2 : 0.0f;
-  res2 = warp_sum(res2);
-  if (lane == 0) *resp = res2;
-}
-
-// Residual pass after the last iteration: ||F xi^K - e(xi^{K-1})||^2 of this
-// unit, row by row as (F (xi^K - xi^{K-1}))_row - q_row(xi^{K-1}).
-template <int DIM, int NMAX>
-__device__ void residual_unit(const float* __restrict__ C, const float* __restrict__ Cp,
-                              const float4* __restrict__ basis, int T, int t, int N,
-                              const ProblemConsts& pc, float* resp) {
-  constexpr int RS = DIM * NP;
-  const bool valid = t < T;
-  float Pr[NV];
-  load_row(basis, t, 0, valid, Pr);
-  float r2 = 0.0f, dummy = 0.0f;
-#pragma unroll
-  for (int I0 = 0; I0 < NMAX; I0 += 8) {
-    if (I0 < N) {
-      float pI[8][DIM], dI[8][DIM];
-#pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        state<DIM>(Pr, Cp + (I0 + a) * RS, pI[a]);
-        state_diff<DIM>(Pr, C + (I0 + a) * RS, Cp + (I0 + a) * RS, dI[a]);
+          for (int x = 0; x < DIM; ++x) p[i][x] = 0.0f;
       }
 #pragma unroll
-      for (int a = 0; a < 8; ++a)
+      for (int i = 0; i < NMAX; ++i)
 #pragma unroll
-        for (int b = a + 1; b < 8; ++b) {
-          if (I0 + b < N) {
-            float q[DIM];
-            pair_residual<DIM>(pI[a], pI[b], q, pc, dummy);
+        for (int j = 0; j < NMAX; ++j)
+          if (j > i && j < N) pair_update<DIM>(p[i], p[j], E[i], E[j], valid, pc, res2);
+    } else {
+      // robots in blocks of 8: the block's positions in registers, later
+      // robots recomputed one at a time
 #pragma unroll
-            for (int x = 0; x < DIM; ++x) {
-              const float r = (dI[a][x] - dI[b][x]) - q[x];
-              r2 = fmaf(r, r, r2);
+      for (int I0 = 0; I0 < NMAX; I0 += 8) {
+        if (I0 < N) {
+          float pI[8][DIM];
+#pragma unroll
+          for (int a = 0; a < 8; ++a) state<DIM>(Pr, Cs + (I0 + a) * RS, pI[a]);
+#pragma unroll
+          for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 8; ++b)
+              if (b > a && I0 + b < N) pair_update<DIM>(pI[a], pI[b], E[I0 + a], E[I0 + b], valid, pc, res2);
+#pragma unroll
+          for (int j = 0; j < NMAX; ++j) {
+            if (j >= I0 + 8 && j < N) {
+              float pj[DIM];
+              state<DIM>(Pr, Cs + j * RS, pj);
+#pragma unroll
+              for (int a = 0; a < 8; ++a) pair_update<DIM>(pI[a], pj, E[I0 + a], E[j], valid, pc, res2);
             }
           }
         }
+      }
+    }
+    if (valid) {
+      float* eb = blk + L.EB + tl * L.EP;
 #pragma unroll
-      for (int j = I0 + 8; j < NMAX; ++j) {
-        if (j < N) {
-          float pj[DIM], dj[DIM];
+      for (int i = 0; i < NMAX; ++i)
+        if (i < N)
+#pragma unroll
+          for (int x = 0; x < DIM; ++x) eb[i * DIM + x] = E[i][x];
+      if (want_res) blk[L.RS2 + t] = res2;
+    }
+  }
+}
+
+// Contraction phase of one chunk: F^T of the residual per (sample, robot).
+template <int DIM>
+__device__ void contract_phase(float* SAMP, const Lay& L, const float* BASIS, int G, int N, int t0, int TCc,
+                               bool first_chunk, const ProblemConsts& pc, bool want_res, int tid, int nthr) {
+  const int RS = DIM * NP;
+  const int NQ = L.NQ;
+  const int nB = NQ * G * N;
+  const int TQ = (TCc + NQ - 1) / NQ;
+  for (int u = tid; u < nB; u += nthr) {
+    const int i = u % N;
+    const int s = (u / N) % G;
+    const int tq = u / (N * G);
+    const int ta = tq * TQ;
+    const int tb = min(ta + TQ, TCc);
+    float* blk = SAMP + (size_t)s * L.SB;
+    float c[DIM][NV], g[DIM][NV];
+#pragma unroll
+    for (int x = 0; x < DIM; ++x) {
+      row_from(blk + L.C + i * RS + x * NP, c[x]);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) g[x][k] = 0.0f;
+    }
+    float rb = 0.0f;
+    for (int tl = ta; tl < tb; ++tl) {
+      const float* brow = BASIS + (size_t)(t0 + tl) * BASIS_ROW;
+      float P[NV], Pd[NV], Pdd[NV];
+      row_from(brow, P);
+      row_from(brow + NP, Pd);
+      row_from(brow + 2 * NP, Pdd);
+      const float* eb = blk + L.EB + tl * L.EP + i * DIM;
+      float e[DIM], qv[DIM], qa[DIM];
+#pragma unroll
+      for (int x = 0; x < DIM; ++x) { e[x] = eb[x]; qv[x] = 0.0f; qa[x] = 0.0f; }
+      if (pc.use_v) {
+        float v[DIM];
+#pragma unroll
+        for (int x = 0; x < DIM; ++x) v[x] = dot_reg(Pd, c[x]);
+        ball_residual<DIM>(v, pc.v_max, qv, rb);
+      }
+      if (pc.use_a) {
+        float a[DIM];
+#pragma unroll
+        for (int x = 0; x < DIM; ++x) a[x] = dot_reg(Pdd, c[x]);
+        ball_residual<DIM>(a, pc.a_max, qa, rb);
+      }
+#pragma unroll
+      for (int x = 0; x < DIM; ++x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) g[x][k] = fmaf(P[k], e[x], fmaf(Pd[k], qv[x], fmaf(Pdd[k], qa[x], g[x][k])));
+    }
+    float* pg = blk + L.PG + tq * L.nmax * RS + i * RS;
+#pragma unroll
+    for (int x = 0; x < DIM; ++x)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) pg[x * NP + k] = first_chunk ? g[x][k] : pg[x * NP + k] + g[x][k];
+    if (want_res) {
+      float* r = blk + L.RSB + tq * L.nmax + i;
+      *r = first_chunk ? rb : *r + rb;
+    }
+  }
+}
+
+// Final residual of one (sample, t): ||F xi^K - e(xi^{K-1})||^2 over the rows
+// at t, written to RS2[t]. Cp holds xi^{K-1}, C holds xi^K.
+template <int DIM, int NMAX>
+__device__ void residual_phase(float* SAMP, const Lay& L, const float* BASIS, int G, int N, int T,
+                               const ProblemConsts& pc, int warp, int nwarps, int lane) {
+  constexpr int RS = DIM * NP;
+  const int nA = G * T;
+  for (int base = warp * 32; base < nA; base += nwarps * 32) {
+    const int u = base + lane;
+    const bool valid = u < nA;
+    const int s = valid ? u / T : 0;
+    const int t = valid ? u - s * T : 0;
+    float* blk = SAMP + (size_t)s * L.SB;
+    const float* C = blk + L.C;
+    const float* Cp = blk + L.EB;
+    float Pr[NV];
+    row_from(BASIS + (size_t)t * BASIS_ROW, Pr);
+    float r2 = 0.0f, dummy = 0.0f;
+#pragma unroll
+    for (int I0 = 0; I0 < NMAX; I0 += 8) {
+      if (I0 < N) {
+        float pI[8][DIM], dI[8][DIM];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          state<DIM>(Pr, Cp + (I0 + a) * RS, pI[a]);
+          float pn[DIM];
+          state<DIM>(Pr, C + (I0 + a) * RS, pn);
+#pragma unroll
+          for (int x = 0; x < DIM; ++x) dI[a][x] = pn[x] - pI[a][x];
+        }
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int b = a + 1; b < 8; ++b) {
+            if (I0 + b < N) {
+              float q[DIM];
+              pair_residual<DIM>(pI[a], pI[b], q, pc, dummy);
+#pragma unroll
+              for (int x = 0; x < DIM; ++x) {
+                const float r = (dI[a][x] - dI[b][x]) - q[x];
+                r2 = fmaf(r, r, r2);
+              }
+            }
+          }
+        for (int j = I0 + 8; j < N; ++j) {
+          float pj[DIM], pn[DIM], dj[DIM];
           state<DIM>(Pr, Cp + j * RS, pj);
-          state_diff<DIM>(Pr, C + j * RS, Cp + j * RS, dj);
+          state<DIM>(Pr, C + j * RS, pn);
+#pragma unroll
+          for (int x = 0; x < DIM; ++x) dj[x] = pn[x] - pj[x];
 #pragma unroll
           for (int a = 0; a < 8; ++a) {
             float q[DIM];
@@ -259,34 +324,35 @@ __device__ void residual_unit(const float* __restrict__ C, const float* __restri
         }
       }
     }
-  }
-  float Pd[NV], Pdd[NV];
-  load_row(basis, t, 1, valid, Pd);
-  load_row(basis, t, 2, valid, Pdd);
-#pragma unroll
-  for (int i = 0; i < NMAX; ++i) {
-    if (i < N) {
+    float Pd[NV], Pdd[NV];
+    row_from(BASIS + (size_t)t * BASIS_ROW + NP, Pd);
+    row_from(BASIS + (size_t)t * BASIS_ROW + 2 * NP, Pdd);
+    for (int i = 0; i < N; ++i) {
       if (pc.use_v) {
-        float v[DIM], dv[DIM], q[DIM];
-        state<DIM>(Pd, Cp + i * RS, v);
-        state_diff<DIM>(Pd, C + i * RS, Cp + i * RS, dv);
-        ball_residual<DIM>(v, pc.v_max, q, dummy);
+        float vo[DIM], vn[DIM], q[DIM];
+        state<DIM>(Pd, Cp + i * RS, vo);
+        state<DIM>(Pd, C + i * RS, vn);
+        ball_residual<DIM>(vo, pc.v_max, q, dummy);
 #pragma unroll
-        for (int x = 0; x < DIM; ++x) { const float r = dv[x] - q[x]; r2 = fmaf(r, r, r2); }
+        for (int x = 0; x < DIM; ++x) {
+          const float r = (vn[x] - vo[x]) - q[x];
+          r2 = fmaf(r, r, r2);
+        }
       }
       if (pc.use_a) {
-        float a[DIM], da[DIM], q[DIM];
-        state<DIM>(Pdd, Cp + i * RS, a);
-        state_diff<DIM>(Pdd, C + i * RS, Cp + i * RS, da);
-        ball_residual<DIM>(a, pc.a_max, q, dummy);
+        float ao[DIM], an[DIM], q[DIM];
+        state<DIM>(Pdd, Cp + i * RS, ao);
+        state<DIM>(Pdd, C + i * RS, an);
+        ball_residual<DIM>(ao, pc.a_max, q, dummy);
 #pragma unroll
-        for (int x = 0; x < DIM; ++x) { const float r = da[x] - q[x]; r2 = fmaf(r, r, r2); }
+        for (int x = 0; x < DIM; ++x) {
+          const float r = (an[x] - ao[x]) - q[x];
+          r2 = fmaf(r, r, r2);
+        }
       }
     }
+    if (valid) blk[L.RS2 + t] = r2;
   }
-  r2 = valid ? r2 : 0.0f;
-  r2 = warp_sum(r2);
-  if ((threadIdx.x & 31) == 0) *resp = r2;
 }
 
 template <int DIM, int NMAX, int MAXT>
@@ -296,10 +362,8 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
   float* sm = reinterpret_cast<float*>(smem4);
   const ProblemConsts& pc = A.pc;
   const int T = pc.T;
-  const Layout<DIM, NMAX> L(T);
-  const int TB = L.TB;
+  const Lay L(DIM, NMAX, T, A.tc, A.nq);
 
-  // --- which scene / samples this CTA owns
   int sidx = 0;
   for (int q = 1; q < A.n_scenes; ++q) {
     if (A.sc[q].cta_begin <= (int)blockIdx.x) sidx = q;
@@ -318,21 +382,25 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
 
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
-  float* OPS = sm;
-  float* BETA = sm + 4 * NV * NP;
-  float* SAMP = sm + Layout<DIM, NMAX>::head_floats();
+  float* BASIS = sm;
+  float* OPS = sm + T * BASIS_ROW;
+  float* BETA = OPS + 4 * NV * NP;
+  float* SAMP = sm + L.head;
+  const bool want_res = A.hist != nullptr;
 
-  // --- prologue: operators of this N, beta, per-sample state
+  // ---- prologue: basis, operators of this N, beta, per-sample state
+  {
+    const float4* b4 = A.basis;
+    float4* s4 = reinterpret_cast<float4*>(BASIS);
+    for (int v = tid; v < T * 9; v += nthr) s4[v] = b4[v];
+  }
   const float* gops = A.ops + (size_t)N * OPS_STRIDE;
   for (int v = tid; v < 4 * NV * NP; v += nthr) OPS[v] = gops[v];
   for (int v = tid; v < NMAX * RS; v += nthr) {
     const int i = v / RS, x = (v / NP) % DIM, k = v % NP;
     float beta = 0.0f;
     if (i < N && k < NV) {
-      // b_i = (p, v, a at t = 0; p, v, a at t = H) of robot i along axis x
-      float bi[6], bm[6];
-#pragma unroll
-      for (int q = 0; q < 6; ++q) bm[q] = 0.0f;
+      float bi[6] = {0, 0, 0, 0, 0, 0}, bm[6] = {0, 0, 0, 0, 0, 0};
       for (int j = 0; j < N; ++j) {
         const int rr = robot_off + j;
         float bj[6];
@@ -361,54 +429,53 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
     const int s = v / (NMAX * RS), rem = v % (NMAX * RS);
     const int i = rem / RS, x = (rem / NP) % DIM, k = rem % NP;
     float* blk = SAMP + (size_t)s * L.SB;
-    float c = 0.0f, l = 0.0f, xb = 0.0f;
+    float c = 0.0f, l = 0.0f;
     if (i < N && k < NV) {
       const long long g = coef0 + s * per_sample + ((long long)x * N + i) * NV + k;
-      xb = A.xi_bar[g];
-      c = A.xi0 ? A.xi0[g] : xb;
+      c = A.xi0 ? A.xi0[g] : A.xi_bar[g];
       l = A.lam0 ? A.lam0[g] : 0.0f;
     }
-    blk[L.C() + rem] = c;
-    blk[L.LAM() + rem] = l;
-    blk[L.XIB() + rem] = xb;
-    blk[L.CPREV() + rem] = c;
-    for (int tb = 0; tb < TB; ++tb) blk[L.GP(tb) + rem] = 0.0f;
+    blk[L.C + rem] = c;
+    blk[L.LAM + rem] = l;
+    for (int q = 0; q < L.NQ; ++q) blk[L.PG + q * NMAX * RS + rem] = 0.0f;
   }
   __syncthreads();
 
-  const int units = G * TB;
   const float rho = pc.rho;
   const float invN = 1.0f / (float)N;
+  const int TC = L.TC;
   for (int it = 0; it < pc.K; ++it) {
-    // ---- time phase
-    for (int u = warp; u < units; u += nwarps) {
-      const int s = u / TB, tb = u % TB;
-      float* blk = SAMP + (size_t)s * L.SB;
-      time_unit<DIM, NMAX>(blk + L.C(), A.basis, T, tb * 32 + lane, N, pc, blk + L.GP(tb),
-                           blk + L.RESP() + tb, lane);
+    for (int t0 = 0; t0 < T; t0 += TC) {
+      const int TCc = min(TC, T - t0);
+      pair_phase<DIM, NMAX>(SAMP, L, BASIS, G, N, t0, TCc, pc, want_res, warp, nwarps, lane);
+      __syncthreads();
+      contract_phase<DIM>(SAMP, L, BASIS, G, N, t0, TCc, t0 == 0, pc, want_res, tid, nthr);
+      __syncthreads();
     }
-    __syncthreads();
-    // ---- solve phase 1: lambda step, r, robot means
+    // ---- solve phase 1: lambda step, r, robot means (and the history entry)
     for (int v = tid; v < G * DIM * NV; v += nthr) {
       const int s = v / (DIM * NV), x = (v / NV) % DIM, k = v % NV;
       float* blk = SAMP + (size_t)s * L.SB;
       float sr = 0.0f, sc = 0.0f;
       for (int i = 0; i < N; ++i) {
         const int o = i * RS + x * NP + k;
-        float g = 0.0f;
-        for (int tb = 0; tb < TB; ++tb) g += blk[L.GP(tb) + o];
-        const float lam = fmaf(rho, g, blk[L.LAM() + o]);
-        blk[L.LAM() + o] = lam;
-        const float r = fmaf(rho, g, lam) + blk[L.XIB() + o];
-        blk[L.GP(0) + o] = r;
+        float g = blk[L.PG + o];
+        for (int q = 1; q < L.NQ; ++q) g += blk[L.PG + q * NMAX * RS + o];
+        const float lam = fmaf(rho, g, blk[L.LAM + o]);
+        blk[L.LAM + o] = lam;
+        const float xb = A.xi_bar[coef0 + s * per_sample + ((long long)x * N + i) * NV + k];
+        const float r = fmaf(rho, g, lam) + xb;
+        blk[L.PG + o] = r;
         sr += r;
-        sc += blk[L.C() + o];
+        sc += blk[L.C + o];
       }
-      blk[L.MR() + x * NP + k] = sr * invN;
-      blk[L.MC() + x * NP + k] = sc * invN;
-      if (A.hist && x == 0 && k == 0) {
+      blk[L.MR + x * NP + k] = sr * invN;
+      blk[L.MC + x * NP + k] = sc * invN;
+      if (want_res && x == 0 && k == 0) {
         float r2 = 0.0f;
-        for (int tb = 0; tb < TB; ++tb) r2 += blk[L.RESP() + tb];
+        for (int t = 0; t < T; ++t) r2 += blk[L.RS2 + t];
+        for (int q = 0; q < L.NQ; ++q)
+          for (int i = 0; i < N; ++i) r2 += blk[L.RSB + q * NMAX + i];
         A.hist[(size_t)it * A.total_samples + gsample0 + s] = sqrtf(r2);
       }
     }
@@ -420,13 +487,13 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
       float* blk = SAMP + (size_t)s * L.SB;
       const int o = i * RS + x * NP;
       float c[NP], r[NP], cm[NP], rm[NP];
-      const float4* c4 = reinterpret_cast<const float4*>(blk + L.C() + o);
-      const float4* r4 = reinterpret_cast<const float4*>(blk + L.GP(0) + o);
-      const float4* cm4 = reinterpret_cast<const float4*>(blk + L.MC() + x * NP);
-      const float4* rm4 = reinterpret_cast<const float4*>(blk + L.MR() + x * NP);
+      const float4* c4 = reinterpret_cast<const float4*>(blk + L.C + o);
+      const float4* r4 = reinterpret_cast<const float4*>(blk + L.PG + o);
+      const float4* cm4 = reinterpret_cast<const float4*>(blk + L.MC + x * NP);
+      const float4* rm4 = reinterpret_cast<const float4*>(blk + L.MR + x * NP);
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        float4 a = c4[q], b = r4[q], e = cm4[q], f = rm4[q];
+        const float4 a = c4[q], b = r4[q], e = cm4[q], f = rm4[q];
         c[4 * q] = a.x; c[4 * q + 1] = a.y; c[4 * q + 2] = a.z; c[4 * q + 3] = a.w;
         r[4 * q] = b.x; r[4 * q + 1] = b.y; r[4 * q + 2] = b.z; r[4 * q + 3] = b.w;
         cm[4 * q] = e.x; cm[4 * q + 1] = e.y; cm[4 * q + 2] = e.z; cm[4 * q + 3] = e.w;
@@ -446,8 +513,8 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
         out[k] = acc;
       }
       out[NV] = 0.0f;
-      float4* o4 = reinterpret_cast<float4*>(blk + L.C() + o);
-      float4* p4 = reinterpret_cast<float4*>(blk + L.CPREV() + o);
+      float4* o4 = reinterpret_cast<float4*>(blk + L.C + o);
+      float4* p4 = reinterpret_cast<float4*>(blk + L.EB + o);
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         if (last) p4[q] = make_float4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]);
@@ -457,18 +524,19 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
     __syncthreads();
   }
 
-  // ---- final residual, Eq. (primal_residual)
-  for (int u = warp; u < units; u += nwarps) {
-    const int s = u / TB, tb = u % TB;
-    float* blk = SAMP + (size_t)s * L.SB;
-    residual_unit<DIM, NMAX>(blk + L.C(), blk + L.CPREV(), A.basis, T, tb * 32 + lane, N, pc,
-                             blk + L.RESP() + tb);
+  // ---- final residual, Eq. (primal_residual); robot rows beyond N of the
+  // xi^{K-1} copy are zero-filled first
+  for (int v = tid; v < G * NMAX * RS; v += nthr) {
+    const int s = v / (NMAX * RS), rem = v % (NMAX * RS);
+    if (rem / RS >= N) SAMP[(size_t)s * L.SB + L.EB + rem] = 0.0f;
   }
+  __syncthreads();
+  residual_phase<DIM, NMAX>(SAMP, L, BASIS, G, N, T, pc, warp, nwarps, lane);
   __syncthreads();
   for (int s = tid; s < G; s += nthr) {
     const float* blk = SAMP + (size_t)s * L.SB;
     float r2 = 0.0f;
-    for (int tb = 0; tb < TB; ++tb) r2 += blk[L.RESP() + tb];
+    for (int t = 0; t < T; ++t) r2 += blk[L.RS2 + t];
     const float r = sqrtf(r2);
     A.resid_out[gsample0 + s] = r;
     if (!isfinite(r)) atomicOr(A.status, ST_NONFINITE);
@@ -479,8 +547,8 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
     const float* blk = SAMP + (size_t)s * L.SB;
     const int o = i * RS + x * NP + k;
     const long long g = coef0 + (long long)s * per_sample + rem;
-    A.xi_out[g] = blk[L.C() + o];
-    A.lam_out[g] = blk[L.LAM() + o];
+    A.xi_out[g] = blk[L.C + o];
+    A.lam_out[g] = blk[L.LAM + o];
   }
 }
 

@@ -77,6 +77,8 @@ struct FusedArgs {
   float* hist;             // [K][total samples] or null
   int total_samples;
   int* status;
+  int tc;                  // time steps per chunk
+  int nq;                  // time ranges per chunk in the contraction phase
   SceneDesc sc[MAX_SCENES_PER_LAUNCH];
 };
 
@@ -134,11 +136,23 @@ struct FusedLaunch {
   int warps;    // warps per CTA
   int gmax;     // largest samples-per-CTA of the scenes in this launch
   int n_ctas;
+  int tc, nq;   // time chunk, contraction ranges
   size_t smem;  // dynamic shared memory bytes
 };
-size_t fused_smem_bytes(int dim, int nmax, int T, int gmax);
+size_t fused_smem_bytes(int dim, int nmax, int T, int gmax, int tc, int nq);
 cudaError_t launch_fused(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st);
-int fused_max_warps();
+int fused_max_warps(int nmax);
+
+// Launch shape of the fused kernel for one group of scenes: samples per CTA,
+// warps, time chunk, contraction ranges (cost model over the candidates,
+// shared-memory bound checked).
+struct FusedPlan {
+  int G, warps, tc, nq;
+  size_t smem;
+  double cost;
+};
+FusedPlan plan_fused(int dim, int nmax, int T, const int* n_robots, const int* n_samples, int n_scenes,
+                     int num_sms, size_t smem_cap, int force_G, int force_warps, int force_tc);
 
 struct PlainArgs {
   ProblemConsts pc;

@@ -181,6 +181,14 @@ class SafetyFilter:
         nat.check(self._lib, self._h, code)
         return out
 
+    def set_launch_shape(self, samples_per_cta: int = 0, warps: int = 0, time_chunk: int = 0):
+        nat.check(self._lib, self._h, self._lib.sf_set_launch_shape(self._h, samples_per_cta, warps, time_chunk))
+
+    def launch_shape(self):
+        out = (C.c_int * 4)()
+        nat.check(self._lib, self._h, self._lib.sf_get_launch_shape(self._h, out))
+        return {"G": out[0], "warps": out[1], "tc": out[2], "nq": out[3]}
+
     def launch_count(self) -> int:
         return int(self._lib.sf_launch_count(self._h))
 
