@@ -227,11 +227,45 @@ def run_gpu(args):
             "wall_s_timed": wall,
             "clocks": clocks,
         }
+        if not args.no_diff:
+            line["differentiation"] = diff_timing(P, dev)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(spec, sc, args.cpu_samples)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def diff_timing(P, dev):
+    """Forward / backward times of the differentiable SF on the
+    differentiation workload (N=16 3D, S=512, T=100, K=50, checkpoint every
+    10), CUDA events, mean of 5 after one warm-up call."""
+    import torch
+    spec = si.config_diff()
+    sc = si.scene(spec, 5)
+    f = P.SafetyFilter(dim=3, T=spec.T, rho=RHO, coll_a=spec.coll, v_max=spec.v_max, a_max=spec.a_max,
+                       max_robots=spec.n_robots, checkpoint_every=10, device=dev.index)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    xb, st, gl = t(sc.xi_bar), t(sc.start), t(sc.goal)
+    g = torch.randn(xb.shape, generator=torch.Generator().manual_seed(0)).to(dev)
+
+    def timed(fn, n=5):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    fwd = timed(lambda: f.project(xb, st, gl, spec.K))
+    trn = timed(lambda: f.project_train(xb, st, gl, spec.K))
+    _, _, ck = f.project_train(xb, st, gl, spec.K)
+    bwd = timed(lambda: f.project_backward(xb, st, gl, spec.K, ck, grad_xi=g))
+    return {"workload": f"3D N={spec.n_robots}, S={spec.n_samples}, T={spec.T}, K={spec.K}, checkpoint every 10",
+            "fwd_ms": fwd, "train_fwd_ms": trn, "bwd_ms": bwd, "bwd_over_fwd": bwd / fwd}
 
 
 def cpu_baseline(spec, sc, n_samples):
@@ -295,6 +329,7 @@ def main():
     ap.add_argument("--form", default="fused", choices=["fused", "plain"])
     ap.add_argument("--cpu-samples", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-diff", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

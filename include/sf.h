@@ -207,6 +207,45 @@ sf_status sf_project_plain_noalloc(sf_handle *h, void *stream, const sf_batch *b
                                    const float *xi0, const float *lambda0, float *xi_out,
                                    float *lambda_out, float *residual_out, float *residual_hist);
 
+/* Forward for training (fused form, SF_PREC_FP32): as sf_project, and in
+ * addition
+ *   fp_res2_out  device [sum S_s] or NULL: sum over k < K of
+ *                ||z^{k+1} - z^k||^2 with z = (xi, lambda), the first term of
+ *                Eq. (NN_loss) (the fixed-point residual of the unroll);
+ *   checkpoints  device, sf_checkpoint_bytes() bytes (required): (xi, lambda)
+ *                of every sample at iterations 0, k, 2k, ... (k =
+ *                checkpoint_every of the problem), layout
+ *                [n_checkpoints][2][total coefficients].
+ * Needs a handle created with checkpoint_every > 0. */
+sf_status sf_project_train(sf_handle *h, void *stream, const sf_batch *batch, int K,
+                           const float *xi0, const float *lambda0, float *xi_out, float *lambda_out,
+                           float *residual_out, float *fp_res2_out, void *checkpoints);
+
+/* Device workspace of sf_project_backward: the iterates of one checkpoint
+ * segment, (checkpoint_every + 1) x 2 x total coefficients floats. */
+size_t sf_backward_workspace_bytes(const sf_handle *h, const sf_batch *batch, int K);
+
+/* Reverse mode through the K unrolled iterations of a previous
+ * sf_project_train call with the same batch, K and initial iterate (the
+ * paper trains its initialisation network through the unrolled solver,
+ * Sec. III-C, Eq. NN_loss). With
+ *   L = <grad_xi_out, xi^K> + <grad_lambda_out, lambda^K>
+ *       + sum_s grad_fp_res2[s] * fp_res2[s],
+ * it writes dL/dxi^0 (grad_xi0), dL/dlambda^0 (grad_lambda0) and dL/dxi_bar
+ * (grad_xi_bar); any of the three may be NULL, and so may each of the three
+ * incoming gradients (= 0). init_from_xi_bar != 0 states that the forward
+ * ran with xi0 == NULL (xi^0 = xi_bar); grad_xi_bar then includes that path.
+ * Each segment of checkpoint_every iterations is recomputed from its
+ * checkpoint into `workspace` (sf_backward_workspace_bytes() bytes) and
+ * walked back. At non-differentiable points the Jacobian of the closed-form
+ * steps is taken as the one-sided value of the active or inactive branch;
+ * at delta = 0 the Jacobian of e is 0. */
+sf_status sf_project_backward(sf_handle *h, void *stream, const sf_batch *batch, int K,
+                              int init_from_xi_bar, const void *checkpoints,
+                              const float *grad_xi_out, const float *grad_lambda_out,
+                              const float *grad_fp_res2, float *grad_xi0, float *grad_lambda0,
+                              float *grad_xi_bar, void *workspace, size_t workspace_bytes);
+
 /* Synchronises `stream` and returns any device-side error latched by earlier
  * calls on the handle (SF_ERR_TIMEOUT, SF_ERR_NONFINITE), clearing it. */
 sf_status sf_sync_status(sf_handle *h, void *stream);

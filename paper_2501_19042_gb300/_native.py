@@ -23,6 +23,7 @@ FORM = {"fused": 0, "plain": 1}
 EXPORTS = ("sf_create", "sf_destroy", "sf_last_error", "sf_workspace_bytes", "sf_checkpoint_bytes",
            "sf_project", "sf_host_staging_bytes", "sf_project_host", "sf_launch_count",
            "sf_project_plain_noalloc", "sf_set_launch_shape", "sf_get_launch_shape",
+           "sf_project_train", "sf_backward_workspace_bytes", "sf_project_backward",
            "sf_sync_status")
 
 
@@ -93,6 +94,13 @@ def load(path: str = LIB_PATH):
         lib.sf_set_launch_shape.restype = C.c_int
         lib.sf_get_launch_shape.argtypes = [vp, C.POINTER(C.c_int)]
         lib.sf_get_launch_shape.restype = C.c_int
+        lib.sf_project_train.argtypes = [vp, vp, C.POINTER(SfBatch), C.c_int, vp, vp, vp, vp, vp, vp, vp]
+        lib.sf_project_train.restype = C.c_int
+        lib.sf_backward_workspace_bytes.argtypes = [vp, C.POINTER(SfBatch), C.c_int]
+        lib.sf_backward_workspace_bytes.restype = sz
+        lib.sf_project_backward.argtypes = [vp, vp, C.POINTER(SfBatch), C.c_int, C.c_int, vp, vp, vp, vp, vp,
+                                            vp, vp, vp, sz]
+        lib.sf_project_backward.restype = C.c_int
         lib.sf_sync_status.argtypes = [vp, vp]
         lib.sf_sync_status.restype = C.c_int
         _lib = lib

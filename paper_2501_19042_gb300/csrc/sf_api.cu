@@ -92,6 +92,116 @@ sf_status check_batch(sf_handle* h, const sf_batch* b, long long* tot_robots, lo
   return SF_OK;
 }
 
+
+struct FusedRequest {
+  const float* xi0 = nullptr;
+  const float* lam0 = nullptr;
+  float* xi_out = nullptr;
+  float* lam_out = nullptr;
+  float* resid_out = nullptr;
+  float* hist = nullptr;
+  float* ckpt = nullptr;
+  float* fp_res2 = nullptr;
+  bool backward = false;
+  BwdLaunchArgs bwd{};
+};
+
+long long total_coefs(const sf_handle* h, const sf_batch* b) {
+  long long c = 0;
+  for (int q = 0; q < b->n_scenes; ++q) c += (long long)b->n_samples[q] * h->pb.dim * b->n_robots[q] * NV;
+  return c;
+}
+
+// Fused form: scenes grouped by robot-count bucket, one launch per group of
+// up to MAX_SCENES_PER_LAUNCH scenes; the planner picks the launch shape.
+sf_status run_fused(sf_handle* h, cudaStream_t st, const sf_batch* b, int K, long long S, const FusedRequest& rq) {
+  const int dim = h->pb.dim, T = h->pb.T;
+  const ProblemConsts pc = consts(h->pb, K);
+  const long long tot = total_coefs(h, b);
+  struct Item { int scene; long long roff, soff, coff; };
+  std::vector<Item> items[3];
+  {
+    long long roff = 0, soff = 0, coff = 0;
+    for (int sc = 0; sc < b->n_scenes; ++sc) {
+      const int N = b->n_robots[sc], Ss = b->n_samples[sc];
+      const int bk = nmax_bucket(N) == 8 ? 0 : (nmax_bucket(N) == 16 ? 1 : 2);
+      if (Ss > 0) items[bk].push_back({sc, roff, soff, coff});
+      roff += N;
+      soff += Ss;
+      coff += (long long)Ss * dim * N * NV;
+    }
+  }
+  for (int bk = 0; bk < 3; ++bk) {
+    const int nmax = 8 << bk;
+    for (size_t first = 0; first < items[bk].size(); first += MAX_SCENES_PER_LAUNCH) {
+      const size_t last = std::min(items[bk].size(), first + (size_t)MAX_SCENES_PER_LAUNCH);
+      std::vector<int> nr, ns;
+      for (size_t q = first; q < last; ++q) {
+        nr.push_back(b->n_robots[items[bk][q].scene]);
+        ns.push_back(b->n_samples[items[bk][q].scene]);
+      }
+      const FusedPlan plan = plan_fused(dim, nmax, T, nr.data(), ns.data(), (int)nr.size(), h->num_sms,
+                                        h->max_smem_optin, h->force_G, h->force_warps, h->force_tc, rq.backward);
+      if (plan.G == 0) return fail(h, SF_ERR_UNSUPPORTED, "no fused launch shape fits in shared memory");
+      FusedArgs a;
+      std::memset(&a, 0, sizeof(a));
+      a.pc = pc;
+      a.basis = reinterpret_cast<const float4*>(h->basis);
+      a.ops = h->ops;
+      a.start = b->start;
+      a.goal = b->goal;
+      a.start_va = b->start_va;
+      a.goal_va = b->goal_va;
+      a.xi_bar = b->xi_bar;
+      a.xi0 = rq.xi0;
+      a.lam0 = rq.lam0;
+      a.xi_out = rq.xi_out;
+      a.lam_out = rq.lam_out;
+      a.resid_out = rq.resid_out;
+      a.hist = rq.hist;
+      a.total_samples = (int)S;
+      a.status = h->status;
+      a.tc = plan.tc;
+      a.nq = plan.nq;
+      a.ckpt = rq.ckpt;
+      a.ck_every = std::max(1, h->pb.checkpoint_every);
+      a.total_coefs = tot;
+      a.fp_res2 = rq.fp_res2;
+      int ctas = 0, gmax = 1;
+      a.n_scenes = (int)(last - first);
+      for (size_t q = first; q < last; ++q) {
+        const Item& it = items[bk][q];
+        SceneDesc& d = a.sc[q - first];
+        d.N = b->n_robots[it.scene];
+        d.S = b->n_samples[it.scene];
+        d.G = std::min(plan.G, d.S);
+        d.cta_begin = ctas;
+        d.robot_off = (int)it.roff;
+        d.sample_off = (int)it.soff;
+        d.coef_off = it.coff;
+        ctas += (d.S + d.G - 1) / d.G;
+        gmax = std::max(gmax, d.G);
+      }
+      FusedLaunch l;
+      l.nmax = nmax;
+      l.gmax = gmax;
+      l.n_ctas = ctas;
+      l.warps = plan.warps;
+      l.tc = plan.tc;
+      l.nq = plan.nq;
+      l.smem = fused_smem_bytes(dim, nmax, T, gmax, plan.tc, plan.nq, rq.backward);
+      h->last_plan[0] = plan.G;
+      h->last_plan[1] = plan.warps;
+      h->last_plan[2] = plan.tc;
+      h->last_plan[3] = plan.nq;
+      cudaError_t e = rq.backward ? launch_backward(a, rq.bwd, l, st) : launch_fused(a, l, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, rq.backward ? "backward launch" : "fused form launch");
+      h->launches += 1;
+    }
+  }
+  return SF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -202,7 +312,6 @@ sf_status sf_project(sf_handle* h, void* stream, const sf_batch* b, int K, int f
   if (form != SF_FORM_FUSED && form != SF_FORM_PLAIN) return fail(h, SF_ERR_INVALID_ARG, "unknown form");
   if (h->pb.precision != SF_PREC_FP32)
     return fail(h, SF_ERR_UNSUPPORTED, "only SF_PREC_FP32 is built into this library");
-  if (checkpoints) return fail(h, SF_ERR_UNSUPPORTED, "checkpointed forward not built");
   if (S == 0) return SF_OK;
   DeviceGuard g(h->device);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -252,85 +361,82 @@ sf_status sf_project(sf_handle* h, void* stream, const sf_batch* b, int K, int f
     return SF_OK;
   }
 
-  // ---- fused form: scenes grouped by robot-count bucket, one launch per group
-  struct Item { int scene; long long roff, soff, coff; };
-  std::vector<Item> items[3];
-  {
-    long long roff = 0, soff = 0, coff = 0;
-    for (int sc = 0; sc < b->n_scenes; ++sc) {
-      const int N = b->n_robots[sc], Ss = b->n_samples[sc];
-      const int bk = nmax_bucket(N) == 8 ? 0 : (nmax_bucket(N) == 16 ? 1 : 2);
-      if (Ss > 0) items[bk].push_back({sc, roff, soff, coff});
-      roff += N;
-      soff += Ss;
-      coff += (long long)Ss * dim * N * NV;
-    }
-  }
-  for (int bk = 0; bk < 3; ++bk) {
-    const int nmax = 8 << bk;
-    for (size_t first = 0; first < items[bk].size(); first += MAX_SCENES_PER_LAUNCH) {
-      const size_t last = std::min(items[bk].size(), first + (size_t)MAX_SCENES_PER_LAUNCH);
-      std::vector<int> nr, ns;
-      for (size_t q = first; q < last; ++q) {
-        nr.push_back(b->n_robots[items[bk][q].scene]);
-        ns.push_back(b->n_samples[items[bk][q].scene]);
-      }
-      const FusedPlan plan = plan_fused(dim, nmax, T, nr.data(), ns.data(), (int)nr.size(), h->num_sms,
-                                        h->max_smem_optin, h->force_G, h->force_warps, h->force_tc);
-      if (plan.G == 0) return fail(h, SF_ERR_UNSUPPORTED, "no fused launch shape fits in shared memory");
-      FusedArgs a;
-      std::memset(&a, 0, sizeof(a));
-      a.pc = pc;
-      a.basis = reinterpret_cast<const float4*>(h->basis);
-      a.ops = h->ops;
-      a.start = b->start;
-      a.goal = b->goal;
-      a.start_va = b->start_va;
-      a.goal_va = b->goal_va;
-      a.xi_bar = b->xi_bar;
-      a.xi0 = xi0;
-      a.lam0 = lam0;
-      a.xi_out = xi_out;
-      a.lam_out = lam_out;
-      a.resid_out = resid_out;
-      a.hist = resid_hist;
-      a.total_samples = (int)S;
-      a.status = h->status;
-      a.tc = plan.tc;
-      a.nq = plan.nq;
-      int ctas = 0, gmax = 1;
-      a.n_scenes = (int)(last - first);
-      for (size_t q = first; q < last; ++q) {
-        const Item& it = items[bk][q];
-        SceneDesc& d = a.sc[q - first];
-        d.N = b->n_robots[it.scene];
-        d.S = b->n_samples[it.scene];
-        d.G = std::min(plan.G, d.S);
-        d.cta_begin = ctas;
-        d.robot_off = (int)it.roff;
-        d.sample_off = (int)it.soff;
-        d.coef_off = it.coff;
-        ctas += (d.S + d.G - 1) / d.G;
-        gmax = std::max(gmax, d.G);
-      }
-      FusedLaunch l;
-      l.nmax = nmax;
-      l.gmax = gmax;
-      l.n_ctas = ctas;
-      l.warps = plan.warps;
-      l.tc = plan.tc;
-      l.nq = plan.nq;
-      l.smem = fused_smem_bytes(dim, nmax, T, gmax, plan.tc, plan.nq);
-      h->last_plan[0] = plan.G;
-      h->last_plan[1] = plan.warps;
-      h->last_plan[2] = plan.tc;
-      h->last_plan[3] = plan.nq;
-      cudaError_t e = launch_fused(a, l, st);
-      if (e != cudaSuccess) return cuda_fail(h, e, "fused form launch");
-      h->launches += 1;
-    }
-  }
-  return SF_OK;
+  FusedRequest rq;
+  rq.xi0 = xi0;
+  rq.lam0 = lam0;
+  rq.xi_out = xi_out;
+  rq.lam_out = lam_out;
+  rq.resid_out = resid_out;
+  rq.hist = resid_hist;
+  rq.ckpt = reinterpret_cast<float*>(checkpoints);
+  if (checkpoints && h->pb.checkpoint_every <= 0)
+    return fail(h, SF_ERR_INVALID_ARG, "checkpoints need a handle with checkpoint_every > 0");
+  return run_fused(h, st, b, K, S, rq);
+}
+
+sf_status sf_project_train(sf_handle* h, void* stream, const sf_batch* b, int K, const float* xi0,
+                           const float* lam0, float* xi_out, float* lam_out, float* resid_out, float* fp_res2_out,
+                           void* checkpoints) {
+  if (!h) return SF_ERR_INVALID_ARG;
+  long long R = 0, S = 0;
+  sf_status s0 = check_batch(h, b, &R, &S);
+  if (s0 != SF_OK) return s0;
+  if (K < 1) return fail(h, SF_ERR_INVALID_ARG, "K must be >= 1");
+  if (h->pb.checkpoint_every <= 0) return fail(h, SF_ERR_INVALID_ARG, "handle has checkpoint_every = 0");
+  if (h->pb.precision != SF_PREC_FP32) return fail(h, SF_ERR_UNSUPPORTED, "training forward is float32 only");
+  if (S > 0 && (!xi_out || !lam_out || !resid_out || !checkpoints))
+    return fail(h, SF_ERR_INVALID_ARG, "xi_out / lambda_out / residual_out / checkpoints is NULL");
+  if (S == 0) return SF_OK;
+  DeviceGuard g(h->device);
+  FusedRequest rq;
+  rq.xi0 = xi0;
+  rq.lam0 = lam0;
+  rq.xi_out = xi_out;
+  rq.lam_out = lam_out;
+  rq.resid_out = resid_out;
+  rq.ckpt = reinterpret_cast<float*>(checkpoints);
+  rq.fp_res2 = fp_res2_out;
+  return run_fused(h, reinterpret_cast<cudaStream_t>(stream), b, K, S, rq);
+}
+
+size_t sf_backward_workspace_bytes(const sf_handle* hc, const sf_batch* b, int K) {
+  sf_handle* h = const_cast<sf_handle*>(hc);
+  if (!h || h->pb.checkpoint_every <= 0 || K < 1) return 0;
+  long long R = 0, S = 0;
+  if (check_batch(h, b, &R, &S) != SF_OK) return 0;
+  return (size_t)(h->pb.checkpoint_every + 1) * 2 * (size_t)total_coefs(h, b) * sizeof(float);
+}
+
+sf_status sf_project_backward(sf_handle* h, void* stream, const sf_batch* b, int K, int init_from_xi_bar,
+                              const void* checkpoints, const float* g_xi, const float* g_lam, const float* g_fp,
+                              float* gx0, float* gl0, float* gxb, void* workspace, size_t workspace_bytes) {
+  if (!h) return SF_ERR_INVALID_ARG;
+  long long R = 0, S = 0;
+  sf_status s0 = check_batch(h, b, &R, &S);
+  if (s0 != SF_OK) return s0;
+  if (K < 1) return fail(h, SF_ERR_INVALID_ARG, "K must be >= 1");
+  if (h->pb.checkpoint_every <= 0) return fail(h, SF_ERR_INVALID_ARG, "handle has checkpoint_every = 0");
+  if (h->pb.precision != SF_PREC_FP32) return fail(h, SF_ERR_UNSUPPORTED, "backward is float32 only");
+  if (S == 0) return SF_OK;
+  if (!checkpoints) return fail(h, SF_ERR_INVALID_ARG, "checkpoints is NULL");
+  const size_t need = sf_backward_workspace_bytes(h, b, K);
+  if (!workspace || workspace_bytes < need)
+    return fail(h, SF_ERR_WORKSPACE, "backward needs " + std::to_string(need) + " workspace bytes");
+  DeviceGuard g(h->device);
+  FusedRequest rq;
+  rq.backward = true;
+  rq.bwd.ckpt = reinterpret_cast<const float*>(checkpoints);
+  rq.bwd.ck_every = h->pb.checkpoint_every;
+  rq.bwd.total_coefs = total_coefs(h, b);
+  rq.bwd.ring = reinterpret_cast<float*>(workspace);
+  rq.bwd.g_xi = g_xi;
+  rq.bwd.g_lam = g_lam;
+  rq.bwd.g_fp = g_fp;
+  rq.bwd.gx0 = gx0;
+  rq.bwd.gl0 = gl0;
+  rq.bwd.gxb = gxb;
+  rq.bwd.xi0_is_xi_bar = init_from_xi_bar ? 1 : 0;
+  return run_fused(h, reinterpret_cast<cudaStream_t>(stream), b, K, S, rq);
 }
 
 unsigned long long sf_launch_count(const sf_handle* h) { return h ? h->launches : 0ULL; }

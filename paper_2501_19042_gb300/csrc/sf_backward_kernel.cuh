@@ -1,0 +1,408 @@
+// Adjoint (reverse mode) of the unrolled safety-filter iterations: the
+// gradient of
+//   L = <gx, xi^K> + <gl, lambda^K> + sum_s w_s sum_{k<K} ||z^{k+1} - z^k||^2
+// (z = (xi, lambda); the sum is the first term of Eq. (NN_loss)) with respect
+// to xi^0, lambda^0 and xi_bar. The paper notes that every step of f_FP has a
+// closed form, so the unroll is differentiable (Sec. III-C); this kernel
+// differentiates the steps by hand.
+//
+// Forward step written for the adjoint (per sample):
+//   q = e(F xi) - F xi,  g = F^T q,  lambda' = lambda + rho g,
+//   r = rho g + lambda' + xi_bar,  xi' = Wop xi + Sop r + beta,
+// with Sop = Pi_dev (x) S1 + Pi_mean (x) S0 (symmetric) and Wop = Sop rho H.
+// Given (xb, lb) = dL/d(xi', lambda'):
+//   r_bar = Sop^T xb;  xi_bar_grad += r_bar;  lb_total = lb + r_bar;
+//   g_bar = rho (r_bar + lb_total);  dL/dlambda = lb_total;
+//   dL/dxi = Wop^T xb + F^T (J_e - I)^T F g_bar,
+// where J_e is the Jacobian of the alpha / beta / d closed forms: for a pair
+// row with scaled distance s2 < 1, e = delta / sqrt(s2); for a ball row
+// outside the ball, e = r v / ||v||; inactive rows have J_e = I; at delta = 0
+// J_e is taken as 0.
+//
+// The CTA recomputes each segment of checkpoint_every iterations forward from
+// its checkpoint into a ring in global memory, then walks the segment back.
+#pragma once
+#include "sf_fused_kernel.cuh"
+
+namespace sf {
+namespace fused_impl {
+
+struct BwdArgs {
+  ProblemConsts pc;
+  int n_scenes;
+  const float4* basis;
+  const float* ops;
+  const float* start;
+  const float* goal;
+  const float* start_va;
+  const float* goal_va;
+  const float* xi_bar;
+  const float* ckpt;       // [n_ck][2][total_coefs]
+  int ck_every;
+  long long total_coefs;
+  float* ring;             // [ck_every + 1][2][total_coefs]
+  const float* g_xi;       // dL/dxi^K or null
+  const float* g_lam;      // dL/dlambda^K or null
+  const float* g_fp;       // per-sample weight of sum ||z^{k+1} - z^k||^2, or null
+  float* gx0;              // dL/dxi^0 (or null)
+  float* gl0;              // dL/dlambda^0 (or null)
+  float* gxb;              // dL/dxi_bar (or null); includes the xi^0 path when xi0_is_xi_bar
+  int xi0_is_xi_bar;
+  int tc, nq;
+  int total_samples;
+  int* status;
+  SceneDesc sc[MAX_SCENES_PER_LAUNCH];
+};
+
+// Pair rows of the adjoint for one chunk: Delta_bar = (J_e - I)^T (u_i - u_j)
+// with u = positions of g_bar, added to E_bar_i and subtracted from E_bar_j
+// in the chunk buffer.
+template <int DIM, int NMAX>
+__device__ void adj_pair_phase(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, int t0, int TCc) {
+  constexpr int RS = DIM * NP;
+  const Lay& L = c.L;
+  const int N = c.N;
+  const int nA = c.G * TCc;
+  for (int base = c.warp * 32; base < nA; base += c.nwarps * 32) {
+    const int u = base + c.lane;
+    const bool valid = u < nA;
+    const int s = valid ? u / TCc : 0;
+    const int tl = valid ? u - s * TCc : 0;
+    const int t = t0 + tl;
+    float* blk = c.blk(s);
+    float Pr[NV];
+    row_from(c.BASIS + (size_t)t * BASIS_ROW, Pr);
+    float* eb = blk + L.EB + tl * L.EP;
+    if (valid)
+      for (int q = 0; q < N * DIM; ++q) eb[q] = 0.0f;
+    float p[NMAX][DIM], ug[NMAX][DIM];
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i) {
+      if (i < N) {
+        state<DIM>(Pr, blk + L.C + i * RS, p[i]);
+        state<DIM>(Pr, blk + L.U + i * RS, ug[i]);
+      } else {
+#pragma unroll
+        for (int x = 0; x < DIM; ++x) { p[i][x] = 0.0f; ug[i][x] = 0.0f; }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i)
+#pragma unroll
+      for (int j = 0; j < NMAX; ++j) {
+        if (j > i && j < N) {
+          float d[DIM];
+#pragma unroll
+          for (int x = 0; x < DIM; ++x) d[x] = p[i][x] - p[j][x];
+          float s2;
+          if (DIM == 3)
+            s2 = fmaf(d[2] * d[2], pc.inv_b2, (d[0] * d[0] + d[1] * d[1]) * pc.inv_a2);
+          else
+            s2 = (d[0] * d[0] + d[1] * d[1]) * pc.inv_a2;
+          s2 = valid ? s2 : 2.0f;
+          const bool act = s2 < 1.0f;
+          if (__any_sync(FULL, act)) {
+            float U[DIM], m[DIM];
+            float du = 0.0f;
+#pragma unroll
+            for (int x = 0; x < DIM; ++x) {
+              U[x] = ug[i][x] - ug[j][x];
+              m[x] = d[x] * (x == 2 ? pc.inv_b2 : pc.inv_a2);
+              du = fmaf(d[x], U[x], du);
+            }
+            const bool zero = (s2 == 0.0f);
+            const float inv = rsqrtf(zero ? 1.0f : s2);
+            const float f = act ? (zero ? -1.0f : inv - 1.0f) : 0.0f;
+            const float w = (act && !zero) ? inv * inv * inv * du : 0.0f;
+            if (valid && act) {
+#pragma unroll
+              for (int x = 0; x < DIM; ++x) {
+                const float db = fmaf(f, U[x], -w * m[x]);
+                eb[i * DIM + x] += db;
+                eb[j * DIM + x] -= db;
+              }
+            }
+          }
+        }
+      }
+  }
+}
+
+// Ball rows and the transposed contraction of the adjoint for one chunk:
+// dL/dxi += F^T Delta_bar, per (sample, robot, range of t), into PG partials.
+template <int DIM, int NMAX>
+__device__ void adj_contract_phase(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, int t0, int TCc,
+                                   bool first_chunk) {
+  constexpr int RS = DIM * NP;
+  const Lay& L = c.L;
+  const int N = c.N, G = c.G, NQ = L.NQ;
+  const int nB = NQ * G * N;
+  const int TQ = (TCc + NQ - 1) / NQ;
+  for (int base = c.warp * 32; base < nB; base += c.nwarps * 32) {
+    const int u = base + c.lane;
+    const bool uvalid = u < nB;
+    const int uu = uvalid ? u : 0;
+    const int i = uu % N;
+    const int s = (uu / N) % G;
+    const int tq = uu / (N * G);
+    const int ta = tq * TQ;
+    const int tb = uvalid ? min(ta + TQ, TCc) : ta;
+    float* blk = c.blk(s);
+    float cc[DIM][NV], gb[DIM][NV], g2[DIM][NV];
+#pragma unroll
+    for (int x = 0; x < DIM; ++x) {
+      row_from(blk + L.C + i * RS + x * NP, cc[x]);
+      row_from(blk + L.U + i * RS + x * NP, gb[x]);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) g2[x][k] = 0.0f;
+    }
+    // uniform trip count over the warp so that the votes see every lane
+    int trip = tb - ta;
+    int wtrip = trip;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) wtrip = max(wtrip, __shfl_xor_sync(FULL, wtrip, o));
+    for (int step = 0; step < wtrip; ++step) {
+      const bool live = step < trip;
+      const int tl = live ? ta + step : ta;
+      const float* brow = c.BASIS + (size_t)(t0 + tl) * BASIS_ROW;
+      float P[NV], Pd[NV], Pdd[NV];
+      row_from(brow, P);
+      row_from(brow + NP, Pd);
+      row_from(brow + 2 * NP, Pdd);
+      float e[DIM], vb[DIM], ab[DIM];
+      const float* ebp = blk + L.EB + tl * L.EP + i * DIM;
+#pragma unroll
+      for (int x = 0; x < DIM; ++x) { e[x] = live ? ebp[x] : 0.0f; vb[x] = 0.0f; ab[x] = 0.0f; }
+      if (pc.use_v) {
+        float v[DIM], n2 = 0.0f;
+#pragma unroll
+        for (int x = 0; x < DIM; ++x) { v[x] = dot_reg(Pd, cc[x]); n2 = fmaf(v[x], v[x], n2); }
+        const bool act = live && n2 > pc.v_max * pc.v_max;
+        if (__any_sync(FULL, act)) {
+          float U[DIM], du = 0.0f;
+#pragma unroll
+          for (int x = 0; x < DIM; ++x) { U[x] = dot_reg(Pd, gb[x]); du = fmaf(v[x], U[x], du); }
+          const float inv = rsqrtf(act ? n2 : 1.0f);
+          const float rr = pc.v_max * inv;
+#pragma unroll
+          for (int x = 0; x < DIM; ++x) vb[x] = act ? fmaf(rr - 1.0f, U[x], -rr * inv * inv * du * v[x]) : 0.0f;
+        }
+      }
+      if (pc.use_a) {
+        float a[DIM], n2 = 0.0f;
+#pragma unroll
+        for (int x = 0; x < DIM; ++x) { a[x] = dot_reg(Pdd, cc[x]); n2 = fmaf(a[x], a[x], n2); }
+        const bool act = live && n2 > pc.a_max * pc.a_max;
+        if (__any_sync(FULL, act)) {
+          float U[DIM], du = 0.0f;
+#pragma unroll
+          for (int x = 0; x < DIM; ++x) { U[x] = dot_reg(Pdd, gb[x]); du = fmaf(a[x], U[x], du); }
+          const float inv = rsqrtf(act ? n2 : 1.0f);
+          const float rr = pc.a_max * inv;
+#pragma unroll
+          for (int x = 0; x < DIM; ++x) ab[x] = act ? fmaf(rr - 1.0f, U[x], -rr * inv * inv * du * a[x]) : 0.0f;
+        }
+      }
+      bool ne = false, nb = false;
+#pragma unroll
+      for (int x = 0; x < DIM; ++x) {
+        ne |= e[x] != 0.0f;
+        nb |= (vb[x] != 0.0f) || (ab[x] != 0.0f);
+      }
+      if (__any_sync(FULL, ne)) {
+#pragma unroll
+        for (int x = 0; x < DIM; ++x)
+#pragma unroll
+          for (int k = 0; k < NV; ++k) g2[x][k] = fmaf(P[k], e[x], g2[x][k]);
+      }
+      if (__any_sync(FULL, nb)) {
+#pragma unroll
+        for (int x = 0; x < DIM; ++x)
+#pragma unroll
+          for (int k = 0; k < NV; ++k) g2[x][k] = fmaf(Pd[k], vb[x], fmaf(Pdd[k], ab[x], g2[x][k]));
+      }
+    }
+    if (uvalid) {
+      float* pg = blk + L.PG + tq * NMAX * RS + i * RS;
+#pragma unroll
+      for (int x = 0; x < DIM; ++x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) pg[x * NP + k] = first_chunk ? g2[x][k] : pg[x * NP + k] + g2[x][k];
+    }
+  }
+}
+
+// Ring slot j holds (xi^{kb+j}, lambda^{kb+j}) in the checkpoint layout.
+__device__ __forceinline__ const float* ring_xi(const float* ring, int j, long long tot) {
+  return ring + (size_t)j * 2 * tot;
+}
+__device__ __forceinline__ const float* ring_lam(const float* ring, int j, long long tot) {
+  return ring + (size_t)j * 2 * tot + tot;
+}
+
+// Adjoint of iteration k (z^k -> z^{k+1}); XB, LB hold dL/dz^{k+1} on entry
+// and dL/dz^k on exit.
+template <int DIM, int NMAX>
+__device__ void adjoint_step(const Cta<DIM, NMAX>& c, const BwdArgs& A, int j) {
+  constexpr int RS = DIM * NP;
+  const Lay& L = c.L;
+  const ProblemConsts& pc = A.pc;
+  const int N = c.N, G = c.G, T = pc.T;
+  const long long tot = A.total_coefs;
+  const float rho = pc.rho;
+  const float invN = 1.0f / (float)N;
+  const float* xk = ring_xi(A.ring, j, tot);
+  const float* xk1 = ring_xi(A.ring, j + 1, tot);
+  const float* lk = ring_lam(A.ring, j, tot);
+  const float* lk1 = ring_lam(A.ring, j + 1, tot);
+  // (0) xi^k into C; fixed-point-residual term with respect to z^{k+1}
+  for (int v = c.tid; v < G * NMAX * RS; v += c.nthr) {
+    const int s = v / (NMAX * RS), rem = v % (NMAX * RS);
+    const int i = rem / RS, x = (rem / NP) % DIM, k = rem % NP;
+    float* blk = c.blk(s);
+    float val = 0.0f;
+    if (i < N && k < NV) {
+      const long long g = c.gidx(s, x, i, k);
+      val = xk[g];
+      if (A.g_fp) {
+        const float w2 = 2.0f * A.g_fp[c.gsample0 + s];
+        blk[L.XB + rem] = fmaf(w2, xk1[g] - val, blk[L.XB + rem]);
+        blk[L.LB + rem] = fmaf(w2, lk1[g] - lk[g], blk[L.LB + rem]);
+      }
+    }
+    blk[L.C + rem] = val;
+  }
+  __syncthreads();
+  // (1) robot mean of xb
+  for (int v = c.tid; v < G * DIM * NV; v += c.nthr) {
+    const int s = v / (DIM * NV), x = (v / NV) % DIM, k = v % NV;
+    float* blk = c.blk(s);
+    float sm = 0.0f;
+    for (int i = 0; i < N; ++i) sm += blk[L.XB + i * RS + x * NP + k];
+    blk[L.MC + x * NP + k] = sm * invN;
+  }
+  __syncthreads();
+  // (2) coefficient-space adjoint of the xi step and the lambda step
+  for (int v = c.tid; v < G * N * DIM; v += c.nthr) {
+    const int s = v / (N * DIM), i = (v / DIM) % N, x = v % DIM;
+    float* blk = c.blk(s);
+    const int o = i * RS + x * NP;
+    float xb[NV], mx[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) { xb[k] = blk[L.XB + o + k]; mx[k] = blk[L.MC + x * NP + k]; }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      float u1 = 0.0f, cw = 0.0f;
+#pragma unroll
+      for (int m = 0; m < NV; ++m) {
+        u1 = fmaf(c.OPS[OPS_S1 + m * NP + k], xb[m], u1);
+        u1 = fmaf(c.OPS[OPS_DS + m * NP + k], mx[m], u1);
+        cw = fmaf(c.OPS[OPS_W1 + m * NP + k], xb[m], cw);
+        cw = fmaf(c.OPS[OPS_DW + m * NP + k], mx[m], cw);
+      }
+      const float lt = blk[L.LB + o + k] + u1;
+      blk[L.U + o + k] = rho * (u1 + lt);
+      blk[L.GXB + o + k] += u1;
+      blk[L.LB + o + k] = lt;
+      blk[L.CW + o + k] = cw;
+    }
+  }
+  __syncthreads();
+  // (3) time-domain adjoint of the alpha / beta / d steps, in chunks
+  for (int t0 = 0; t0 < T; t0 += L.TC) {
+    const int TCc = min(L.TC, T - t0);
+    adj_pair_phase<DIM, NMAX>(c, pc, t0, TCc);
+    __syncthreads();
+    adj_contract_phase<DIM, NMAX>(c, pc, t0, TCc, t0 == 0);
+    __syncthreads();
+  }
+  // (4) dL/dxi^k = Wop^T xb + F^T Delta_bar; fixed-point term w.r.t. z^k
+  for (int v = c.tid; v < G * NMAX * RS; v += c.nthr) {
+    const int s = v / (NMAX * RS), rem = v % (NMAX * RS);
+    const int i = rem / RS, x = (rem / NP) % DIM, k = rem % NP;
+    if (i >= N || k >= NV) continue;
+    float* blk = c.blk(s);
+    float val = blk[L.CW + rem];
+    for (int q = 0; q < L.NQ; ++q) val += blk[L.PG + q * NMAX * RS + rem];
+    if (A.g_fp) {
+      const long long g = c.gidx(s, x, i, k);
+      const float w2 = 2.0f * A.g_fp[c.gsample0 + s];
+      val = fmaf(-w2, xk1[g] - xk[g], val);
+      blk[L.LB + rem] = fmaf(-w2, lk1[g] - lk[g], blk[L.LB + rem]);
+    }
+    blk[L.XB + rem] = val;
+  }
+  __syncthreads();
+}
+
+template <int DIM, int NMAX, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) fused_bwd_kernel(const __grid_constant__ BwdArgs A) {
+  constexpr int RS = DIM * NP;
+  extern __shared__ float4 smem4[];
+  float* sm = reinterpret_cast<float*>(smem4);
+  const ProblemConsts& pc = A.pc;
+  const int T = pc.T, K = pc.K;
+  const Cta<DIM, NMAX> c(A.sc, A.n_scenes, T, A.tc, A.nq, true, sm);
+  if (c.G <= 0) return;
+  const Lay& L = c.L;
+  const int N = c.N, G = c.G;
+  const long long tot = A.total_coefs;
+  prologue<DIM, NMAX>(c, T, A.basis, A.ops, A.start, A.goal, A.start_va, A.goal_va);
+  for (int v = c.tid; v < G * NMAX * RS; v += c.nthr) {
+    const int s = v / (NMAX * RS), rem = v % (NMAX * RS);
+    const int i = rem / RS, x = (rem / NP) % DIM, k = rem % NP;
+    float* blk = c.blk(s);
+    float xb = 0.0f, lb = 0.0f;
+    if (i < N && k < NV) {
+      const long long g = c.gidx(s, x, i, k);
+      xb = A.g_xi ? A.g_xi[g] : 0.0f;
+      lb = A.g_lam ? A.g_lam[g] : 0.0f;
+    }
+    blk[L.XB + rem] = xb;
+    blk[L.LB + rem] = lb;
+    blk[L.GXB + rem] = 0.0f;
+    blk[L.U + rem] = 0.0f;
+    blk[L.CW + rem] = 0.0f;
+  }
+  __syncthreads();
+  const int ck = A.ck_every;
+  const int nseg = (K + ck - 1) / ck;
+  float* ring = A.ring;
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int kb = seg * ck, ke = min(K, kb + ck);
+    const float* cx = A.ckpt + (size_t)seg * 2 * tot;
+    load_state<DIM, NMAX>(c, cx, cx + tot, nullptr);
+    __syncthreads();
+    store_state<DIM, NMAX>(c, ring, ring + tot, 0);
+    for (int k = kb; k < ke; ++k) {
+      fwd_iteration<DIM, NMAX>(c, pc, A.xi_bar, k, false, nullptr, 0, false);
+      float* slot = ring + (size_t)(k - kb + 1) * 2 * tot;
+      store_state<DIM, NMAX>(c, slot, slot + tot, 0);
+    }
+    __syncthreads();
+    for (int k = ke - 1; k >= kb; --k) adjoint_step<DIM, NMAX>(c, A, k - kb);
+  }
+  for (int v = c.tid; v < G * DIM * N * NV; v += c.nthr) {
+    const int s = v / (DIM * N * NV), rem = v % (DIM * N * NV);
+    const int x = rem / (N * NV), i = (rem / NV) % N, k = rem % NV;
+    const float* blk = c.blk(s);
+    const int o = i * RS + x * NP + k;
+    const long long g = c.coef0 + (long long)s * c.per_sample + rem;
+    if (A.gx0) A.gx0[g] = blk[L.XB + o];
+    if (A.gl0) A.gl0[g] = blk[L.LB + o];
+    if (A.gxb) A.gxb[g] = blk[L.GXB + o] + (A.xi0_is_xi_bar ? blk[L.XB + o] : 0.0f);
+  }
+}
+
+template <int DIM, int NMAX, int MAXT>
+cudaError_t launch_bwd_t(const BwdArgs& a, int n_ctas, int warps, size_t smem, cudaStream_t st) {
+  auto k = fused_bwd_kernel<DIM, NMAX, MAXT>;
+  if (warps * 32 > MAXT) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<n_ctas, warps * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace fused_impl
+}  // namespace sf

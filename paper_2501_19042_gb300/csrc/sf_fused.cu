@@ -8,14 +8,17 @@
 
 namespace sf {
 
-#define SF_DECL(D, NM) cudaError_t launch_fused_d##D##_n##NM(const FusedArgs&, const FusedLaunch&, cudaStream_t);
+#define SF_DECL(D, NM)                                                                                   \
+  cudaError_t launch_fused_d##D##_n##NM(const FusedArgs&, const FusedLaunch&, cudaStream_t);           \
+  cudaError_t launch_bwd_d##D##_n##NM(const FusedArgs&, const BwdLaunchArgs&, const FusedLaunch&,      \
+                                      cudaStream_t);
 SF_DECL(2, 8) SF_DECL(2, 16) SF_DECL(2, 32) SF_DECL(3, 8) SF_DECL(3, 16) SF_DECL(3, 32)
 #undef SF_DECL
 
 int fused_max_warps(int nmax) { return nmax == 32 ? 8 : 12; }
 
-size_t fused_smem_bytes(int dim, int nmax, int T, int gmax, int tc, int nq) {
-  const fused_impl::Lay L(dim, nmax, T, tc, nq);
+size_t fused_smem_bytes(int dim, int nmax, int T, int gmax, int tc, int nq, bool bwd) {
+  const fused_impl::Lay L(dim, nmax, T, tc, nq, bwd);
   return sizeof(float) * ((size_t)L.head + (size_t)gmax * L.SB);
 }
 
@@ -25,7 +28,7 @@ size_t fused_smem_bytes(int dim, int nmax, int T, int gmax, int tc, int nq) {
 // instructions per cycle; plus a charge per block-wide barrier. The CTA count
 // over the SM count gives the number of waves.
 FusedPlan plan_fused(int dim, int nmax, int T, const int* nr, const int* ns, int n_scenes, int num_sms,
-                     size_t smem_cap, int force_G, int force_warps, int force_tc) {
+                     size_t smem_cap, int force_G, int force_warps, int force_tc, bool bwd) {
   FusedPlan best;
   best.G = 0;
   best.cost = INFINITY;
@@ -51,7 +54,7 @@ FusedPlan plan_fused(int dim, int nmax, int T, const int* nr, const int* ns, int
         if (force_warps > 0 && w != force_warps) continue;
         const int nthr = 32 * w;
         const int nq = std::max(1, std::min(tc, nthr / std::max(1, G * Nbig)));
-        const size_t smem = fused_smem_bytes(dim, nmax, T, G, tc, nq);
+        const size_t smem = fused_smem_bytes(dim, nmax, T, G, tc, nq, bwd);
         if (smem > smem_cap) continue;
         const int real_nch = (T + tc - 1) / tc;
         const double rate = std::min(4.0, w / 2.0);
@@ -66,6 +69,20 @@ FusedPlan plan_fused(int dim, int nmax, int T, const int* nr, const int* ns, int
     }
   }
   return best;
+}
+
+cudaError_t launch_backward(const FusedArgs& a, const BwdLaunchArgs& b, const FusedLaunch& l, cudaStream_t st) {
+  const int dim = a.pc.dim;
+  if (dim == 3) {
+    if (l.nmax == 8) return launch_bwd_d3_n8(a, b, l, st);
+    if (l.nmax == 16) return launch_bwd_d3_n16(a, b, l, st);
+    if (l.nmax == 32) return launch_bwd_d3_n32(a, b, l, st);
+  } else if (dim == 2) {
+    if (l.nmax == 8) return launch_bwd_d2_n8(a, b, l, st);
+    if (l.nmax == 16) return launch_bwd_d2_n16(a, b, l, st);
+    if (l.nmax == 32) return launch_bwd_d2_n32(a, b, l, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_fused(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st) {

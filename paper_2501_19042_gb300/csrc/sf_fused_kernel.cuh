@@ -39,9 +39,9 @@ constexpr unsigned FULL = 0xffffffffu;
 // RS2 [T] (pair residual per t); RSB [NQ][NMAX] (ball residual partials).
 struct Lay {
   int RS, EP, TC, NQ, T, nmax, dim;
-  int C, LAM, PG, MC, MR, EB, RS2, RSB, SB;
+  int C, LAM, PG, MC, MR, EB, RS2, RSB, FPP, FPR, XB, LB, GXB, U, CW, SB;
   int head;
-  __host__ __device__ Lay(int dim_, int nmax_, int T_, int TC_, int NQ_) {
+  __host__ __device__ Lay(int dim_, int nmax_, int T_, int TC_, int NQ_, bool bwd = false) {
     dim = dim_; nmax = nmax_; T = T_; TC = TC_; NQ = NQ_;
     RS = dim * NP;
     EP = nmax * dim + 1;
@@ -55,7 +55,14 @@ struct Lay {
     if (eb < nmax * RS) eb = nmax * RS;
     RS2 = EB + ((eb + 3) / 4) * 4;
     RSB = RS2 + T;
-    SB = ((RSB + NQ * nmax + 3) / 4) * 4;
+    FPP = RSB + NQ * nmax;
+    FPR = FPP + dim * NV + nmax * dim;
+    XB = ((FPR + 1 + 3) / 4) * 4;
+    LB = XB + (bwd ? nmax * RS : 0);
+    GXB = LB + (bwd ? nmax * RS : 0);
+    U = GXB + (bwd ? nmax * RS : 0);
+    CW = U + (bwd ? nmax * RS : 0);
+    SB = CW + (bwd ? nmax * RS : 0);
     head = T * BASIS_ROW + 4 * NV * NP + nmax * RS;
   }
 };
@@ -200,6 +207,8 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
 }
 
 // Contraction phase of one chunk: F^T of the residual per (sample, robot).
+// Each 11-term group P[t] E, Pd[t] qv, Pdd[t] qa is skipped when it is zero
+// on every lane of the warp (inactive rows contribute exactly 0).
 template <int DIM>
 __device__ void contract_phase(float* SAMP, const Lay& L, const float* BASIS, int G, int N, int t0, int TCc,
                                bool first_chunk, const ProblemConsts& pc, bool want_res, int tid, int nthr) {
@@ -207,12 +216,19 @@ __device__ void contract_phase(float* SAMP, const Lay& L, const float* BASIS, in
   const int NQ = L.NQ;
   const int nB = NQ * G * N;
   const int TQ = (TCc + NQ - 1) / NQ;
-  for (int u = tid; u < nB; u += nthr) {
-    const int i = u % N;
-    const int s = (u / N) % G;
-    const int tq = u / (N * G);
+  const int lane = tid & 31;
+  for (int base = tid - lane; base < nB; base += nthr) {
+    const int u = base + lane;
+    const bool uvalid = u < nB;
+    const int uu = uvalid ? u : 0;
+    const int i = uu % N;
+    const int s = (uu / N) % G;
+    const int tq = uu / (N * G);
     const int ta = tq * TQ;
-    const int tb = min(ta + TQ, TCc);
+    const int trip = uvalid ? max(0, min(ta + TQ, TCc) - ta) : 0;
+    int wtrip = trip;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) wtrip = max(wtrip, __shfl_xor_sync(FULL, wtrip, o));
     float* blk = SAMP + (size_t)s * L.SB;
     float c[DIM][NV], g[DIM][NV];
 #pragma unroll
@@ -222,41 +238,67 @@ __device__ void contract_phase(float* SAMP, const Lay& L, const float* BASIS, in
       for (int k = 0; k < NV; ++k) g[x][k] = 0.0f;
     }
     float rb = 0.0f;
-    for (int tl = ta; tl < tb; ++tl) {
+    for (int step = 0; step < wtrip; ++step) {
+      const bool live = step < trip;
+      const int tl = live ? ta + step : ta;
       const float* brow = BASIS + (size_t)(t0 + tl) * BASIS_ROW;
-      float P[NV], Pd[NV], Pdd[NV];
-      row_from(brow, P);
+      float Pd[NV], Pdd[NV];
       row_from(brow + NP, Pd);
       row_from(brow + 2 * NP, Pdd);
       const float* eb = blk + L.EB + tl * L.EP + i * DIM;
       float e[DIM], qv[DIM], qa[DIM];
+      bool ne = false;
 #pragma unroll
-      for (int x = 0; x < DIM; ++x) { e[x] = eb[x]; qv[x] = 0.0f; qa[x] = 0.0f; }
+      for (int x = 0; x < DIM; ++x) {
+        e[x] = live ? eb[x] : 0.0f;
+        ne |= e[x] != 0.0f;
+        qv[x] = 0.0f;
+        qa[x] = 0.0f;
+      }
+      float rl = 0.0f;
       if (pc.use_v) {
         float v[DIM];
 #pragma unroll
         for (int x = 0; x < DIM; ++x) v[x] = dot_reg(Pd, c[x]);
-        ball_residual<DIM>(v, pc.v_max, qv, rb);
+        ball_residual<DIM>(v, pc.v_max, qv, rl);
       }
       if (pc.use_a) {
         float a[DIM];
 #pragma unroll
         for (int x = 0; x < DIM; ++x) a[x] = dot_reg(Pdd, c[x]);
-        ball_residual<DIM>(a, pc.a_max, qa, rb);
+        ball_residual<DIM>(a, pc.a_max, qa, rl);
       }
+      if (live) rb += rl;
+      if (__any_sync(FULL, ne)) {
+        float P[NV];
+        row_from(brow, P);
+#pragma unroll
+        for (int x = 0; x < DIM; ++x)
+#pragma unroll
+          for (int k = 0; k < NV; ++k) g[x][k] = fmaf(P[k], e[x], g[x][k]);
+      }
+      if (__any_sync(FULL, live && rl > 0.0f)) {
+#pragma unroll
+        for (int x = 0; x < DIM; ++x)
+#pragma unroll
+          for (int k = 0; k < NV; ++k) {
+            float acc = g[x][k];
+            if (pc.use_v) acc = fmaf(Pd[k], live ? qv[x] : 0.0f, acc);
+            if (pc.use_a) acc = fmaf(Pdd[k], live ? qa[x] : 0.0f, acc);
+            g[x][k] = acc;
+          }
+      }
+    }
+    if (uvalid) {
+      float* pg = blk + L.PG + tq * L.nmax * RS + i * RS;
 #pragma unroll
       for (int x = 0; x < DIM; ++x)
 #pragma unroll
-        for (int k = 0; k < NV; ++k) g[x][k] = fmaf(P[k], e[x], fmaf(Pd[k], qv[x], fmaf(Pdd[k], qa[x], g[x][k])));
-    }
-    float* pg = blk + L.PG + tq * L.nmax * RS + i * RS;
-#pragma unroll
-    for (int x = 0; x < DIM; ++x)
-#pragma unroll
-      for (int k = 0; k < NV; ++k) pg[x * NP + k] = first_chunk ? g[x][k] : pg[x * NP + k] + g[x][k];
-    if (want_res) {
-      float* r = blk + L.RSB + tq * L.nmax + i;
-      *r = first_chunk ? rb : *r + rb;
+        for (int k = 0; k < NV; ++k) pg[x * NP + k] = first_chunk ? g[x][k] : pg[x * NP + k] + g[x][k];
+      if (want_res) {
+        float* r = blk + L.RSB + tq * L.nmax + i;
+        *r = first_chunk ? rb : *r + rb;
+      }
     }
   }
 }
@@ -355,61 +397,72 @@ __device__ void residual_phase(float* SAMP, const Lay& L, const float* BASIS, in
   }
 }
 
-template <int DIM, int NMAX, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constant__ FusedArgs A) {
+// Per-CTA context: which scene and samples the CTA owns and where things
+// live in shared memory.
+template <int DIM, int NMAX>
+struct Cta {
+  Lay L;
+  int N, G, robot_off, gsample0;
+  long long per_sample, coef0;
+  float *BASIS, *OPS, *BETA, *SAMP;
+  int tid, nthr, warp, lane, nwarps;
+  __device__ Cta(const SceneDesc* sc, int n_scenes, int T, int tc, int nq, bool bwd, float* sm)
+      : L(DIM, NMAX, T, tc, nq, bwd) {
+    int sidx = 0;
+    for (int q = 1; q < n_scenes; ++q) {
+      if (sc[q].cta_begin <= (int)blockIdx.x) sidx = q;
+      else break;
+    }
+    N = sc[sidx].N;
+    const int Gs = sc[sidx].G;
+    const int s_first = ((int)blockIdx.x - sc[sidx].cta_begin) * Gs;
+    G = min(Gs, sc[sidx].S - s_first);
+    robot_off = sc[sidx].robot_off;
+    gsample0 = sc[sidx].sample_off + s_first;
+    per_sample = (long long)DIM * N * NV;
+    coef0 = sc[sidx].coef_off + (long long)s_first * per_sample;
+    BASIS = sm;
+    OPS = sm + T * BASIS_ROW;
+    BETA = OPS + 4 * NV * NP;
+    SAMP = sm + L.head;
+    tid = threadIdx.x;
+    nthr = blockDim.x;
+    warp = tid >> 5;
+    lane = tid & 31;
+    nwarps = nthr >> 5;
+  }
+  // global index of coefficient (s, x, i, k) and shared offset of its row
+  __device__ long long gidx(int s, int x, int i, int k) const {
+    return coef0 + s * per_sample + ((long long)x * N + i) * NV + k;
+  }
+  __device__ float* blk(int s) const { return SAMP + (size_t)s * L.SB; }
+};
+
+// Basis table, operators of this N and beta_i = R1 b_i + (R0 - R1) bbar.
+template <int DIM, int NMAX>
+__device__ void prologue(const Cta<DIM, NMAX>& c, int T, const float4* basis, const float* ops,
+                         const float* start, const float* goal, const float* start_va, const float* goal_va) {
   constexpr int RS = DIM * NP;
-  extern __shared__ float4 smem4[];
-  float* sm = reinterpret_cast<float*>(smem4);
-  const ProblemConsts& pc = A.pc;
-  const int T = pc.T;
-  const Lay L(DIM, NMAX, T, A.tc, A.nq);
-
-  int sidx = 0;
-  for (int q = 1; q < A.n_scenes; ++q) {
-    if (A.sc[q].cta_begin <= (int)blockIdx.x) sidx = q;
-    else break;
-  }
-  const int N = A.sc[sidx].N;
-  const int Gs = A.sc[sidx].G;
-  const int S = A.sc[sidx].S;
-  const int s_first = ((int)blockIdx.x - A.sc[sidx].cta_begin) * Gs;
-  const int G = min(Gs, S - s_first);
-  const int robot_off = A.sc[sidx].robot_off;
-  const int gsample0 = A.sc[sidx].sample_off + s_first;
-  const long long per_sample = (long long)DIM * N * NV;
-  const long long coef0 = A.sc[sidx].coef_off + (long long)s_first * per_sample;
-  if (G <= 0) return;
-
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
-  float* BASIS = sm;
-  float* OPS = sm + T * BASIS_ROW;
-  float* BETA = OPS + 4 * NV * NP;
-  float* SAMP = sm + L.head;
-  const bool want_res = A.hist != nullptr;
-
-  // ---- prologue: basis, operators of this N, beta, per-sample state
-  {
-    const float4* b4 = A.basis;
-    float4* s4 = reinterpret_cast<float4*>(BASIS);
-    for (int v = tid; v < T * 9; v += nthr) s4[v] = b4[v];
-  }
-  const float* gops = A.ops + (size_t)N * OPS_STRIDE;
-  for (int v = tid; v < 4 * NV * NP; v += nthr) OPS[v] = gops[v];
-  for (int v = tid; v < NMAX * RS; v += nthr) {
+  const float4* b4 = basis;
+  float4* s4 = reinterpret_cast<float4*>(c.BASIS);
+  for (int v = c.tid; v < T * 9; v += c.nthr) s4[v] = b4[v];
+  const float* gops = ops + (size_t)c.N * OPS_STRIDE;
+  for (int v = c.tid; v < 4 * NV * NP; v += c.nthr) c.OPS[v] = gops[v];
+  const int N = c.N;
+  for (int v = c.tid; v < NMAX * RS; v += c.nthr) {
     const int i = v / RS, x = (v / NP) % DIM, k = v % NP;
     float beta = 0.0f;
     if (i < N && k < NV) {
       float bi[6] = {0, 0, 0, 0, 0, 0}, bm[6] = {0, 0, 0, 0, 0, 0};
       for (int j = 0; j < N; ++j) {
-        const int rr = robot_off + j;
+        const int rr = c.robot_off + j;
         float bj[6];
-        bj[0] = A.start[rr * DIM + x];
-        bj[1] = A.start_va ? A.start_va[(rr * 2 + 0) * DIM + x] : 0.0f;
-        bj[2] = A.start_va ? A.start_va[(rr * 2 + 1) * DIM + x] : 0.0f;
-        bj[3] = A.goal[rr * DIM + x];
-        bj[4] = A.goal_va ? A.goal_va[(rr * 2 + 0) * DIM + x] : 0.0f;
-        bj[5] = A.goal_va ? A.goal_va[(rr * 2 + 1) * DIM + x] : 0.0f;
+        bj[0] = start[rr * DIM + x];
+        bj[1] = start_va ? start_va[(rr * 2 + 0) * DIM + x] : 0.0f;
+        bj[2] = start_va ? start_va[(rr * 2 + 1) * DIM + x] : 0.0f;
+        bj[3] = goal[rr * DIM + x];
+        bj[4] = goal_va ? goal_va[(rr * 2 + 0) * DIM + x] : 0.0f;
+        bj[5] = goal_va ? goal_va[(rr * 2 + 1) * DIM + x] : 0.0f;
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
           bm[q] += bj[q];
@@ -423,133 +476,201 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
         beta = fmaf(r1, bi[q], fmaf(r0 - r1, bm[q] * invN, beta));
       }
     }
-    BETA[v] = beta;
+    c.BETA[v] = beta;
   }
-  for (int v = tid; v < G * NMAX * RS; v += nthr) {
+}
+
+// Loads (xi, lambda) of every sample into C, LAM (rows beyond N and the
+// padding column are zero) and clears the partials.
+template <int DIM, int NMAX>
+__device__ void load_state(const Cta<DIM, NMAX>& c, const float* xi, const float* lam, const float* fallback_xi) {
+  constexpr int RS = DIM * NP;
+  for (int v = c.tid; v < c.G * NMAX * RS; v += c.nthr) {
     const int s = v / (NMAX * RS), rem = v % (NMAX * RS);
     const int i = rem / RS, x = (rem / NP) % DIM, k = rem % NP;
-    float* blk = SAMP + (size_t)s * L.SB;
-    float c = 0.0f, l = 0.0f;
-    if (i < N && k < NV) {
-      const long long g = coef0 + s * per_sample + ((long long)x * N + i) * NV + k;
-      c = A.xi0 ? A.xi0[g] : A.xi_bar[g];
-      l = A.lam0 ? A.lam0[g] : 0.0f;
+    float* b = c.blk(s);
+    float cv = 0.0f, l = 0.0f;
+    if (i < c.N && k < NV) {
+      const long long g = c.gidx(s, x, i, k);
+      cv = xi ? xi[g] : fallback_xi[g];
+      l = lam ? lam[g] : 0.0f;
     }
-    blk[L.C + rem] = c;
-    blk[L.LAM + rem] = l;
-    for (int q = 0; q < L.NQ; ++q) blk[L.PG + q * NMAX * RS + rem] = 0.0f;
+    b[c.L.C + rem] = cv;
+    b[c.L.LAM + rem] = l;
+    for (int q = 0; q < c.L.NQ; ++q) b[c.L.PG + q * NMAX * RS + rem] = 0.0f;
   }
-  __syncthreads();
+}
 
+// Copies C, LAM of every sample to global memory in the [dim][N][nvar] layout.
+template <int DIM, int NMAX>
+__device__ void store_state(const Cta<DIM, NMAX>& c, float* xi_dst, float* lam_dst, long long base) {
+  constexpr int RS = DIM * NP;
+  const int N = c.N;
+  for (int v = c.tid; v < c.G * DIM * N * NV; v += c.nthr) {
+    const int s = v / (DIM * N * NV), rem = v % (DIM * N * NV);
+    const int x = rem / (N * NV), i = (rem / NV) % N, k = rem % NV;
+    const float* b = c.blk(s);
+    const int o = i * RS + x * NP + k;
+    const long long g = base + c.coef0 + (long long)s * c.per_sample + rem;
+    xi_dst[g] = b[c.L.C + o];
+    lam_dst[g] = b[c.L.LAM + o];
+  }
+}
+
+// One iteration of f_FP on every sample of the CTA (time chunks, then the
+// lambda step and the xi step). keep_prev stores xi^k in the EB region for
+// the final residual. fp (when set) adds ||z^{k+1} - z^k||^2 per sample to FPR.
+template <int DIM, int NMAX>
+__device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, const float* xi_bar, int it,
+                              bool keep_prev, float* hist, int total_samples, bool fp) {
+  constexpr int RS = DIM * NP;
+  const Lay& L = c.L;
+  const int T = pc.T, N = c.N, G = c.G, TC = L.TC;
+  const bool want_res = hist != nullptr;
   const float rho = pc.rho;
   const float invN = 1.0f / (float)N;
-  const int TC = L.TC;
+  for (int t0 = 0; t0 < T; t0 += TC) {
+    const int TCc = min(TC, T - t0);
+    pair_phase<DIM, NMAX>(c.SAMP, L, c.BASIS, G, N, t0, TCc, pc, want_res, c.warp, c.nwarps, c.lane);
+    __syncthreads();
+    contract_phase<DIM>(c.SAMP, L, c.BASIS, G, N, t0, TCc, t0 == 0, pc, want_res, c.tid, c.nthr);
+    __syncthreads();
+  }
+  // ---- solve phase 1: lambda step, r, robot means (and the history entry)
+  for (int v = c.tid; v < G * DIM * NV; v += c.nthr) {
+    const int s = v / (DIM * NV), x = (v / NV) % DIM, k = v % NV;
+    float* blk = c.blk(s);
+    float sr = 0.0f, sc = 0.0f, dl2 = 0.0f;
+    for (int i = 0; i < N; ++i) {
+      const int o = i * RS + x * NP + k;
+      float g = blk[L.PG + o];
+      for (int q = 1; q < L.NQ; ++q) g += blk[L.PG + q * NMAX * RS + o];
+      const float lam = fmaf(rho, g, blk[L.LAM + o]);
+      dl2 = fmaf(lam - blk[L.LAM + o], lam - blk[L.LAM + o], dl2);
+      blk[L.LAM + o] = lam;
+      const float r = fmaf(rho, g, lam) + xi_bar[c.gidx(s, x, i, k)];
+      blk[L.PG + o] = r;
+      sr += r;
+      sc += blk[L.C + o];
+    }
+    blk[L.MR + x * NP + k] = sr * invN;
+    blk[L.MC + x * NP + k] = sc * invN;
+    if (fp) blk[L.FPP + x * NV + k] = dl2;
+    if (want_res && x == 0 && k == 0) {
+      float r2 = 0.0f;
+      for (int t = 0; t < T; ++t) r2 += blk[L.RS2 + t];
+      for (int q = 0; q < L.NQ; ++q)
+        for (int i = 0; i < N; ++i) r2 += blk[L.RSB + q * NMAX + i];
+      hist[(size_t)it * total_samples + c.gsample0 + s] = sqrtf(r2);
+    }
+  }
+  __syncthreads();
+  // ---- solve phase 2: xi step
+  for (int v = c.tid; v < G * N * DIM; v += c.nthr) {
+    const int s = v / (N * DIM), i = (v / DIM) % N, x = v % DIM;
+    float* blk = c.blk(s);
+    const int o = i * RS + x * NP;
+    float cc[NP], r[NP], cm[NP], rm[NP];
+    const float4* c4 = reinterpret_cast<const float4*>(blk + L.C + o);
+    const float4* r4 = reinterpret_cast<const float4*>(blk + L.PG + o);
+    const float4* cm4 = reinterpret_cast<const float4*>(blk + L.MC + x * NP);
+    const float4* rm4 = reinterpret_cast<const float4*>(blk + L.MR + x * NP);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float4 a = c4[q], b = r4[q], e = cm4[q], f = rm4[q];
+      cc[4 * q] = a.x; cc[4 * q + 1] = a.y; cc[4 * q + 2] = a.z; cc[4 * q + 3] = a.w;
+      r[4 * q] = b.x; r[4 * q + 1] = b.y; r[4 * q + 2] = b.z; r[4 * q + 3] = b.w;
+      cm[4 * q] = e.x; cm[4 * q + 1] = e.y; cm[4 * q + 2] = e.z; cm[4 * q + 3] = e.w;
+      rm[4 * q] = f.x; rm[4 * q + 1] = f.y; rm[4 * q + 2] = f.z; rm[4 * q + 3] = f.w;
+    }
+    float out[NP];
+    float dx2 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      float acc = c.BETA[o + k];
+#pragma unroll
+      for (int m = 0; m < NV; ++m) {
+        acc = fmaf(c.OPS[OPS_W1 + k * NP + m], cc[m], acc);
+        acc = fmaf(c.OPS[OPS_S1 + k * NP + m], r[m], acc);
+        acc = fmaf(c.OPS[OPS_DW + k * NP + m], cm[m], acc);
+        acc = fmaf(c.OPS[OPS_DS + k * NP + m], rm[m], acc);
+      }
+      out[k] = acc;
+      dx2 = fmaf(acc - cc[k], acc - cc[k], dx2);
+    }
+    out[NV] = 0.0f;
+    float4* o4 = reinterpret_cast<float4*>(blk + L.C + o);
+    float4* p4 = reinterpret_cast<float4*>(blk + L.EB + o);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if (keep_prev) p4[q] = make_float4(cc[4 * q], cc[4 * q + 1], cc[4 * q + 2], cc[4 * q + 3]);
+      o4[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+    }
+    if (fp) blk[L.FPP + DIM * NV + i * DIM + x] = dx2;
+  }
+  __syncthreads();
+  if (fp) {
+    for (int s = c.tid; s < G; s += c.nthr) {
+      float* blk = c.blk(s);
+      float acc = 0.0f;
+      for (int q = 0; q < DIM * NV; ++q) acc += blk[L.FPP + q];
+      for (int q = 0; q < N * DIM; ++q) acc += blk[L.FPP + DIM * NV + q];
+      blk[L.FPR] += acc;
+    }
+    // FPR is read only after the last iteration's barrier
+  }
+}
+
+// Writes checkpoint `ck` = (xi, lambda) of every sample: layout
+// [ck][2][total coefficients] (xi first, then lambda).
+template <int DIM, int NMAX>
+__device__ void write_checkpoint(const Cta<DIM, NMAX>& c, float* ckpt, int ck, long long total_coefs) {
+  float* base = ckpt + (size_t)ck * 2 * total_coefs;
+  store_state<DIM, NMAX>(c, base, base + total_coefs, 0);
+}
+
+template <int DIM, int NMAX, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constant__ FusedArgs A) {
+  extern __shared__ float4 smem4[];
+  float* sm = reinterpret_cast<float*>(smem4);
+  const ProblemConsts& pc = A.pc;
+  const int T = pc.T;
+  const Cta<DIM, NMAX> c(A.sc, A.n_scenes, T, A.tc, A.nq, false, sm);
+  if (c.G <= 0) return;
+  const Lay& L = c.L;
+  const int N = c.N, G = c.G;
+  const bool fp = A.fp_res2 != nullptr;
+
+  prologue<DIM, NMAX>(c, T, A.basis, A.ops, A.start, A.goal, A.start_va, A.goal_va);
+  load_state<DIM, NMAX>(c, A.xi0, A.lam0, A.xi_bar);
+  for (int s = c.tid; s < G; s += c.nthr) c.blk(s)[L.FPR] = 0.0f;
+  __syncthreads();
+
   for (int it = 0; it < pc.K; ++it) {
-    for (int t0 = 0; t0 < T; t0 += TC) {
-      const int TCc = min(TC, T - t0);
-      pair_phase<DIM, NMAX>(SAMP, L, BASIS, G, N, t0, TCc, pc, want_res, warp, nwarps, lane);
-      __syncthreads();
-      contract_phase<DIM>(SAMP, L, BASIS, G, N, t0, TCc, t0 == 0, pc, want_res, tid, nthr);
-      __syncthreads();
-    }
-    // ---- solve phase 1: lambda step, r, robot means (and the history entry)
-    for (int v = tid; v < G * DIM * NV; v += nthr) {
-      const int s = v / (DIM * NV), x = (v / NV) % DIM, k = v % NV;
-      float* blk = SAMP + (size_t)s * L.SB;
-      float sr = 0.0f, sc = 0.0f;
-      for (int i = 0; i < N; ++i) {
-        const int o = i * RS + x * NP + k;
-        float g = blk[L.PG + o];
-        for (int q = 1; q < L.NQ; ++q) g += blk[L.PG + q * NMAX * RS + o];
-        const float lam = fmaf(rho, g, blk[L.LAM + o]);
-        blk[L.LAM + o] = lam;
-        const float xb = A.xi_bar[coef0 + s * per_sample + ((long long)x * N + i) * NV + k];
-        const float r = fmaf(rho, g, lam) + xb;
-        blk[L.PG + o] = r;
-        sr += r;
-        sc += blk[L.C + o];
-      }
-      blk[L.MR + x * NP + k] = sr * invN;
-      blk[L.MC + x * NP + k] = sc * invN;
-      if (want_res && x == 0 && k == 0) {
-        float r2 = 0.0f;
-        for (int t = 0; t < T; ++t) r2 += blk[L.RS2 + t];
-        for (int q = 0; q < L.NQ; ++q)
-          for (int i = 0; i < N; ++i) r2 += blk[L.RSB + q * NMAX + i];
-        A.hist[(size_t)it * A.total_samples + gsample0 + s] = sqrtf(r2);
-      }
-    }
-    __syncthreads();
-    // ---- solve phase 2: xi step
-    const bool last = (it == pc.K - 1);
-    for (int v = tid; v < G * N * DIM; v += nthr) {
-      const int s = v / (N * DIM), i = (v / DIM) % N, x = v % DIM;
-      float* blk = SAMP + (size_t)s * L.SB;
-      const int o = i * RS + x * NP;
-      float c[NP], r[NP], cm[NP], rm[NP];
-      const float4* c4 = reinterpret_cast<const float4*>(blk + L.C + o);
-      const float4* r4 = reinterpret_cast<const float4*>(blk + L.PG + o);
-      const float4* cm4 = reinterpret_cast<const float4*>(blk + L.MC + x * NP);
-      const float4* rm4 = reinterpret_cast<const float4*>(blk + L.MR + x * NP);
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const float4 a = c4[q], b = r4[q], e = cm4[q], f = rm4[q];
-        c[4 * q] = a.x; c[4 * q + 1] = a.y; c[4 * q + 2] = a.z; c[4 * q + 3] = a.w;
-        r[4 * q] = b.x; r[4 * q + 1] = b.y; r[4 * q + 2] = b.z; r[4 * q + 3] = b.w;
-        cm[4 * q] = e.x; cm[4 * q + 1] = e.y; cm[4 * q + 2] = e.z; cm[4 * q + 3] = e.w;
-        rm[4 * q] = f.x; rm[4 * q + 1] = f.y; rm[4 * q + 2] = f.z; rm[4 * q + 3] = f.w;
-      }
-      float out[NP];
-#pragma unroll
-      for (int k = 0; k < NV; ++k) {
-        float acc = BETA[o + k];
-#pragma unroll
-        for (int m = 0; m < NV; ++m) {
-          acc = fmaf(OPS[OPS_W1 + k * NP + m], c[m], acc);
-          acc = fmaf(OPS[OPS_S1 + k * NP + m], r[m], acc);
-          acc = fmaf(OPS[OPS_DW + k * NP + m], cm[m], acc);
-          acc = fmaf(OPS[OPS_DS + k * NP + m], rm[m], acc);
-        }
-        out[k] = acc;
-      }
-      out[NV] = 0.0f;
-      float4* o4 = reinterpret_cast<float4*>(blk + L.C + o);
-      float4* p4 = reinterpret_cast<float4*>(blk + L.EB + o);
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        if (last) p4[q] = make_float4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]);
-        o4[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
-      }
-    }
-    __syncthreads();
+    if (A.ckpt && it % A.ck_every == 0) write_checkpoint<DIM, NMAX>(c, A.ckpt, it / A.ck_every, A.total_coefs);
+    fwd_iteration<DIM, NMAX>(c, pc, A.xi_bar, it, it == pc.K - 1, A.hist, A.total_samples, fp);
   }
 
   // ---- final residual, Eq. (primal_residual); robot rows beyond N of the
   // xi^{K-1} copy are zero-filled first
-  for (int v = tid; v < G * NMAX * RS; v += nthr) {
+  constexpr int RS = DIM * NP;
+  for (int v = c.tid; v < G * NMAX * RS; v += c.nthr) {
     const int s = v / (NMAX * RS), rem = v % (NMAX * RS);
-    if (rem / RS >= N) SAMP[(size_t)s * L.SB + L.EB + rem] = 0.0f;
+    if (rem / RS >= N) c.blk(s)[L.EB + rem] = 0.0f;
   }
   __syncthreads();
-  residual_phase<DIM, NMAX>(SAMP, L, BASIS, G, N, T, pc, warp, nwarps, lane);
+  residual_phase<DIM, NMAX>(c.SAMP, L, c.BASIS, G, N, T, pc, c.warp, c.nwarps, c.lane);
   __syncthreads();
-  for (int s = tid; s < G; s += nthr) {
-    const float* blk = SAMP + (size_t)s * L.SB;
+  for (int s = c.tid; s < G; s += c.nthr) {
+    const float* blk = c.blk(s);
     float r2 = 0.0f;
     for (int t = 0; t < T; ++t) r2 += blk[L.RS2 + t];
     const float r = sqrtf(r2);
-    A.resid_out[gsample0 + s] = r;
+    A.resid_out[c.gsample0 + s] = r;
+    if (fp) A.fp_res2[c.gsample0 + s] = blk[L.FPR];
     if (!isfinite(r)) atomicOr(A.status, ST_NONFINITE);
   }
-  for (int v = tid; v < G * DIM * N * NV; v += nthr) {
-    const int s = v / (DIM * N * NV), rem = v % (DIM * N * NV);
-    const int x = rem / (N * NV), i = (rem / NV) % N, k = rem % NV;
-    const float* blk = SAMP + (size_t)s * L.SB;
-    const int o = i * RS + x * NP + k;
-    const long long g = coef0 + (long long)s * per_sample + rem;
-    A.xi_out[g] = blk[L.C + o];
-    A.lam_out[g] = blk[L.LAM + o];
-  }
+  store_state<DIM, NMAX>(c, A.xi_out, A.lam_out, 0);
 }
 
 template <int DIM, int NMAX, int MAXT>

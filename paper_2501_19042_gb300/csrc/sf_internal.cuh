@@ -79,6 +79,10 @@ struct FusedArgs {
   int* status;
   int tc;                  // time steps per chunk
   int nq;                  // time ranges per chunk in the contraction phase
+  float* ckpt;             // [n_ck][2][total_coefs] or null
+  int ck_every;            // checkpoint period
+  long long total_coefs;
+  float* fp_res2;          // [total samples] sum_k ||z^{k+1} - z^k||^2, or null
   SceneDesc sc[MAX_SCENES_PER_LAUNCH];
 };
 
@@ -139,7 +143,7 @@ struct FusedLaunch {
   int tc, nq;   // time chunk, contraction ranges
   size_t smem;  // dynamic shared memory bytes
 };
-size_t fused_smem_bytes(int dim, int nmax, int T, int gmax, int tc, int nq);
+size_t fused_smem_bytes(int dim, int nmax, int T, int gmax, int tc, int nq, bool bwd = false);
 cudaError_t launch_fused(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st);
 int fused_max_warps(int nmax);
 
@@ -152,7 +156,25 @@ struct FusedPlan {
   double cost;
 };
 FusedPlan plan_fused(int dim, int nmax, int T, const int* n_robots, const int* n_samples, int n_scenes,
-                     int num_sms, size_t smem_cap, int force_G, int force_warps, int force_tc);
+                     int num_sms, size_t smem_cap, int force_G, int force_warps, int force_tc,
+                     bool bwd = false);
+
+// Backward launch: everything the adjoint kernel needs besides the scene
+// table (which it shares with FusedArgs).
+struct BwdLaunchArgs {
+  const float* ckpt;
+  int ck_every;
+  long long total_coefs;
+  float* ring;
+  const float* g_xi;
+  const float* g_lam;
+  const float* g_fp;
+  float* gx0;
+  float* gl0;
+  float* gxb;
+  int xi0_is_xi_bar;
+};
+cudaError_t launch_backward(const FusedArgs& a, const BwdLaunchArgs& b, const FusedLaunch& l, cudaStream_t st);
 
 struct PlainArgs {
   ProblemConsts pc;

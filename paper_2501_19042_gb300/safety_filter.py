@@ -189,6 +189,52 @@ class SafetyFilter:
         nat.check(self._lib, self._h, self._lib.sf_get_launch_shape(self._h, out))
         return {"G": out[0], "warps": out[1], "tc": out[2], "nq": out[3]}
 
+    def checkpoint_bytes(self, xi_bar, start, goal, K, n_robots=None, n_samples=None) -> int:
+        b, _keep, _, _ = self._batch(xi_bar, start, goal, n_robots, n_samples, None, None)
+        return int(self._lib.sf_checkpoint_bytes(self._h, C.byref(b), int(K)))
+
+    def project_train(self, xi_bar, start, goal, K, n_robots=None, n_samples=None, xi0=None, lam0=None,
+                      start_va=None, goal_va=None, stream=None):
+        """``sf_project_train``: forward that also returns the fixed-point
+        residual sum per sample and the checkpoints for the backward."""
+        b, keep, ncoef, nsamp = self._batch(xi_bar, start, goal, n_robots, n_samples, start_va, goal_va)
+        nck = int(self._lib.sf_checkpoint_bytes(self._h, C.byref(b), int(K)))
+        ckpt = torch.empty(nck // 4, dtype=torch.float32, device=self.device)
+        out = ProjectResult(xi=torch.empty_like(xi_bar), lam=torch.empty_like(xi_bar),
+                            residual=torch.empty(nsamp, dtype=torch.float32, device=self.device))
+        fp = torch.empty(nsamp, dtype=torch.float32, device=self.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        code = self._lib.sf_project_train(self._h, C.c_void_p(stream.cuda_stream), C.byref(b), int(K), _ptr(xi0),
+                                          _ptr(lam0), _ptr(out.xi), _ptr(out.lam), _ptr(out.residual), _ptr(fp),
+                                          _ptr(ckpt))
+        del keep
+        nat.check(self._lib, self._h, code)
+        return out, fp, ckpt
+
+    def project_backward(self, xi_bar, start, goal, K, ckpt, grad_xi=None, grad_lam=None, grad_fp=None,
+                         init_from_xi_bar=True, n_robots=None, n_samples=None, start_va=None, goal_va=None,
+                         stream=None):
+        """``sf_project_backward``: returns (dL/dxi0, dL/dlambda0, dL/dxi_bar)."""
+        b, keep, ncoef, nsamp = self._batch(xi_bar, start, goal, n_robots, n_samples, start_va, goal_va)
+        nws = int(self._lib.sf_backward_workspace_bytes(self._h, C.byref(b), int(K)))
+        ws = torch.empty(max(nws, 4) // 4, dtype=torch.float32, device=self.device)
+        gx0 = torch.empty_like(xi_bar)
+        gl0 = torch.empty_like(xi_bar)
+        gxb = torch.empty_like(xi_bar)
+        for t in (grad_xi, grad_lam, grad_fp):
+            if t is not None and (t.dtype != torch.float32 or not t.is_contiguous() or t.device != self.device):
+                raise ValueError("gradients must be contiguous float32 on the device")
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        code = self._lib.sf_project_backward(self._h, C.c_void_p(stream.cuda_stream), C.byref(b), int(K),
+                                             int(bool(init_from_xi_bar)), _ptr(ckpt), _ptr(grad_xi), _ptr(grad_lam),
+                                             _ptr(grad_fp), _ptr(gx0), _ptr(gl0), _ptr(gxb), _ptr(ws),
+                                             C.c_size_t(nws))
+        del keep
+        nat.check(self._lib, self._h, code)
+        return gx0, gl0, gxb
+
     def launch_count(self) -> int:
         return int(self._lib.sf_launch_count(self._h))
 

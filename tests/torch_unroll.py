@@ -56,28 +56,29 @@ class TorchSF:
         return torch.einsum("tk,sdnk->sdnt", M, xi)
 
     def project_q(self, xi):
-        """q = e - F xi for every block, as time-domain tensors."""
+        """q = e - F xi for every block, as time-domain tensors. e is built
+        explicitly so that autograd sees de/ddelta = 0 at delta = 0 (the
+        tie-break point) and I on inactive rows."""
         p = self._states(xi, self.P)
         D = p[:, :, self.pi, :] - p[:, :, self.pj, :]               # [S, dim, npair, T]
         scale = torch.tensor([1 / self.a] * 2 + [1 / self.b], dtype=torch.float64)[: self.dim]
         s2 = ((D * scale[None, :, None, None]) ** 2).sum(1, keepdim=True)
         zero = s2 == 0
         inv = torch.where(zero, torch.ones_like(s2), s2).rsqrt()
-        fac = torch.where(s2 < 1, inv - 1, torch.zeros_like(s2))
-        fac = torch.where(zero, torch.zeros_like(fac), fac)
-        qD = fac * D
-        tie = torch.zeros_like(qD)
+        inside = (s2 < 1) & ~zero
+        e = torch.where(inside, D * inv, D)
+        tie = torch.zeros_like(D)
         tie[:, -1 if self.dim == 3 else 0] = self.b if self.dim == 3 else self.a
-        qD = torch.where(zero.expand_as(qD), tie, qD)
-        out = {"pair": qD}
+        e = torch.where(zero.expand_as(D), tie, e)
+        out = {"pair": e - D}
         for name, M, r in (("vel", self.Pd, self.v_max), ("acc", self.Pdd, self.a_max)):
             if r > 0:
                 v = self._states(xi, M)
                 n2 = (v ** 2).sum(1, keepdim=True)
-                nz = n2 > 0
-                nrm = torch.where(nz, n2, torch.ones_like(n2)).sqrt()
-                f = torch.where(nz & (nrm > r), r / nrm - 1, torch.zeros_like(nrm))
-                out[name] = f * v
+                outside = n2 > r * r
+                nrm = torch.where(outside, n2, torch.ones_like(n2)).sqrt()
+                ev = torch.where(outside, r * v / nrm, v)
+                out[name] = ev - v
         return out
 
     def Ft(self, q):
