@@ -229,6 +229,8 @@ def run_gpu(args):
         }
         if not args.no_diff:
             line["differentiation"] = diff_timing(P, dev)
+        if not args.no_batching:
+            line["batching"] = batching_timing(P, dev)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(spec, sc, args.cpu_samples)
         print(json.dumps(line), flush=True)
@@ -266,6 +268,52 @@ def diff_timing(P, dev):
     bwd = timed(lambda: f.project_backward(xb, st, gl, spec.K, ck, grad_xi=g))
     return {"workload": f"3D N={spec.n_robots}, S={spec.n_samples}, T={spec.T}, K={spec.K}, checkpoint every 10",
             "fwd_ms": fwd, "train_fwd_ms": trn, "bwd_ms": bwd, "bwd_over_fwd": bwd / fwd}
+
+
+def batching_timing(P, dev):
+    """The ragged batching workload: 64 scenes, N ~ U{8..32}, S ~ U{128..512},
+    K=150, 3D. Aggregate: one captured graph (all robot-count groups, autotuned
+    shapes), CUDA events, mean of 3 after a warm-up. Per scene: each scene
+    alone through sf_project."""
+    import torch
+    scenes = si.ragged_batch(2)
+    K = 150
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    xb = t(np.concatenate([s.xi_bar.reshape(-1) for s in scenes]))
+    st = t(np.concatenate([s.start for s in scenes]))
+    gl = t(np.concatenate([s.goal for s in scenes]))
+    nr = [s.spec.n_robots for s in scenes]
+    ns = [s.spec.n_samples for s in scenes]
+    f = P.SafetyFilter(dim=3, T=100, rho=RHO, coll_a=scenes[0].spec.coll, max_robots=32, device=dev.index)
+    f.autotune(xb, st, gl, K_probe=5, n_candidates=6, n_robots=nr, n_samples=ns)
+    g = f.capture(xb, st, gl, K, n_robots=nr, n_samples=ns)
+    g.launch()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = f.launch_count()
+    a.record()
+    for _ in range(3):
+        g.launch()
+    b.record()
+    torch.cuda.synchronize()
+    agg_ms = a.elapsed_time(b) / 3
+    per = []
+    for s in scenes:
+        xs, ss, gs = t(s.xi_bar), t(s.start), t(s.goal)
+        out = f.project(xs, ss, gs, K)
+        torch.cuda.synchronize()
+        a.record()
+        f.project(xs, ss, gs, K, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        per.append({"N": s.spec.n_robots, "S": s.spec.n_samples,
+                    "samples_per_s": s.spec.n_samples / (a.elapsed_time(b) * 1e-3)})
+    g.close()
+    tot = sum(ns)
+    return {"workload": "64 scenes, N ~ U{8..32}, S ~ U{128..512}, T=100, K=150, 3D, one captured graph",
+            "total_samples": tot, "aggregate_ms": agg_ms, "aggregate_samples_per_s": tot / (agg_ms * 1e-3),
+            "per_scene_alone_sum_ms": float(sum(p["S"] / p["samples_per_s"] * 1e3 for p in per)),
+            "per_scene": per}
 
 
 def cpu_baseline(spec, sc, n_samples):
@@ -330,6 +378,7 @@ def main():
     ap.add_argument("--cpu-samples", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-diff", action="store_true")
+    ap.add_argument("--no-batching", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -177,6 +177,30 @@ sf_status sf_set_launch_shape(sf_handle *h, int samples_per_cta, int warps, int 
  * the number of time ranges of the contraction phase. */
 sf_status sf_get_launch_shape(const sf_handle *h, int *out4);
 
+/* Measurement-based choice of the fused launch shape for this batch's scene
+ * mix: for every launch group (scenes sharing a robot-count bucket) the
+ * n_candidates cheapest shapes of the cost model are each run with K_probe
+ * iterations on `stream` and timed with CUDA events; the fastest is stored
+ * in the handle and used by later sf_project / sf_graph_capture calls for
+ * the same scene mix. Writes scratch results into xi_out, lambda_out,
+ * residual_out (device, sized as for sf_project). Synchronises `stream`. */
+sf_status sf_autotune(sf_handle *h, void *stream, const sf_batch *batch, int K_probe,
+                      int n_candidates, float *xi_out, float *lambda_out, float *residual_out);
+
+/* A CUDA graph of one sf_project call with fixed pointers: the launches of
+ * every robot-count group (concurrent branches when there are several) in
+ * one graph. The buffers passed at capture must stay allocated while the
+ * graph is used; their contents may change between launches. */
+typedef struct sf_graph sf_graph;
+sf_status sf_graph_capture(sf_handle *h, const sf_batch *batch, int K, int form, const float *xi0,
+                           const float *lambda0, float *xi_out, float *lambda_out,
+                           float *residual_out, float *residual_hist, void *workspace,
+                           size_t workspace_bytes, sf_graph **out);
+/* Launches the graph on `stream` (asynchronous). */
+sf_status sf_graph_launch(sf_graph *g, void *stream);
+/* Frees the graph. NULL is a no-op. */
+void sf_graph_destroy(sf_graph *g);
+
 /* Plain form without any device allocation. The paper has no counterpart to
  * this entry point; it exists for callers that cannot allocate device
  * memory at call time, for example a host framework that owns every device

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -22,6 +23,10 @@ struct sf_handle {
   unsigned long long launches = 0;
   int force_G = 0, force_warps = 0, force_tc = 0;  // launch-shape overrides (tuning)
   int last_plan[4] = {0, 0, 0, 0};                 // G, warps, tc, nq of the last fused launch
+  std::map<std::string, sf::FusedPlan> tuned;      // autotuned shapes per launch-group key
+  bool use_tuned = true;
+  cudaStream_t aux[2] = {nullptr, nullptr};        // extra streams for concurrent launch groups
+  cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
   std::string err;
 };
 
@@ -112,9 +117,23 @@ long long total_coefs(const sf_handle* h, const sf_batch* b) {
   return c;
 }
 
+struct LaunchGroup {
+  FusedArgs a;
+  FusedLaunch l;
+  std::string key;
+};
+
+std::string group_key(bool bwd, int dim, int nmax, int T, const std::vector<int>& nr, const std::vector<int>& ns) {
+  std::string k = (bwd ? "b" : "f") + std::to_string(dim) + "/" + std::to_string(nmax) + "/" + std::to_string(T) + ":";
+  for (size_t q = 0; q < nr.size(); ++q) k += std::to_string(nr[q]) + "x" + std::to_string(ns[q]) + ",";
+  return k;
+}
+
 // Fused form: scenes grouped by robot-count bucket, one launch per group of
-// up to MAX_SCENES_PER_LAUNCH scenes; the planner picks the launch shape.
-sf_status run_fused(sf_handle* h, cudaStream_t st, const sf_batch* b, int K, long long S, const FusedRequest& rq) {
+// up to MAX_SCENES_PER_LAUNCH scenes. The launch shape is the autotuned one
+// for the group's key when known, else the planner's.
+sf_status build_groups(sf_handle* h, const sf_batch* b, int K, long long S, const FusedRequest& rq,
+                       std::vector<LaunchGroup>* out) {
   const int dim = h->pb.dim, T = h->pb.T;
   const ProblemConsts pc = consts(h->pb, K);
   const long long tot = total_coefs(h, b);
@@ -140,10 +159,19 @@ sf_status run_fused(sf_handle* h, cudaStream_t st, const sf_batch* b, int K, lon
         nr.push_back(b->n_robots[items[bk][q].scene]);
         ns.push_back(b->n_samples[items[bk][q].scene]);
       }
-      const FusedPlan plan = plan_fused(dim, nmax, T, nr.data(), ns.data(), (int)nr.size(), h->num_sms,
-                                        h->max_smem_optin, h->force_G, h->force_warps, h->force_tc, rq.backward);
+      LaunchGroup lg;
+      lg.key = group_key(rq.backward, dim, nmax, T, nr, ns);
+      FusedPlan plan;
+      auto hit = h->tuned.find(lg.key);
+      const bool forced = h->force_G || h->force_warps || h->force_tc;
+      if (!forced && h->use_tuned && hit != h->tuned.end()) {
+        plan = hit->second;
+      } else {
+        plan = plan_fused(dim, nmax, T, nr.data(), ns.data(), (int)nr.size(), h->num_sms, h->max_smem_optin,
+                          h->force_G, h->force_warps, h->force_tc, rq.backward);
+      }
       if (plan.G == 0) return fail(h, SF_ERR_UNSUPPORTED, "no fused launch shape fits in shared memory");
-      FusedArgs a;
+      FusedArgs& a = lg.a;
       std::memset(&a, 0, sizeof(a));
       a.pc = pc;
       a.basis = reinterpret_cast<const float4*>(h->basis);
@@ -182,7 +210,7 @@ sf_status run_fused(sf_handle* h, cudaStream_t st, const sf_batch* b, int K, lon
         ctas += (d.S + d.G - 1) / d.G;
         gmax = std::max(gmax, d.G);
       }
-      FusedLaunch l;
+      FusedLaunch& l = lg.l;
       l.nmax = nmax;
       l.gmax = gmax;
       l.n_ctas = ctas;
@@ -190,16 +218,54 @@ sf_status run_fused(sf_handle* h, cudaStream_t st, const sf_batch* b, int K, lon
       l.tc = plan.tc;
       l.nq = plan.nq;
       l.smem = fused_smem_bytes(dim, nmax, T, gmax, plan.tc, plan.nq, rq.backward);
+      if (l.smem > h->max_smem_optin) return fail(h, SF_ERR_UNSUPPORTED, "launch shape exceeds shared memory");
       h->last_plan[0] = plan.G;
       h->last_plan[1] = plan.warps;
       h->last_plan[2] = plan.tc;
       h->last_plan[3] = plan.nq;
-      cudaError_t e = rq.backward ? launch_backward(a, rq.bwd, l, st) : launch_fused(a, l, st);
-      if (e != cudaSuccess) return cuda_fail(h, e, rq.backward ? "backward launch" : "fused form launch");
-      h->launches += 1;
+      out->push_back(lg);
     }
   }
   return SF_OK;
+}
+
+cudaError_t launch_group(const LaunchGroup& g, const FusedRequest& rq, cudaStream_t st) {
+  return rq.backward ? launch_backward(g.a, rq.bwd, g.l, st) : launch_fused(g.a, g.l, st);
+}
+
+// Launches the groups; with more than one group they run concurrently on
+// the handle's extra streams, forked from and joined back to `st` (inside a
+// stream capture this becomes parallel branches of the graph).
+sf_status launch_groups(sf_handle* h, cudaStream_t st, const std::vector<LaunchGroup>& gs, const FusedRequest& rq) {
+  const char* what = rq.backward ? "backward launch" : "fused form launch";
+  if (gs.size() == 1) {
+    cudaError_t e = launch_group(gs[0], rq, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, what);
+    h->launches += 1;
+    return SF_OK;
+  }
+  cudaError_t e = cudaEventRecord(h->fork, st);
+  for (int q = 0; q < 2 && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(h->aux[q], h->fork, 0);
+  if (e != cudaSuccess) return cuda_fail(h, e, "fork of launch groups");
+  for (size_t gi = 0; gi < gs.size(); ++gi) {
+    cudaStream_t s = gi % 3 == 0 ? st : h->aux[gi % 3 - 1];
+    e = launch_group(gs[gi], rq, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, what);
+    h->launches += 1;
+  }
+  for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+    e = cudaEventRecord(h->join[q], h->aux[q]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->join[q], 0);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "join of launch groups");
+  return SF_OK;
+}
+
+sf_status run_fused(sf_handle* h, cudaStream_t st, const sf_batch* b, int K, long long S, const FusedRequest& rq) {
+  std::vector<LaunchGroup> gs;
+  sf_status s = build_groups(h, b, K, S, rq, &gs);
+  if (s != SF_OK) return s;
+  return launch_groups(h, st, gs, rq);
 }
 
 }  // namespace
@@ -259,6 +325,16 @@ sf_status sf_create(const sf_problem* pb, int device, sf_handle** out) {
     sf_destroy(h);
     return e == cudaErrorInvalidValue ? SF_ERR_INVALID_ARG : SF_ERR_CUDA;
   }
+  e = prepare_kernels(pb->dim, (int)h->max_smem_optin);
+  for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+    e = cudaStreamCreateWithFlags(&h->aux[q], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join[q], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    sf_destroy(h);
+    return SF_ERR_CUDA;
+  }
   *out = h;
   return SF_OK;
 }
@@ -266,6 +342,11 @@ sf_status sf_create(const sf_problem* pb, int device, sf_handle** out) {
 void sf_destroy(sf_handle* h) {
   if (!h) return;
   DeviceGuard g(h->device);
+  for (int q = 0; q < 2; ++q) {
+    if (h->aux[q]) cudaStreamDestroy(h->aux[q]);
+    if (h->join[q]) cudaEventDestroy(h->join[q]);
+  }
+  if (h->fork) cudaEventDestroy(h->fork);
   cudaFree(h->basis);
   cudaFree(h->ops);
   cudaFree(h->status);
@@ -437,6 +518,154 @@ sf_status sf_project_backward(sf_handle* h, void* stream, const sf_batch* b, int
   rq.bwd.gxb = gxb;
   rq.bwd.xi0_is_xi_bar = init_from_xi_bar ? 1 : 0;
   return run_fused(h, reinterpret_cast<cudaStream_t>(stream), b, K, S, rq);
+}
+
+struct sf_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int device = 0;
+};
+
+sf_status sf_autotune(sf_handle* h, void* stream, const sf_batch* b, int K_probe, int n_candidates, float* xi_out,
+                      float* lam_out, float* resid_out) {
+  if (!h) return SF_ERR_INVALID_ARG;
+  long long R = 0, S = 0;
+  sf_status s0 = check_batch(h, b, &R, &S);
+  if (s0 != SF_OK) return s0;
+  if (K_probe < 1 || n_candidates < 1 || n_candidates > 64)
+    return fail(h, SF_ERR_INVALID_ARG, "K_probe >= 1 and 1 <= n_candidates <= 64");
+  if (S > 0 && (!xi_out || !lam_out || !resid_out)) return fail(h, SF_ERR_INVALID_ARG, "outputs are NULL");
+  if (h->pb.precision != SF_PREC_FP32) return fail(h, SF_ERR_UNSUPPORTED, "only SF_PREC_FP32 is built");
+  if (S == 0) return SF_OK;
+  DeviceGuard g(h->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  FusedRequest rq;
+  rq.xi_out = xi_out;
+  rq.lam_out = lam_out;
+  rq.resid_out = resid_out;
+  const int fG = h->force_G, fW = h->force_warps, fT = h->force_tc;
+  h->force_G = h->force_warps = h->force_tc = 0;
+  h->use_tuned = false;
+  std::vector<LaunchGroup> gs;
+  sf_status s = build_groups(h, b, K_probe, S, rq, &gs);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (size_t gi = 0; s == SF_OK && e == cudaSuccess && gi < gs.size(); ++gi) {
+    LaunchGroup lg = gs[gi];
+    std::vector<int> nr, ns;
+    for (int q = 0; q < lg.a.n_scenes; ++q) {
+      nr.push_back(lg.a.sc[q].N);
+      ns.push_back(lg.a.sc[q].S);
+    }
+    std::vector<FusedPlan> top(n_candidates);
+    plan_fused(h->pb.dim, lg.l.nmax, h->pb.T, nr.data(), ns.data(), (int)nr.size(), h->num_sms, h->max_smem_optin,
+               0, 0, 0, false, top.data(), n_candidates);
+    float best_ms = INFINITY;
+    FusedPlan best = top[0];
+    for (int c = 0; c < n_candidates && e == cudaSuccess; ++c) {
+      const FusedPlan& p = top[c];
+      if (p.G == 0) continue;
+      LaunchGroup t = lg;
+      int ctas = 0, gmax = 1;
+      for (int q = 0; q < t.a.n_scenes; ++q) {
+        SceneDesc& d = t.a.sc[q];
+        d.G = std::min(p.G, d.S);
+        d.cta_begin = ctas;
+        ctas += (d.S + d.G - 1) / d.G;
+        gmax = std::max(gmax, d.G);
+      }
+      t.a.tc = p.tc;
+      t.a.nq = p.nq;
+      t.l.n_ctas = ctas;
+      t.l.gmax = gmax;
+      t.l.warps = p.warps;
+      t.l.tc = p.tc;
+      t.l.nq = p.nq;
+      t.l.smem = fused_smem_bytes(h->pb.dim, t.l.nmax, h->pb.T, gmax, p.tc, p.nq, false);
+      if (t.l.smem > h->max_smem_optin) continue;
+      float ms_sum = 0.0f;
+      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {   // first run warms up
+        e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) e = launch_group(t, rq, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) ms_sum += ms;
+        h->launches += 1;
+      }
+      if (e == cudaSuccess && ms_sum < best_ms) {
+        best_ms = ms_sum;
+        best = p;
+      }
+    }
+    if (e == cudaSuccess) h->tuned[lg.key] = best;   // the key does not depend on K
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  h->force_G = fG;
+  h->force_warps = fW;
+  h->force_tc = fT;
+  h->use_tuned = true;
+  if (s != SF_OK) return s;
+  if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
+  return SF_OK;
+}
+
+sf_status sf_graph_capture(sf_handle* h, const sf_batch* b, int K, int form, const float* xi0, const float* lam0,
+                           float* xi_out, float* lam_out, float* resid_out, float* resid_hist, void* workspace,
+                           size_t workspace_bytes, sf_graph** out) {
+  if (!h || !out) return SF_ERR_INVALID_ARG;
+  *out = nullptr;
+  DeviceGuard g(h->device);
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(h, e, "capture stream");
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return cuda_fail(h, e, "begin capture");
+  }
+  sf_status s = sf_project(h, cs, b, K, form, xi0, lam0, xi_out, lam_out, resid_out, resid_hist, workspace,
+                           workspace_bytes, nullptr);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(cs, &graph);
+  cudaStreamDestroy(cs);
+  if (s != SF_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+  sf_graph* gr = new (std::nothrow) sf_graph();
+  if (!gr) {
+    cudaGraphDestroy(graph);
+    return SF_ERR_OOM;
+  }
+  gr->graph = graph;
+  gr->device = h->device;
+  e = cudaGraphInstantiate(&gr->exec, graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    delete gr;
+    return cuda_fail(h, e, "graph instantiate");
+  }
+  *out = gr;
+  return SF_OK;
+}
+
+sf_status sf_graph_launch(sf_graph* gr, void* stream) {
+  if (!gr) return SF_ERR_INVALID_ARG;
+  DeviceGuard g(gr->device);
+  return cudaGraphLaunch(gr->exec, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? SF_OK : SF_ERR_CUDA;
+}
+
+void sf_graph_destroy(sf_graph* gr) {
+  if (!gr) return;
+  DeviceGuard g(gr->device);
+  if (gr->exec) cudaGraphExecDestroy(gr->exec);
+  if (gr->graph) cudaGraphDestroy(gr->graph);
+  delete gr;
 }
 
 unsigned long long sf_launch_count(const sf_handle* h) { return h ? h->launches : 0ULL; }

@@ -35,4 +35,8 @@ cudaError_t launch_bwd_d3_n16(const FusedArgs& a, const BwdLaunchArgs& b, const 
   std::memcpy(x.sc, a.sc, sizeof(x.sc));
   return fused_impl::launch_bwd_t<3, 16, 384>(x, l.n_ctas, l.warps, l.smem, st);
 }
+cudaError_t prepare_bwd_d3_n16(int smem) {
+  return cudaFuncSetAttribute(fused_impl::fused_bwd_kernel<3, 16, 384>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
 }  // namespace sf

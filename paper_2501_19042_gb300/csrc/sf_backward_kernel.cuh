@@ -398,8 +398,6 @@ template <int DIM, int NMAX, int MAXT>
 cudaError_t launch_bwd_t(const BwdArgs& a, int n_ctas, int warps, size_t smem, cudaStream_t st) {
   auto k = fused_bwd_kernel<DIM, NMAX, MAXT>;
   if (warps * 32 > MAXT) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   k<<<n_ctas, warps * 32, smem, st>>>(a);
   return cudaGetLastError();
 }

@@ -14,6 +14,25 @@ namespace sf {
                                       cudaStream_t);
 SF_DECL(2, 8) SF_DECL(2, 16) SF_DECL(2, 32) SF_DECL(3, 8) SF_DECL(3, 16) SF_DECL(3, 32)
 #undef SF_DECL
+#define SF_PREP(D, NM) cudaError_t prepare_fused_d##D##_n##NM(int); cudaError_t prepare_bwd_d##D##_n##NM(int);
+SF_PREP(2, 8) SF_PREP(2, 16) SF_PREP(2, 32) SF_PREP(3, 8) SF_PREP(3, 16) SF_PREP(3, 32)
+#undef SF_PREP
+
+// Raises the dynamic shared-memory limit of every fused / adjoint kernel of
+// this dimension once, at handle creation, so that no launch (and no stream
+// capture) has to configure a kernel.
+cudaError_t prepare_kernels(int dim, int smem) {
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+  if (dim == 3) {
+    chk(prepare_fused_d3_n8(smem)); chk(prepare_fused_d3_n16(smem)); chk(prepare_fused_d3_n32(smem));
+    chk(prepare_bwd_d3_n8(smem)); chk(prepare_bwd_d3_n16(smem)); chk(prepare_bwd_d3_n32(smem));
+  } else {
+    chk(prepare_fused_d2_n8(smem)); chk(prepare_fused_d2_n16(smem)); chk(prepare_fused_d2_n32(smem));
+    chk(prepare_bwd_d2_n8(smem)); chk(prepare_bwd_d2_n16(smem)); chk(prepare_bwd_d2_n32(smem));
+  }
+  return e;
+}
 
 int fused_max_warps(int nmax) { return nmax == 32 ? 8 : 12; }
 
@@ -28,10 +47,12 @@ size_t fused_smem_bytes(int dim, int nmax, int T, int gmax, int tc, int nq, bool
 // instructions per cycle; plus a charge per block-wide barrier. The CTA count
 // over the SM count gives the number of waves.
 FusedPlan plan_fused(int dim, int nmax, int T, const int* nr, const int* ns, int n_scenes, int num_sms,
-                     size_t smem_cap, int force_G, int force_warps, int force_tc, bool bwd) {
+                     size_t smem_cap, int force_G, int force_warps, int force_tc, bool bwd, FusedPlan* top,
+                     int n_top) {
   FusedPlan best;
   best.G = 0;
   best.cost = INFINITY;
+  for (int q = 0; q < n_top; ++q) top[q] = FusedPlan{0, 0, 0, 0, 0, INFINITY};
   long long tot = 0;
   int Nbig = 1;
   for (int q = 0; q < n_scenes; ++q) {
@@ -64,7 +85,17 @@ FusedPlan plan_fused(int dim, int nmax, int T, const int* nr, const int* ns, int
         const double per_iter = real_nch * (a_rounds * w * cA + b_rounds * w * tq * cB) / rate +
                                 (2.0 * real_nch + 2.0) * 400.0 + 24.0 * G * Nbig * dim * 4.0 / rate;
         const double cost = waves * per_iter;
-        if (cost < best.cost) best = FusedPlan{G, w, tc, nq, smem, cost};
+        const FusedPlan cand{G, w, tc, nq, smem, cost};
+        if (cost < best.cost) best = cand;
+        if (top && n_top > 0) {
+          // keep the n_top cheapest candidates, sorted by model cost
+          int pos = n_top;
+          while (pos > 0 && (top[pos - 1].G == 0 || cost < top[pos - 1].cost)) --pos;
+          if (pos < n_top) {
+            for (int q = n_top - 1; q > pos; --q) top[q] = top[q - 1];
+            top[pos] = cand;
+          }
+        }
       }
     }
   }

@@ -677,8 +677,6 @@ template <int DIM, int NMAX, int MAXT>
 cudaError_t launch_t(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st) {
   auto k = fused_fwd_kernel<DIM, NMAX, MAXT>;
   if (l.warps * 32 > MAXT) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem);
-  if (e != cudaSuccess) return e;
   k<<<l.n_ctas, l.warps * 32, l.smem, st>>>(a);
   return cudaGetLastError();
 }

@@ -146,6 +146,7 @@ struct FusedLaunch {
 size_t fused_smem_bytes(int dim, int nmax, int T, int gmax, int tc, int nq, bool bwd = false);
 cudaError_t launch_fused(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st);
 int fused_max_warps(int nmax);
+cudaError_t prepare_kernels(int dim, int smem);
 
 // Launch shape of the fused kernel for one group of scenes: samples per CTA,
 // warps, time chunk, contraction ranges (cost model over the candidates,
@@ -157,7 +158,7 @@ struct FusedPlan {
 };
 FusedPlan plan_fused(int dim, int nmax, int T, const int* n_robots, const int* n_samples, int n_scenes,
                      int num_sms, size_t smem_cap, int force_G, int force_warps, int force_tc,
-                     bool bwd = false);
+                     bool bwd = false, FusedPlan* top = nullptr, int n_top = 0);
 
 // Backward launch: everything the adjoint kernel needs besides the scene
 // table (which it shares with FusedArgs).

@@ -235,6 +235,39 @@ class SafetyFilter:
         nat.check(self._lib, self._h, code)
         return gx0, gl0, gxb
 
+    def autotune(self, xi_bar, start, goal, K_probe=10, n_candidates=8, n_robots=None, n_samples=None,
+                 start_va=None, goal_va=None, stream=None):
+        """``sf_autotune``: times the cost model's best launch shapes for this
+        scene mix and keeps the fastest for later calls."""
+        b, keep, ncoef, nsamp = self._batch(xi_bar, start, goal, n_robots, n_samples, start_va, goal_va)
+        scratch = ProjectResult(xi=torch.empty_like(xi_bar), lam=torch.empty_like(xi_bar),
+                                residual=torch.empty(nsamp, dtype=torch.float32, device=self.device))
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        code = self._lib.sf_autotune(self._h, C.c_void_p(stream.cuda_stream), C.byref(b), int(K_probe),
+                                     int(n_candidates), _ptr(scratch.xi), _ptr(scratch.lam), _ptr(scratch.residual))
+        del keep
+        nat.check(self._lib, self._h, code)
+
+    def capture(self, xi_bar, start, goal, K, n_robots=None, n_samples=None, xi0=None, lam0=None,
+                start_va=None, goal_va=None, form="fused", hist=False):
+        """``sf_graph_capture``: a replayable CUDA graph of one ``project`` call
+        on fixed buffers. Returns a ``SFGraph`` whose ``out`` holds the outputs."""
+        b, keep, ncoef, nsamp = self._batch(xi_bar, start, goal, n_robots, n_samples, start_va, goal_va)
+        out = ProjectResult(
+            xi=torch.empty_like(xi_bar), lam=torch.empty_like(xi_bar),
+            residual=torch.empty(nsamp, dtype=torch.float32, device=self.device),
+            hist=torch.empty((K, nsamp), dtype=torch.float32, device=self.device) if hist else None)
+        wsb = int(self._lib.sf_workspace_bytes(self._h, C.byref(b), nat.FORM[form], int(K)))
+        ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=self.device) if wsb else None
+        g = C.c_void_p()
+        code = self._lib.sf_graph_capture(self._h, C.byref(b), int(K), nat.FORM[form], _ptr(xi0), _ptr(lam0),
+                                          _ptr(out.xi), _ptr(out.lam), _ptr(out.residual), _ptr(out.hist),
+                                          _ptr(ws), C.c_size_t(wsb), C.byref(g))
+        del keep
+        nat.check(self._lib, self._h, code)
+        return SFGraph(self, g, out, (xi_bar, start, goal, xi0, lam0, start_va, goal_va, ws))
+
     def launch_count(self) -> int:
         return int(self._lib.sf_launch_count(self._h))
 
@@ -242,3 +275,29 @@ class SafetyFilter:
         if stream is None:
             stream = torch.cuda.current_stream(self.device)
         nat.check(self._lib, self._h, self._lib.sf_sync_status(self._h, C.c_void_p(stream.cuda_stream)))
+
+
+class SFGraph:
+    """A captured sf_project call (``sf_graph_*``). Inputs captured by pointer:
+    update them in place and call ``launch()``."""
+
+    def __init__(self, sf: SafetyFilter, g, out: ProjectResult, keep):
+        self._sf, self._g, self.out, self._keep = sf, g, out, keep
+
+    def launch(self, stream=None):
+        if stream is None:
+            stream = torch.cuda.current_stream(self._sf.device)
+        nat.check(self._sf._lib, self._sf._h,
+                  self._sf._lib.sf_graph_launch(self._g, C.c_void_p(stream.cuda_stream)))
+        return self.out
+
+    def close(self):
+        if getattr(self, "_g", None):
+            self._sf._lib.sf_graph_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

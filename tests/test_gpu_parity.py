@@ -170,3 +170,68 @@ def test_invalid_arguments(sfmod):
     n0 = f.launch_count()
     f.project(_dev(sc8.xi_bar), _dev(sc8.start), _dev(sc8.goal), 5)
     assert f.launch_count() == n0 + 1
+
+
+def _ragged_inputs(scenes):
+    xb = np.concatenate([s.xi_bar.reshape(-1) for s in scenes])
+    starts = np.concatenate([s.start for s in scenes])
+    goals = np.concatenate([s.goal for s in scenes])
+    nr = [s.spec.n_robots for s in scenes]
+    ns = [s.spec.n_samples for s in scenes]
+    return xb, starts, goals, nr, ns
+
+
+def test_graph_replay_and_in_place_update(sfmod):
+    """A captured graph of a multi-bucket batch (concurrent branches) replays
+    bit-identically to the direct call, also after the inputs change in place."""
+    P = sfmod
+    st = si.Stream(31)
+    scenes = [si.make_scene(si.config_n16_3d(n_robots=n, n_samples=s, K=30), st)
+              for n, s in [(6, 9), (12, 20), (20, 7), (31, 4)]]
+    xb, starts, goals, nr, ns = _ragged_inputs(scenes)
+    f = P.SafetyFilter(dim=3, T=100, rho=RHO_3D, coll_a=0.5, max_robots=32)
+    dxb, dst, dgl = _dev(xb), _dev(starts), _dev(goals)
+    ref = f.project(dxb, dst, dgl, 30, n_robots=nr, n_samples=ns, hist=True)
+    g = f.capture(dxb, dst, dgl, 30, n_robots=nr, n_samples=ns, hist=True)
+    for _ in range(2):
+        out = g.launch()
+        torch.cuda.synchronize()
+        assert torch.equal(out.xi, ref.xi) and torch.equal(out.lam, ref.lam)
+        assert torch.equal(out.residual, ref.residual) and torch.equal(out.hist, ref.hist)
+    dxb.mul_(0.9)
+    ref2 = f.project(dxb, dst, dgl, 30, n_robots=nr, n_samples=ns, hist=True)
+    out = g.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(out.xi, ref2.xi) and not torch.equal(ref2.xi, ref.xi)
+    g.close()
+
+
+def test_ragged_64_scenes_full_size_sampled(sfmod, oracle_lib):
+    """The batching workload at full size: 64 scenes, N ~ U{8..32},
+    S ~ U{128..512}, K=150, autotuned and replayed from one captured graph;
+    sampled outputs against the oracle one by one."""
+    P = sfmod
+    scenes = si.ragged_batch(2)
+    xb, starts, goals, nr, ns = _ragged_inputs(scenes)
+    f = P.SafetyFilter(dim=3, T=100, rho=RHO_3D, coll_a=0.5, max_robots=32)
+    dxb, dst, dgl = _dev(xb), _dev(starts), _dev(goals)
+    f.autotune(dxb, dst, dgl, K_probe=5, n_candidates=4, n_robots=nr, n_samples=ns)
+    g = f.capture(dxb, dst, dgl, 150, n_robots=nr, n_samples=ns)
+    out = g.launch()
+    torch.cuda.synchronize()
+    f.sync_status()
+    xi = out.xi.double().cpu().numpy()
+    res = out.residual.double().cpu().numpy()
+    assert np.isfinite(xi).all() and np.isfinite(res).all()
+    offs_c = np.cumsum([0] + [s * 3 * n * 11 for n, s in zip(nr, ns)])
+    offs_s = np.cumsum([0] + ns)
+    picks = [(0, 0), (17, 5), (40, 100), (63, None)]
+    for q, smp in picks:
+        sc = scenes[q]
+        S, N = sc.spec.n_samples, sc.spec.n_robots
+        smp = S - 1 if smp is None else min(smp, S - 1)
+        ref = run_oracle(oracle_lib, sc, RHO_3D, 150, idx=np.array([smp]))
+        got = xi[offs_c[q]:offs_c[q + 1]].reshape(S, -1)[smp:smp + 1]
+        assert rel_l2(got, ref["xi"]).max() <= TOL_XI_REL, (q, N)
+        assert abs(res[offs_s[q] + smp] - ref["rp_final"][0]) <= TOL_RESID_ABS
+    g.close()
