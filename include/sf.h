@@ -127,8 +127,10 @@ const char *sf_last_error(const sf_handle *h);
  * here. Returns 0 and sets the error on invalid input. */
 size_t sf_workspace_bytes(const sf_handle *h, const sf_batch *batch, int form, int K);
 
-/* Bytes of the checkpoint buffer sf_project writes for sf_project_backward:
- * (xi, lambda) of every sample every checkpoint_every iterations. */
+/* Bytes of the checkpoint buffer sf_project / sf_project_train write for
+ * sf_project_backward: (xi, lambda) of every sample every checkpoint_every
+ * iterations, followed by every iterate of the last segment (so that the
+ * backward recomputes all segments but the last). */
 size_t sf_checkpoint_bytes(const sf_handle *h, const sf_batch *batch, int K);
 
 /* Runs K >= 1 iterations of f_FP on every sample of the batch.
@@ -239,7 +241,8 @@ sf_status sf_project_plain_noalloc(sf_handle *h, void *stream, const sf_batch *b
  *   checkpoints  device, sf_checkpoint_bytes() bytes (required): (xi, lambda)
  *                of every sample at iterations 0, k, 2k, ... (k =
  *                checkpoint_every of the problem), layout
- *                [n_checkpoints][2][total coefficients].
+ *                [n_checkpoints][2][total coefficients], then the iterates
+ *                last_checkpoint .. K in the same [slot][2][total] layout.
  * Needs a handle created with checkpoint_every > 0. */
 sf_status sf_project_train(sf_handle *h, void *stream, const sf_batch *batch, int K,
                            const float *xi0, const float *lambda0, float *xi_out, float *lambda_out,

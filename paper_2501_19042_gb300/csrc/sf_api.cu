@@ -57,7 +57,10 @@ sf_status cuda_fail(sf_handle* h, cudaError_t e, const char* where) {
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
-int nmax_bucket(int N) { return N <= 8 ? 8 : (N <= 16 ? 16 : 32); }
+int nmax_bucket(int N) { return N <= 8 ? 8 : (N <= 16 ? 16 : (N <= 24 ? 24 : 32)); }
+int bucket_index(int N) { return N <= 8 ? 0 : (N <= 16 ? 1 : (N <= 24 ? 2 : 3)); }
+constexpr int kBuckets = 4;
+constexpr int kBucketNmax[kBuckets] = {8, 16, 24, 32};
 
 ProblemConsts consts(const sf_problem& pb, int K) {
   ProblemConsts c;
@@ -67,6 +70,10 @@ ProblemConsts consts(const sf_problem& pb, int K) {
   c.rho = (float)pb.rho;
   c.inv_a2 = (float)(1.0 / (pb.coll_a * pb.coll_a));
   c.inv_b2 = (float)(1.0 / (pb.coll_b * pb.coll_b));
+  c.inv_a = (float)(1.0 / pb.coll_a);
+  c.inv_b = (float)(1.0 / pb.coll_b);
+  c.coll_a = (float)pb.coll_a;
+  c.coll_b = (float)pb.coll_b;
   c.tie = (float)(pb.dim == 3 ? pb.coll_b : pb.coll_a);
   c.use_v = pb.v_max > 0.0;
   c.use_a = pb.a_max > 0.0;
@@ -138,20 +145,20 @@ sf_status build_groups(sf_handle* h, const sf_batch* b, int K, long long S, cons
   const ProblemConsts pc = consts(h->pb, K);
   const long long tot = total_coefs(h, b);
   struct Item { int scene; long long roff, soff, coff; };
-  std::vector<Item> items[3];
+  std::vector<Item> items[kBuckets];
   {
     long long roff = 0, soff = 0, coff = 0;
     for (int sc = 0; sc < b->n_scenes; ++sc) {
       const int N = b->n_robots[sc], Ss = b->n_samples[sc];
-      const int bk = nmax_bucket(N) == 8 ? 0 : (nmax_bucket(N) == 16 ? 1 : 2);
+      const int bk = bucket_index(N);
       if (Ss > 0) items[bk].push_back({sc, roff, soff, coff});
       roff += N;
       soff += Ss;
       coff += (long long)Ss * dim * N * NV;
     }
   }
-  for (int bk = 0; bk < 3; ++bk) {
-    const int nmax = 8 << bk;
+  for (int bk = 0; bk < kBuckets; ++bk) {
+    const int nmax = kBucketNmax[bk];
     for (size_t first = 0; first < items[bk].size(); first += MAX_SCENES_PER_LAUNCH) {
       const size_t last = std::min(items[bk].size(), first + (size_t)MAX_SCENES_PER_LAUNCH);
       std::vector<int> nr, ns;
@@ -248,7 +255,7 @@ sf_status launch_groups(sf_handle* h, cudaStream_t st, const std::vector<LaunchG
   for (int q = 0; q < 2 && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(h->aux[q], h->fork, 0);
   if (e != cudaSuccess) return cuda_fail(h, e, "fork of launch groups");
   for (size_t gi = 0; gi < gs.size(); ++gi) {
-    cudaStream_t s = gi % 3 == 0 ? st : h->aux[gi % 3 - 1];
+    cudaStream_t s = gi % 3 == 0 ? st : h->aux[gi % 3 - 1];   // up to 3 groups at once
     e = launch_group(gs[gi], rq, s);
     if (e != cudaSuccess) return cuda_fail(h, e, what);
     h->launches += 1;
@@ -377,7 +384,8 @@ size_t sf_checkpoint_bytes(const sf_handle* hc, const sf_batch* b, int K) {
   const long long nck = (K + h->pb.checkpoint_every - 1) / h->pb.checkpoint_every;
   long long coefs = 0;
   for (int s = 0; s < b->n_scenes; ++s) coefs += (long long)b->n_samples[s] * h->pb.dim * b->n_robots[s] * NV;
-  return (size_t)(nck * 2 * coefs) * sizeof(float);
+  // checkpoints, then the iterates of the last segment (up to checkpoint_every + 1)
+  return (size_t)((nck + h->pb.checkpoint_every + 1) * 2 * coefs) * sizeof(float);
 }
 
 sf_status sf_project(sf_handle* h, void* stream, const sf_batch* b, int K, int form, const float* xi0,

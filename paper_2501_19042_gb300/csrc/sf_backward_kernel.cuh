@@ -243,7 +243,7 @@ __device__ __forceinline__ const float* ring_lam(const float* ring, int j, long 
 // Adjoint of iteration k (z^k -> z^{k+1}); XB, LB hold dL/dz^{k+1} on entry
 // and dL/dz^k on exit.
 template <int DIM, int NMAX>
-__device__ void adjoint_step(const Cta<DIM, NMAX>& c, const BwdArgs& A, int j) {
+__device__ void adjoint_step(const Cta<DIM, NMAX>& c, const BwdArgs& A, const float* ring, int j) {
   constexpr int RS = DIM * NP;
   const Lay& L = c.L;
   const ProblemConsts& pc = A.pc;
@@ -251,10 +251,10 @@ __device__ void adjoint_step(const Cta<DIM, NMAX>& c, const BwdArgs& A, int j) {
   const long long tot = A.total_coefs;
   const float rho = pc.rho;
   const float invN = 1.0f / (float)N;
-  const float* xk = ring_xi(A.ring, j, tot);
-  const float* xk1 = ring_xi(A.ring, j + 1, tot);
-  const float* lk = ring_lam(A.ring, j, tot);
-  const float* lk1 = ring_lam(A.ring, j + 1, tot);
+  const float* xk = ring_xi(ring, j, tot);
+  const float* xk1 = ring_xi(ring, j + 1, tot);
+  const float* lk = ring_lam(ring, j, tot);
+  const float* lk1 = ring_lam(ring, j + 1, tot);
   // (0) xi^k into C; fixed-point-residual term with respect to z^{k+1}
   for (int v = c.tid; v < G * NMAX * RS; v += c.nthr) {
     const int s = v / (NMAX * RS), rem = v % (NMAX * RS);
@@ -368,19 +368,27 @@ __global__ void __launch_bounds__(MAXT, 1) fused_bwd_kernel(const __grid_constan
   const int ck = A.ck_every;
   const int nseg = (K + ck - 1) / ck;
   float* ring = A.ring;
+  // the forward stored every iterate of the last segment after the
+  // checkpoints; earlier segments are recomputed into the workspace ring
+  const float* tail = A.ckpt + (size_t)nseg * 2 * tot;
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int kb = seg * ck, ke = min(K, kb + ck);
-    const float* cx = A.ckpt + (size_t)seg * 2 * tot;
-    load_state<DIM, NMAX>(c, cx, cx + tot, nullptr);
-    __syncthreads();
-    store_state<DIM, NMAX>(c, ring, ring + tot, 0);
-    for (int k = kb; k < ke; ++k) {
-      fwd_iteration<DIM, NMAX>(c, pc, A.xi_bar, k, false, nullptr, 0, false);
-      float* slot = ring + (size_t)(k - kb + 1) * 2 * tot;
-      store_state<DIM, NMAX>(c, slot, slot + tot, 0);
+    const float* rg = ring;
+    if (seg == nseg - 1) {
+      rg = tail;
+    } else {
+      const float* cx = A.ckpt + (size_t)seg * 2 * tot;
+      load_state<DIM, NMAX>(c, cx, cx + tot, nullptr, A.xi_bar);
+      __syncthreads();
+      store_state<DIM, NMAX>(c, ring, ring + tot, 0);
+      for (int k = kb; k < ke; ++k) {
+        fwd_iteration<DIM, NMAX>(c, pc, A.xi_bar, k, false, nullptr, 0, false);
+        float* slot = ring + (size_t)(k - kb + 1) * 2 * tot;
+        store_state<DIM, NMAX>(c, slot, slot + tot, 0);
+      }
     }
     __syncthreads();
-    for (int k = ke - 1; k >= kb; --k) adjoint_step<DIM, NMAX>(c, A, k - kb);
+    for (int k = ke - 1; k >= kb; --k) adjoint_step<DIM, NMAX>(c, A, rg, k - kb);
   }
   for (int v = c.tid; v < G * DIM * N * NV; v += c.nthr) {
     const int s = v / (DIM * N * NV), rem = v % (DIM * N * NV);

@@ -12,10 +12,10 @@ namespace sf {
   cudaError_t launch_fused_d##D##_n##NM(const FusedArgs&, const FusedLaunch&, cudaStream_t);           \
   cudaError_t launch_bwd_d##D##_n##NM(const FusedArgs&, const BwdLaunchArgs&, const FusedLaunch&,      \
                                       cudaStream_t);
-SF_DECL(2, 8) SF_DECL(2, 16) SF_DECL(2, 32) SF_DECL(3, 8) SF_DECL(3, 16) SF_DECL(3, 32)
+SF_DECL(2, 8) SF_DECL(2, 16) SF_DECL(2, 24) SF_DECL(2, 32) SF_DECL(3, 8) SF_DECL(3, 16) SF_DECL(3, 24) SF_DECL(3, 32)
 #undef SF_DECL
 #define SF_PREP(D, NM) cudaError_t prepare_fused_d##D##_n##NM(int); cudaError_t prepare_bwd_d##D##_n##NM(int);
-SF_PREP(2, 8) SF_PREP(2, 16) SF_PREP(2, 32) SF_PREP(3, 8) SF_PREP(3, 16) SF_PREP(3, 32)
+SF_PREP(2, 8) SF_PREP(2, 16) SF_PREP(2, 24) SF_PREP(2, 32) SF_PREP(3, 8) SF_PREP(3, 16) SF_PREP(3, 24) SF_PREP(3, 32)
 #undef SF_PREP
 
 // Raises the dynamic shared-memory limit of every fused / adjoint kernel of
@@ -25,16 +25,20 @@ cudaError_t prepare_kernels(int dim, int smem) {
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
   if (dim == 3) {
-    chk(prepare_fused_d3_n8(smem)); chk(prepare_fused_d3_n16(smem)); chk(prepare_fused_d3_n32(smem));
-    chk(prepare_bwd_d3_n8(smem)); chk(prepare_bwd_d3_n16(smem)); chk(prepare_bwd_d3_n32(smem));
+    chk(prepare_fused_d3_n8(smem)); chk(prepare_fused_d3_n16(smem)); chk(prepare_fused_d3_n24(smem));
+    chk(prepare_fused_d3_n32(smem));
+    chk(prepare_bwd_d3_n8(smem)); chk(prepare_bwd_d3_n16(smem)); chk(prepare_bwd_d3_n24(smem));
+    chk(prepare_bwd_d3_n32(smem));
   } else {
-    chk(prepare_fused_d2_n8(smem)); chk(prepare_fused_d2_n16(smem)); chk(prepare_fused_d2_n32(smem));
-    chk(prepare_bwd_d2_n8(smem)); chk(prepare_bwd_d2_n16(smem)); chk(prepare_bwd_d2_n32(smem));
+    chk(prepare_fused_d2_n8(smem)); chk(prepare_fused_d2_n16(smem)); chk(prepare_fused_d2_n24(smem));
+    chk(prepare_fused_d2_n32(smem));
+    chk(prepare_bwd_d2_n8(smem)); chk(prepare_bwd_d2_n16(smem)); chk(prepare_bwd_d2_n24(smem));
+    chk(prepare_bwd_d2_n32(smem));
   }
   return e;
 }
 
-int fused_max_warps(int nmax) { return nmax == 32 ? 8 : 12; }
+int fused_max_warps(int nmax, bool bwd) { return (bwd && nmax > 16) ? 8 : 12; }
 
 size_t fused_smem_bytes(int dim, int nmax, int T, int gmax, int tc, int nq, bool bwd) {
   const fused_impl::Lay L(dim, nmax, T, tc, nq, bwd);
@@ -59,7 +63,7 @@ FusedPlan plan_fused(int dim, int nmax, int T, const int* nr, const int* ns, int
     tot += ns[q];
     Nbig = std::max(Nbig, nr[q]);
   }
-  const int maxw = fused_max_warps(nmax);
+  const int maxw = fused_max_warps(nmax, bwd);
   const double cA = 0.5 * Nbig * (Nbig - 1) * 14.0 + 45.0 * Nbig;
   const double cB = 200.0;
   const int gmax_try = (int)std::min<long long>(64, std::max<long long>(1, tot));
@@ -107,10 +111,12 @@ cudaError_t launch_backward(const FusedArgs& a, const BwdLaunchArgs& b, const Fu
   if (dim == 3) {
     if (l.nmax == 8) return launch_bwd_d3_n8(a, b, l, st);
     if (l.nmax == 16) return launch_bwd_d3_n16(a, b, l, st);
+    if (l.nmax == 24) return launch_bwd_d3_n24(a, b, l, st);
     if (l.nmax == 32) return launch_bwd_d3_n32(a, b, l, st);
   } else if (dim == 2) {
     if (l.nmax == 8) return launch_bwd_d2_n8(a, b, l, st);
     if (l.nmax == 16) return launch_bwd_d2_n16(a, b, l, st);
+    if (l.nmax == 24) return launch_bwd_d2_n24(a, b, l, st);
     if (l.nmax == 32) return launch_bwd_d2_n32(a, b, l, st);
   }
   return cudaErrorInvalidValue;
@@ -121,10 +127,12 @@ cudaError_t launch_fused(const FusedArgs& a, const FusedLaunch& l, cudaStream_t 
   if (dim == 3) {
     if (l.nmax == 8) return launch_fused_d3_n8(a, l, st);
     if (l.nmax == 16) return launch_fused_d3_n16(a, l, st);
+    if (l.nmax == 24) return launch_fused_d3_n24(a, l, st);
     if (l.nmax == 32) return launch_fused_d3_n32(a, l, st);
   } else if (dim == 2) {
     if (l.nmax == 8) return launch_fused_d2_n8(a, l, st);
     if (l.nmax == 16) return launch_fused_d2_n16(a, l, st);
+    if (l.nmax == 24) return launch_fused_d2_n24(a, l, st);
     if (l.nmax == 32) return launch_fused_d2_n32(a, l, st);
   }
   return cudaErrorInvalidValue;

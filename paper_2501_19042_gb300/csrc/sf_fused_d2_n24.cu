@@ -1,0 +1,12 @@
+// Fused forward kernel instantiated for dim = 2, up to 24 robots.
+#include "sf_fused_kernel.cuh"
+
+namespace sf {
+cudaError_t launch_fused_d2_n24(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st) {
+  return fused_impl::launch_t<2, 24, 384>(a, l, st);
+}
+cudaError_t prepare_fused_d2_n24(int smem) {
+  return cudaFuncSetAttribute(fused_impl::fused_fwd_kernel<2, 24, 384>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+}  // namespace sf

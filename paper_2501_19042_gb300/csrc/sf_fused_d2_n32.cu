@@ -3,10 +3,10 @@
 
 namespace sf {
 cudaError_t launch_fused_d2_n32(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st) {
-  return fused_impl::launch_t<2, 32, 256>(a, l, st);
+  return fused_impl::launch_t<2, 32, 384>(a, l, st);
 }
 cudaError_t prepare_fused_d2_n32(int smem) {
-  return cudaFuncSetAttribute(fused_impl::fused_fwd_kernel<2, 32, 256>,
+  return cudaFuncSetAttribute(fused_impl::fused_fwd_kernel<2, 32, 384>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 }  // namespace sf

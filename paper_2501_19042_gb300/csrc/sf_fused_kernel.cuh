@@ -39,7 +39,7 @@ constexpr unsigned FULL = 0xffffffffu;
 // RS2 [T] (pair residual per t); RSB [NQ][NMAX] (ball residual partials).
 struct Lay {
   int RS, EP, TC, NQ, T, nmax, dim;
-  int C, LAM, PG, MC, MR, EB, RS2, RSB, FPP, FPR, XB, LB, GXB, U, CW, SB;
+  int C, LAM, XIB, PG, MC, MR, EB, RS2, RSB, FPP, FPR, XB, LB, GXB, U, CW, SB;
   int head;
   __host__ __device__ Lay(int dim_, int nmax_, int T_, int TC_, int NQ_, bool bwd = false) {
     dim = dim_; nmax = nmax_; T = T_; TC = TC_; NQ = NQ_;
@@ -47,7 +47,8 @@ struct Lay {
     EP = nmax * dim + 1;
     C = 0;
     LAM = C + nmax * RS;
-    PG = LAM + nmax * RS;
+    XIB = LAM + nmax * RS;
+    PG = XIB + nmax * RS;
     MC = PG + NQ * nmax * RS;
     MR = MC + dim * NP;
     EB = MR + dim * NP;
@@ -132,6 +133,75 @@ __device__ __forceinline__ void pair_update(const float (&pi)[DIM], const float 
   }
 }
 
+// Positions in the pair phase are kept scaled by M_a^-1 = diag(1/a, 1/a, 1/b),
+// so the distance test of a pair row is |ps_i - ps_j|^2 < 1.
+template <int DIM>
+__device__ __forceinline__ float scaled_d2(const float (&pi)[DIM], const float (&pj)[DIM]) {
+  float s2 = 0.0f;
+#pragma unroll
+  for (int x = 0; x < DIM; ++x) {
+    const float d = pi[x] - pj[x];
+    s2 = fmaf(d, d, s2);
+  }
+  return s2;
+}
+
+// q = e - delta of one pair row from scaled positions: delta = M (ps_i - ps_j);
+// e = delta / sqrt(s2) inside the spheroid, delta outside, (0, 0, b) / (a, 0)
+// at delta = 0. Added to E_i, subtracted from E_j.
+template <int DIM>
+__device__ __forceinline__ void pair_apply_scaled(const float (&pi)[DIM], const float (&pj)[DIM], float (&Ei)[DIM],
+                                                  float (&Ej)[DIM], const ProblemConsts& pc, float& res2) {
+  float ds[DIM];
+#pragma unroll
+  for (int x = 0; x < DIM; ++x) ds[x] = pi[x] - pj[x];
+  float s2 = 0.0f;
+#pragma unroll
+  for (int x = 0; x < DIM; ++x) s2 = fmaf(ds[x], ds[x], s2);
+  const bool zero = (s2 == 0.0f);
+  float f = fmaxf(rsqrtf(s2) - 1.0f, 0.0f);
+  f = zero ? 0.0f : f;
+  float q[DIM];
+#pragma unroll
+  for (int x = 0; x < DIM; ++x) q[x] = f * ds[x] * (x == 2 ? pc.coll_b : pc.coll_a);
+  if (zero) q[DIM == 3 ? 2 : 0] = pc.tie;
+#pragma unroll
+  for (int x = 0; x < DIM; ++x) {
+    Ei[x] += q[x];
+    Ej[x] -= q[x];
+    res2 = fmaf(q[x], q[x], res2);
+  }
+}
+
+// Update of one pair row known to be active on some lane of the warp.
+template <int DIM>
+__device__ __forceinline__ void pair_apply(const float (&pi)[DIM], const float (&pj)[DIM], float (&Ei)[DIM],
+                                           float (&Ej)[DIM], bool valid, const ProblemConsts& pc,
+                                           float& res2) {
+  float d[DIM];
+#pragma unroll
+  for (int x = 0; x < DIM; ++x) d[x] = pi[x] - pj[x];
+  float s2;
+  if (DIM == 3)
+    s2 = fmaf(d[2] * d[2], pc.inv_b2, (d[0] * d[0] + d[1] * d[1]) * pc.inv_a2);
+  else
+    s2 = (d[0] * d[0] + d[1] * d[1]) * pc.inv_a2;
+  s2 = valid ? s2 : 2.0f;
+  const bool zero = (s2 == 0.0f);
+  float f = fmaxf(rsqrtf(s2) - 1.0f, 0.0f);
+  f = zero ? 0.0f : f;
+  float q[DIM];
+#pragma unroll
+  for (int x = 0; x < DIM; ++x) q[x] = f * d[x];
+  if (zero) q[DIM == 3 ? 2 : 0] = pc.tie;
+#pragma unroll
+  for (int x = 0; x < DIM; ++x) {
+    Ei[x] += q[x];
+    Ej[x] -= q[x];
+    res2 = fmaf(q[x], q[x], res2);
+  }
+}
+
 // Pair phase of one chunk [t0, t0 + TCc).
 template <int DIM, int NMAX>
 __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G, int N, int t0, int TCc,
@@ -154,41 +224,96 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
 #pragma unroll
       for (int x = 0; x < DIM; ++x) E[i][x] = 0.0f;
     float res2 = 0.0f;
+    float* ebw = blk + L.EB + tl * L.EP;   // this lane's row of the chunk buffer
     if (NMAX <= 16) {
+      // scaled positions of all robots in registers; lanes past the chunk get
+      // far-apart dummies so that none of their rows tests active
       float p[NMAX][DIM];
 #pragma unroll
       for (int i = 0; i < NMAX; ++i) {
-        if (i < N) state<DIM>(Pr, Cs + i * RS, p[i]);
-        else
+        if (i < N) {
+          state<DIM>(Pr, Cs + i * RS, p[i]);
+#pragma unroll
+          for (int x = 0; x < DIM; ++x) p[i][x] *= (x == 2 ? pc.inv_b : pc.inv_a);
+        } else {
 #pragma unroll
           for (int x = 0; x < DIM; ++x) p[i][x] = 0.0f;
+        }
+        if (!valid) p[i][0] = 4096.0f * (float)i;
       }
+      // a row of pairs (i, j > i) is tested without branches; only a row that
+      // is active on some lane of the warp is walked pair by pair
 #pragma unroll
-      for (int i = 0; i < NMAX; ++i)
+      for (int i = 0; i < NMAX; ++i) {
+        if (i + 1 < N) {
+          bool row = false;
 #pragma unroll
-        for (int j = 0; j < NMAX; ++j)
-          if (j > i && j < N) pair_update<DIM>(p[i], p[j], E[i], E[j], valid, pc, res2);
+          for (int j = 0; j < NMAX; ++j)
+            if (j > i && j < N) row |= scaled_d2<DIM>(p[i], p[j]) < 1.0f;
+          if (__any_sync(FULL, row)) {
+#pragma unroll
+            for (int j = 0; j < NMAX; ++j)
+              if (j > i && j < N)
+                if (__any_sync(FULL, scaled_d2<DIM>(p[i], p[j]) < 1.0f))
+                  pair_apply_scaled<DIM>(p[i], p[j], E[i], E[j], pc, res2);
+          }
+        }
+      }
     } else {
-      // robots in blocks of 8: the block's positions in registers, later
-      // robots recomputed one at a time
+      // scaled positions staged once in the lane's own row of the chunk
+      // buffer (which later receives E); robots in blocks of 8 reloaded
+      // from there, each later robot tested against a block in one group
+#pragma unroll
+      for (int i = 0; i < NMAX; ++i) {
+        if (i < N) {
+          float pi[DIM];
+          state<DIM>(Pr, Cs + i * RS, pi);
+          if (valid)
+#pragma unroll
+            for (int x = 0; x < DIM; ++x) ebw[i * DIM + x] = pi[x] * (x == 2 ? pc.inv_b : pc.inv_a);
+        }
+      }
 #pragma unroll
       for (int I0 = 0; I0 < NMAX; I0 += 8) {
         if (I0 < N) {
           float pI[8][DIM];
 #pragma unroll
-          for (int a = 0; a < 8; ++a) state<DIM>(Pr, Cs + (I0 + a) * RS, pI[a]);
+          for (int a = 0; a < 8; ++a) {
+#pragma unroll
+            for (int x = 0; x < DIM; ++x) pI[a][x] = (valid && I0 + a < N) ? ebw[(I0 + a) * DIM + x] : 0.0f;
+            if (!valid) pI[a][0] = 4096.0f * (float)(I0 + a);
+          }
+          bool blkrow = false;
 #pragma unroll
           for (int a = 0; a < 8; ++a)
 #pragma unroll
             for (int b = 0; b < 8; ++b)
-              if (b > a && I0 + b < N) pair_update<DIM>(pI[a], pI[b], E[I0 + a], E[I0 + b], valid, pc, res2);
+              if (b > a && I0 + b < N) blkrow |= scaled_d2<DIM>(pI[a], pI[b]) < 1.0f;
+          if (__any_sync(FULL, blkrow)) {
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+              for (int b = 0; b < 8; ++b)
+                if (b > a && I0 + b < N)
+                  if (__any_sync(FULL, scaled_d2<DIM>(pI[a], pI[b]) < 1.0f))
+                    pair_apply_scaled<DIM>(pI[a], pI[b], E[I0 + a], E[I0 + b], pc, res2);
+          }
 #pragma unroll
           for (int j = 0; j < NMAX; ++j) {
             if (j >= I0 + 8 && j < N) {
               float pj[DIM];
-              state<DIM>(Pr, Cs + j * RS, pj);
 #pragma unroll
-              for (int a = 0; a < 8; ++a) pair_update<DIM>(pI[a], pj, E[I0 + a], E[j], valid, pc, res2);
+              for (int x = 0; x < DIM; ++x) pj[x] = valid ? ebw[j * DIM + x] : 0.0f;
+              if (!valid) pj[0] = 4096.0f * (float)j;
+              bool grp = false;
+#pragma unroll
+              for (int a = 0; a < 8; ++a) grp |= scaled_d2<DIM>(pI[a], pj) < 1.0f;
+              if (__any_sync(FULL, grp)) {
+#pragma unroll
+                for (int a = 0; a < 8; ++a)
+                  if (__any_sync(FULL, scaled_d2<DIM>(pI[a], pj) < 1.0f))
+                    pair_apply_scaled<DIM>(pI[a], pj, E[I0 + a], E[j], pc, res2);
+              }
             }
           }
         }
@@ -483,7 +608,8 @@ __device__ void prologue(const Cta<DIM, NMAX>& c, int T, const float4* basis, co
 // Loads (xi, lambda) of every sample into C, LAM (rows beyond N and the
 // padding column are zero) and clears the partials.
 template <int DIM, int NMAX>
-__device__ void load_state(const Cta<DIM, NMAX>& c, const float* xi, const float* lam, const float* fallback_xi) {
+__device__ void load_state(const Cta<DIM, NMAX>& c, const float* xi, const float* lam, const float* fallback_xi,
+                           const float* xi_bar_src) {
   constexpr int RS = DIM * NP;
   for (int v = c.tid; v < c.G * NMAX * RS; v += c.nthr) {
     const int s = v / (NMAX * RS), rem = v % (NMAX * RS);
@@ -497,6 +623,7 @@ __device__ void load_state(const Cta<DIM, NMAX>& c, const float* xi, const float
     }
     b[c.L.C + rem] = cv;
     b[c.L.LAM + rem] = l;
+    b[c.L.XIB + rem] = (i < c.N && k < NV) ? xi_bar_src[c.gidx(s, x, i, k)] : 0.0f;
     for (int q = 0; q < c.L.NQ; ++q) b[c.L.PG + q * NMAX * RS + rem] = 0.0f;
   }
 }
@@ -548,7 +675,7 @@ __device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, 
       const float lam = fmaf(rho, g, blk[L.LAM + o]);
       dl2 = fmaf(lam - blk[L.LAM + o], lam - blk[L.LAM + o], dl2);
       blk[L.LAM + o] = lam;
-      const float r = fmaf(rho, g, lam) + xi_bar[c.gidx(s, x, i, k)];
+      const float r = fmaf(rho, g, lam) + blk[L.XIB + o];
       blk[L.PG + o] = r;
       sr += r;
       sc += blk[L.C + o];
@@ -587,13 +714,18 @@ __device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, 
     float dx2 = 0.0f;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
+      float w1[NV], s1[NV], dw[NV], ds[NV];
+      row_from(c.OPS + OPS_W1 + k * NP, w1);
+      row_from(c.OPS + OPS_S1 + k * NP, s1);
+      row_from(c.OPS + OPS_DW + k * NP, dw);
+      row_from(c.OPS + OPS_DS + k * NP, ds);
       float acc = c.BETA[o + k];
 #pragma unroll
       for (int m = 0; m < NV; ++m) {
-        acc = fmaf(c.OPS[OPS_W1 + k * NP + m], cc[m], acc);
-        acc = fmaf(c.OPS[OPS_S1 + k * NP + m], r[m], acc);
-        acc = fmaf(c.OPS[OPS_DW + k * NP + m], cm[m], acc);
-        acc = fmaf(c.OPS[OPS_DS + k * NP + m], rm[m], acc);
+        acc = fmaf(w1[m], cc[m], acc);
+        acc = fmaf(s1[m], r[m], acc);
+        acc = fmaf(dw[m], cm[m], acc);
+        acc = fmaf(ds[m], rm[m], acc);
       }
       out[k] = acc;
       dx2 = fmaf(acc - cc[k], acc - cc[k], dx2);
@@ -642,14 +774,22 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
   const bool fp = A.fp_res2 != nullptr;
 
   prologue<DIM, NMAX>(c, T, A.basis, A.ops, A.start, A.goal, A.start_va, A.goal_va);
-  load_state<DIM, NMAX>(c, A.xi0, A.lam0, A.xi_bar);
+  load_state<DIM, NMAX>(c, A.xi0, A.lam0, A.xi_bar, A.xi_bar);
   for (int s = c.tid; s < G; s += c.nthr) c.blk(s)[L.FPR] = 0.0f;
   __syncthreads();
 
+  // checkpoints: (xi, lambda) at iterations 0, ck, 2 ck, ...; after them a
+  // tail holding every iterate of the last segment (last_ck .. K), so that
+  // the backward does not recompute that segment
+  const int n_ck = (pc.K + A.ck_every - 1) / A.ck_every;
+  const int last_ck = (n_ck - 1) * A.ck_every;
+  float* tail = A.ckpt ? A.ckpt + (size_t)n_ck * 2 * A.total_coefs : nullptr;
   for (int it = 0; it < pc.K; ++it) {
     if (A.ckpt && it % A.ck_every == 0) write_checkpoint<DIM, NMAX>(c, A.ckpt, it / A.ck_every, A.total_coefs);
+    if (tail && it >= last_ck) write_checkpoint<DIM, NMAX>(c, tail, it - last_ck, A.total_coefs);
     fwd_iteration<DIM, NMAX>(c, pc, A.xi_bar, it, it == pc.K - 1, A.hist, A.total_samples, fp);
   }
+  if (tail) write_checkpoint<DIM, NMAX>(c, tail, pc.K - last_ck, A.total_coefs);
 
   // ---- final residual, Eq. (primal_residual); robot rows beyond N of the
   // xi^{K-1} copy are zero-filled first

@@ -54,6 +54,8 @@ struct ProblemConsts {
   int dim, T, K;
   float rho;
   float inv_a2, inv_b2;  // 1/a^2, 1/b^2 of the collision spheroid
+  float inv_a, inv_b;    // 1/a, 1/b
+  float coll_a, coll_b;  // a, b
   float tie;             // e of a pair at delta = 0: (0,0,b) in 3D, (a,0) in 2D
   float v_max, a_max;
   int use_v, use_a;
@@ -145,7 +147,7 @@ struct FusedLaunch {
 };
 size_t fused_smem_bytes(int dim, int nmax, int T, int gmax, int tc, int nq, bool bwd = false);
 cudaError_t launch_fused(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st);
-int fused_max_warps(int nmax);
+int fused_max_warps(int nmax, bool bwd);
 cudaError_t prepare_kernels(int dim, int smem);
 
 // Launch shape of the fused kernel for one group of scenes: samples per CTA,
