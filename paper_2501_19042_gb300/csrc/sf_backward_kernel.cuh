@@ -75,56 +75,84 @@ __device__ void adj_pair_phase(const Cta<DIM, NMAX>& c, const ProblemConsts& pc,
     float* eb = blk + L.EB + tl * L.EP;
     if (valid)
       for (int q = 0; q < N * DIM; ++q) eb[q] = 0.0f;
-    float p[NMAX][DIM], ug[NMAX][DIM];
+    // scaled positions of xi^k (far-apart dummies past the chunk); rows of
+    // pairs are tested without branches, the positions of g_bar are formed
+    // only when some row of the warp is active
+    float p[NMAX][DIM];
 #pragma unroll
     for (int i = 0; i < NMAX; ++i) {
       if (i < N) {
         state<DIM>(Pr, blk + L.C + i * RS, p[i]);
-        state<DIM>(Pr, blk + L.U + i * RS, ug[i]);
+#pragma unroll
+        for (int x = 0; x < DIM; ++x) p[i][x] *= (x == 2 ? pc.inv_b : pc.inv_a);
       } else {
 #pragma unroll
-        for (int x = 0; x < DIM; ++x) { p[i][x] = 0.0f; ug[i][x] = 0.0f; }
+        for (int x = 0; x < DIM; ++x) p[i][x] = 0.0f;
       }
+      if (!valid) p[i][0] = 4096.0f * (float)i;
     }
+    bool anyrow = false;
 #pragma unroll
     for (int i = 0; i < NMAX; ++i)
 #pragma unroll
-      for (int j = 0; j < NMAX; ++j) {
-        if (j > i && j < N) {
-          float d[DIM];
+      for (int j = 0; j < NMAX; ++j)
+        if (j > i && j < N) anyrow |= scaled_d2<DIM>(p[i], p[j]) < 1.0f;
+    if (!__any_sync(FULL, anyrow)) continue;
+    float ug[NMAX][DIM];
 #pragma unroll
-          for (int x = 0; x < DIM; ++x) d[x] = p[i][x] - p[j][x];
-          float s2;
-          if (DIM == 3)
-            s2 = fmaf(d[2] * d[2], pc.inv_b2, (d[0] * d[0] + d[1] * d[1]) * pc.inv_a2);
-          else
-            s2 = (d[0] * d[0] + d[1] * d[1]) * pc.inv_a2;
-          s2 = valid ? s2 : 2.0f;
-          const bool act = s2 < 1.0f;
-          if (__any_sync(FULL, act)) {
-            float U[DIM], m[DIM];
-            float du = 0.0f;
+    for (int i = 0; i < NMAX; ++i) {
+      if (i < N) state<DIM>(Pr, blk + L.U + i * RS, ug[i]);
+      else
 #pragma unroll
-            for (int x = 0; x < DIM; ++x) {
-              U[x] = ug[i][x] - ug[j][x];
-              m[x] = d[x] * (x == 2 ? pc.inv_b2 : pc.inv_a2);
-              du = fmaf(d[x], U[x], du);
-            }
-            const bool zero = (s2 == 0.0f);
-            const float inv = rsqrtf(zero ? 1.0f : s2);
-            const float f = act ? (zero ? -1.0f : inv - 1.0f) : 0.0f;
-            const float w = (act && !zero) ? inv * inv * inv * du : 0.0f;
-            if (valid && act) {
+        for (int x = 0; x < DIM; ++x) ug[i][x] = 0.0f;
+    }
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i) {
+      if (i + 1 < N) {
+        bool row = false;
+#pragma unroll
+        for (int j = 0; j < NMAX; ++j)
+          if (j > i && j < N) row |= scaled_d2<DIM>(p[i], p[j]) < 1.0f;
+        if (!__any_sync(FULL, row)) continue;
+#pragma unroll
+        for (int j = 0; j < NMAX; ++j) {
+          if (j > i && j < N) {
+            float ds[DIM];
+#pragma unroll
+            for (int x = 0; x < DIM; ++x) ds[x] = p[i][x] - p[j][x];
+            float s2 = 0.0f;
+#pragma unroll
+            for (int x = 0; x < DIM; ++x) s2 = fmaf(ds[x], ds[x], s2);
+            const bool act = valid && s2 < 1.0f;
+            if (__any_sync(FULL, act)) {
+              // delta = M ds; M^-2 delta = ds / (a, a, b)
+              float U[DIM], m[DIM], d[DIM];
+              float du = 0.0f;
 #pragma unroll
               for (int x = 0; x < DIM; ++x) {
-                const float db = fmaf(f, U[x], -w * m[x]);
-                eb[i * DIM + x] += db;
-                eb[j * DIM + x] -= db;
+                const float ax = x == 2 ? pc.coll_b : pc.coll_a;
+                d[x] = ds[x] * ax;
+                m[x] = ds[x] / ax;
+                U[x] = ug[i][x] - ug[j][x];
+                du = fmaf(d[x], U[x], du);
+              }
+              const bool zero = (s2 == 0.0f);
+              const float inv = rsqrtf(zero ? 1.0f : s2);
+              const float f = act ? (zero ? -1.0f : inv - 1.0f) : 0.0f;
+              const float w = (act && !zero) ? inv * inv * inv * du : 0.0f;
+              if (act) {
+#pragma unroll
+                for (int x = 0; x < DIM; ++x) {
+                  const float db = fmaf(f, U[x], -w * m[x]);
+                  eb[i * DIM + x] += db;
+                  eb[j * DIM + x] -= db;
+                }
               }
             }
           }
         }
       }
+    }
   }
 }
 
