@@ -231,6 +231,8 @@ def run_gpu(args):
             line["differentiation"] = diff_timing(P, dev)
         if not args.no_batching:
             line["batching"] = batching_timing(P, dev)
+        if not args.no_precision:
+            line["precision"] = precision_timing(P, dev)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(spec, sc, args.cpu_samples)
         print(json.dumps(line), flush=True)
@@ -268,6 +270,55 @@ def diff_timing(P, dev):
     bwd = timed(lambda: f.project_backward(xb, st, gl, spec.K, ck, grad_xi=g))
     return {"workload": f"3D N={spec.n_robots}, S={spec.n_samples}, T={spec.T}, K={spec.K}, checkpoint every 10",
             "fwd_ms": fwd, "train_fwd_ms": trn, "bwd_ms": bwd, "bwd_over_fwd": bwd / fwd}
+
+
+def precision_timing(P, dev, n_check: int = 64, steps: int = 3):
+    """The precision workload: N=32 robots 3D (496 pairs), S=2048, T=120,
+    K=200, sample init. Per precision mode of the fused forward: time per
+    call (CUDA events, mean of `steps` after one warm-up), median final
+    ||r_p|| over all samples, and against the FP64 oracle on samples
+    0..n_check-1: relative L2 of xi^K per sample and |final ||r_p|| difference|."""
+    import torch
+    import oracle
+    spec = si.config_n32_3d()
+    sc = si.scene(spec, 3)
+    oracle.build()
+    pb = oracle.Problem(dim=3, n_robots=spec.n_robots, T=spec.T, order=spec.order, t_final=spec.t_final,
+                        rho=RHO, coll_a=spec.coll, coll_b=spec.coll, v_max=spec.v_max, a_max=spec.a_max)
+    t_or = time.perf_counter()
+    ref = oracle.run_batch(pb, sc.start, sc.goal, sc.xi_bar[:n_check], K=spec.K, n_threads=os.cpu_count() or 1)
+    t_or = time.perf_counter() - t_or
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    xb, st, gl = t(sc.xi_bar), t(sc.start), t(sc.goal)
+    xr = np.asarray(ref["xi"]).reshape(n_check, -1)
+    modes = {}
+    for prec in ("fp32", "bf16", "fp16"):
+        try:
+            f = P.SafetyFilter(dim=3, T=spec.T, rho=RHO, coll_a=spec.coll, v_max=spec.v_max, a_max=spec.a_max,
+                               max_robots=spec.n_robots, t_final=spec.t_final, precision=prec, device=dev.index)
+            out = f.project(xb, st, gl, spec.K)
+        except Exception as e:  # a mode this library does not build
+            modes[prec] = {"unavailable": str(e).splitlines()[0][:160]}
+            continue
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            f.project(xb, st, gl, spec.K, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        f.sync_status()
+        xi = out.xi[:n_check].double().cpu().numpy().reshape(n_check, -1)
+        err = np.linalg.norm(xi - xr, axis=1) / np.linalg.norm(xr, axis=1)
+        dres = np.abs(out.residual[:n_check].double().cpu().numpy() - np.asarray(ref["rp_final"]))
+        modes[prec] = {"ms": ms, "samples_per_s": spec.n_samples / (ms * 1e-3),
+                       "median_final_residual": float(out.residual.median()),
+                       "xi_rel_l2_median": float(np.median(err)), "xi_rel_l2_max": float(err.max()),
+                       "resid_absdiff_max": float(dres.max()), "launch_shape": f.launch_shape()}
+    return {"workload": f"3D N={spec.n_robots}, S={spec.n_samples}, T={spec.T}, K={spec.K}, sample init, "
+                        f"rho={RHO}; errors vs the FP64 oracle on samples 0..{n_check - 1}",
+            "oracle_seconds": t_or, "modes": modes}
 
 
 def batching_timing(P, dev):
@@ -379,6 +430,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--no-batching", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

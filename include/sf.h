@@ -59,9 +59,19 @@ typedef enum {
   SF_ERR_WORKSPACE = 7      /* workspace missing or too small */
 } sf_status;
 
-/* Arithmetic of the contractions (coefficients -> states, and F^T of the
- * residual). The projections, residuals and multiplier updates are float32 in
- * every mode; the one-time factorisation of the KKT matrix is float64. */
+/* Arithmetic of the contractions (coefficients -> states, Eq. (poly), and
+ * F^T of the residual in the lambda step of the Appendix). The projections,
+ * residuals, multiplier updates and the xi step are float32 in every mode;
+ * the one-time factorisation of the KKT matrix is float64.
+ * The 16-bit modes run those contractions on warp-level tensor-core MMAs
+ * with float32 accumulation, in the fused form of sf_project only (the plain
+ * form, sf_project_train, checkpoints and sf_project_backward return
+ * SF_ERR_UNSUPPORTED on such a handle). Products with the coefficients
+ * (positions, velocities, accelerations) are three-term: the operands are
+ * split into a 16-bit part and its 16-bit rounding remainder and the
+ * remainder x remainder term is dropped. F^T of the residual takes the
+ * residual form (only the small residuals enter 16 bits): single-term in
+ * fp16, three-term in bf16. */
 typedef enum {
   SF_PREC_FP32 = 0,  /* float32 everywhere */
   SF_PREC_BF16 = 1,  /* tensor-core bf16 products, float32 accumulation */
@@ -170,9 +180,10 @@ sf_status sf_project_host(sf_handle *h, void *stream, const sf_batch *batch, int
 unsigned long long sf_launch_count(const sf_handle *h);
 
 /* Launch shape of the fused form: samples per CTA (G), warps per CTA, time
- * steps per chunk (tc). Values <= 0 leave that choice to the library's cost
- * model. Applies to later sf_project calls on the handle; a shape that does
- * not fit in shared memory makes them fail with SF_ERR_UNSUPPORTED. */
+ * steps per chunk (tc; even in the 16-bit modes). Values <= 0 leave that
+ * choice to the library's cost model. Applies to later sf_project calls on
+ * the handle; a shape that does not fit in shared memory (or an odd tc in a
+ * 16-bit mode) makes them fail with SF_ERR_UNSUPPORTED. */
 sf_status sf_set_launch_shape(sf_handle *h, int samples_per_cta, int warps, int time_chunk);
 
 /* Shape of the last fused launch of the handle: out[0..3] = G, warps, tc and

@@ -30,7 +30,16 @@ def _nvcc() -> str:
 
 
 def sources():
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+    """The translation units, the slowest to compile first (adjoint and
+    tensor-core kernels, larger robot buckets)."""
+    def cost(f):
+        heavy = ("backward" in f) * 2 + ("_tc_" in f)
+        n = 0
+        for tok in f[:-3].split("_"):
+            if tok.startswith("n") and tok[1:].isdigit():
+                n = int(tok[1:])
+        return (-heavy, -n, f)
+    return [os.path.join(CSRC, f) for f in sorted((f for f in os.listdir(CSRC) if f.endswith(".cu")), key=cost)]
 
 
 def _deps_mtime():
@@ -57,7 +66,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return obj
 
     srcs = sources()
-    with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with ThreadPoolExecutor(max_workers=max(1, min(os.cpu_count() or 1, len(srcs)))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]

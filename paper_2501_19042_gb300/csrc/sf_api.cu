@@ -115,6 +115,7 @@ struct FusedRequest {
   float* ckpt = nullptr;
   float* fp_res2 = nullptr;
   bool backward = false;
+  int prec = 0;             // forward only: 0 float32 form, 1 / 2 tensor-core form
   BwdLaunchArgs bwd{};
 };
 
@@ -175,7 +176,7 @@ sf_status build_groups(sf_handle* h, const sf_batch* b, int K, long long S, cons
         plan = hit->second;
       } else {
         plan = plan_fused(dim, nmax, T, nr.data(), ns.data(), (int)nr.size(), h->num_sms, h->max_smem_optin,
-                          h->force_G, h->force_warps, h->force_tc, rq.backward);
+                          h->force_G, h->force_warps, h->force_tc, rq.backward, nullptr, 0, rq.prec);
       }
       if (plan.G == 0) return fail(h, SF_ERR_UNSUPPORTED, "no fused launch shape fits in shared memory");
       FusedArgs& a = lg.a;
@@ -224,7 +225,8 @@ sf_status build_groups(sf_handle* h, const sf_batch* b, int K, long long S, cons
       l.warps = plan.warps;
       l.tc = plan.tc;
       l.nq = plan.nq;
-      l.smem = fused_smem_bytes(dim, nmax, T, gmax, plan.tc, plan.nq, rq.backward);
+      l.prec = rq.prec;
+      l.smem = fused_smem_bytes(dim, nmax, T, gmax, plan.tc, plan.nq, rq.backward, rq.prec);
       if (l.smem > h->max_smem_optin) return fail(h, SF_ERR_UNSUPPORTED, "launch shape exceeds shared memory");
       h->last_plan[0] = plan.G;
       h->last_plan[1] = plan.warps;
@@ -332,7 +334,7 @@ sf_status sf_create(const sf_problem* pb, int device, sf_handle** out) {
     sf_destroy(h);
     return e == cudaErrorInvalidValue ? SF_ERR_INVALID_ARG : SF_ERR_CUDA;
   }
-  e = prepare_kernels(pb->dim, (int)h->max_smem_optin);
+  e = prepare_kernels(pb->dim, (int)h->max_smem_optin, pb->precision);
   for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
     e = cudaStreamCreateWithFlags(&h->aux[q], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join[q], cudaEventDisableTiming);
@@ -399,8 +401,8 @@ sf_status sf_project(sf_handle* h, void* stream, const sf_batch* b, int K, int f
   if (S > 0 && (!xi_out || !lam_out || !resid_out))
     return fail(h, SF_ERR_INVALID_ARG, "xi_out / lambda_out / residual_out is NULL");
   if (form != SF_FORM_FUSED && form != SF_FORM_PLAIN) return fail(h, SF_ERR_INVALID_ARG, "unknown form");
-  if (h->pb.precision != SF_PREC_FP32)
-    return fail(h, SF_ERR_UNSUPPORTED, "only SF_PREC_FP32 is built into this library");
+  if (form == SF_FORM_PLAIN && h->pb.precision != SF_PREC_FP32)
+    return fail(h, SF_ERR_UNSUPPORTED, "the plain form is float32 only");
   if (S == 0) return SF_OK;
   DeviceGuard g(h->device);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -458,8 +460,11 @@ sf_status sf_project(sf_handle* h, void* stream, const sf_batch* b, int K, int f
   rq.resid_out = resid_out;
   rq.hist = resid_hist;
   rq.ckpt = reinterpret_cast<float*>(checkpoints);
+  rq.prec = h->pb.precision;
   if (checkpoints && h->pb.checkpoint_every <= 0)
     return fail(h, SF_ERR_INVALID_ARG, "checkpoints need a handle with checkpoint_every > 0");
+  if (checkpoints && h->pb.precision != SF_PREC_FP32)
+    return fail(h, SF_ERR_UNSUPPORTED, "checkpoints (for the float32 adjoint) need SF_PREC_FP32");
   return run_fused(h, st, b, K, S, rq);
 }
 
@@ -543,7 +548,6 @@ sf_status sf_autotune(sf_handle* h, void* stream, const sf_batch* b, int K_probe
   if (K_probe < 1 || n_candidates < 1 || n_candidates > 64)
     return fail(h, SF_ERR_INVALID_ARG, "K_probe >= 1 and 1 <= n_candidates <= 64");
   if (S > 0 && (!xi_out || !lam_out || !resid_out)) return fail(h, SF_ERR_INVALID_ARG, "outputs are NULL");
-  if (h->pb.precision != SF_PREC_FP32) return fail(h, SF_ERR_UNSUPPORTED, "only SF_PREC_FP32 is built");
   if (S == 0) return SF_OK;
   DeviceGuard g(h->device);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -551,6 +555,7 @@ sf_status sf_autotune(sf_handle* h, void* stream, const sf_batch* b, int K_probe
   rq.xi_out = xi_out;
   rq.lam_out = lam_out;
   rq.resid_out = resid_out;
+  rq.prec = h->pb.precision;
   const int fG = h->force_G, fW = h->force_warps, fT = h->force_tc;
   h->force_G = h->force_warps = h->force_tc = 0;
   h->use_tuned = false;
@@ -568,7 +573,7 @@ sf_status sf_autotune(sf_handle* h, void* stream, const sf_batch* b, int K_probe
     }
     std::vector<FusedPlan> top(n_candidates);
     plan_fused(h->pb.dim, lg.l.nmax, h->pb.T, nr.data(), ns.data(), (int)nr.size(), h->num_sms, h->max_smem_optin,
-               0, 0, 0, false, top.data(), n_candidates);
+               0, 0, 0, false, top.data(), n_candidates, rq.prec);
     float best_ms = INFINITY;
     FusedPlan best = top[0];
     for (int c = 0; c < n_candidates && e == cudaSuccess; ++c) {
@@ -590,7 +595,7 @@ sf_status sf_autotune(sf_handle* h, void* stream, const sf_batch* b, int K_probe
       t.l.warps = p.warps;
       t.l.tc = p.tc;
       t.l.nq = p.nq;
-      t.l.smem = fused_smem_bytes(h->pb.dim, t.l.nmax, h->pb.T, gmax, p.tc, p.nq, false);
+      t.l.smem = fused_smem_bytes(h->pb.dim, t.l.nmax, h->pb.T, gmax, p.tc, p.nq, false, rq.prec);
       if (t.l.smem > h->max_smem_optin) continue;
       float ms_sum = 0.0f;
       for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {   // first run warms up

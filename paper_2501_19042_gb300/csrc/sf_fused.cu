@@ -12,18 +12,39 @@ namespace sf {
   cudaError_t launch_fused_d##D##_n##NM(const FusedArgs&, const FusedLaunch&, cudaStream_t);           \
   cudaError_t launch_bwd_d##D##_n##NM(const FusedArgs&, const BwdLaunchArgs&, const FusedLaunch&,      \
                                       cudaStream_t);
+#define SF_DECL_TC(D, NM)                                                                          \
+  cudaError_t launch_fused_tc1_d##D##_n##NM(const FusedArgs&, const FusedLaunch&, cudaStream_t);  \
+  cudaError_t launch_fused_tc2_d##D##_n##NM(const FusedArgs&, const FusedLaunch&, cudaStream_t);
 SF_DECL(2, 8) SF_DECL(2, 16) SF_DECL(2, 24) SF_DECL(2, 32) SF_DECL(3, 8) SF_DECL(3, 16) SF_DECL(3, 24) SF_DECL(3, 32)
+SF_DECL_TC(2, 8) SF_DECL_TC(2, 16) SF_DECL_TC(2, 24) SF_DECL_TC(2, 32)
+SF_DECL_TC(3, 8) SF_DECL_TC(3, 16) SF_DECL_TC(3, 24) SF_DECL_TC(3, 32)
 #undef SF_DECL
-#define SF_PREP(D, NM) cudaError_t prepare_fused_d##D##_n##NM(int); cudaError_t prepare_bwd_d##D##_n##NM(int);
+#undef SF_DECL_TC
+#define SF_PREP(D, NM) cudaError_t prepare_fused_d##D##_n##NM(int); cudaError_t prepare_bwd_d##D##_n##NM(int); \
+  cudaError_t prepare_fused_tc1_d##D##_n##NM(int); cudaError_t prepare_fused_tc2_d##D##_n##NM(int);
 SF_PREP(2, 8) SF_PREP(2, 16) SF_PREP(2, 24) SF_PREP(2, 32) SF_PREP(3, 8) SF_PREP(3, 16) SF_PREP(3, 24) SF_PREP(3, 32)
 #undef SF_PREP
 
 // Raises the dynamic shared-memory limit of every fused / adjoint kernel of
-// this dimension once, at handle creation, so that no launch (and no stream
-// capture) has to configure a kernel.
-cudaError_t prepare_kernels(int dim, int smem) {
+// this dimension (and, for a 16-bit precision, of the tensor-core kernels)
+// once, at handle creation, so that no launch (and no stream capture) has to
+// configure a kernel.
+cudaError_t prepare_kernels(int dim, int smem, int prec) {
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+  if (prec == 1 && dim == 3) {
+    chk(prepare_fused_tc1_d3_n8(smem)); chk(prepare_fused_tc1_d3_n16(smem)); chk(prepare_fused_tc1_d3_n24(smem));
+    chk(prepare_fused_tc1_d3_n32(smem));
+  } else if (prec == 1) {
+    chk(prepare_fused_tc1_d2_n8(smem)); chk(prepare_fused_tc1_d2_n16(smem)); chk(prepare_fused_tc1_d2_n24(smem));
+    chk(prepare_fused_tc1_d2_n32(smem));
+  } else if (prec == 2 && dim == 3) {
+    chk(prepare_fused_tc2_d3_n8(smem)); chk(prepare_fused_tc2_d3_n16(smem)); chk(prepare_fused_tc2_d3_n24(smem));
+    chk(prepare_fused_tc2_d3_n32(smem));
+  } else if (prec == 2) {
+    chk(prepare_fused_tc2_d2_n8(smem)); chk(prepare_fused_tc2_d2_n16(smem)); chk(prepare_fused_tc2_d2_n24(smem));
+    chk(prepare_fused_tc2_d2_n32(smem));
+  }
   if (dim == 3) {
     chk(prepare_fused_d3_n8(smem)); chk(prepare_fused_d3_n16(smem)); chk(prepare_fused_d3_n24(smem));
     chk(prepare_fused_d3_n32(smem));
@@ -40,8 +61,8 @@ cudaError_t prepare_kernels(int dim, int smem) {
 
 int fused_max_warps(int nmax, bool bwd) { return (bwd && nmax > 16) ? 8 : 12; }
 
-size_t fused_smem_bytes(int dim, int nmax, int T, int gmax, int tc, int nq, bool bwd) {
-  const fused_impl::Lay L(dim, nmax, T, tc, nq, bwd);
+size_t fused_smem_bytes(int dim, int nmax, int T, int gmax, int tc, int nq, bool bwd, int prec) {
+  const fused_impl::Lay L(dim, nmax, T, tc, nq, bwd, prec != 0);
   return sizeof(float) * ((size_t)L.head + (size_t)gmax * L.SB);
 }
 
@@ -49,10 +70,13 @@ size_t fused_smem_bytes(int dim, int nmax, int T, int gmax, int tc, int nq, bool
 // of the contraction phase (per (sample, robot, t)), padded to whole rounds
 // of the CTA's threads, over an issue rate that saturates at 4 warp
 // instructions per cycle; plus a charge per block-wide barrier. The CTA count
-// over the SM count gives the number of waves.
+// over the SM count gives the number of waves. The tensor-core form (prec
+// 1 / 2) counts warp units instead: (sample, 16-step block) for the
+// positions, (sample, range of blocks) for the contraction; its time chunk
+// is even and its ranges at most one per block.
 FusedPlan plan_fused(int dim, int nmax, int T, const int* nr, const int* ns, int n_scenes, int num_sms,
                      size_t smem_cap, int force_G, int force_warps, int force_tc, bool bwd, FusedPlan* top,
-                     int n_top) {
+                     int n_top, int prec) {
   FusedPlan best;
   best.G = 0;
   best.cost = INFINITY;
@@ -66,12 +90,63 @@ FusedPlan plan_fused(int dim, int nmax, int T, const int* nr, const int* ns, int
   const int maxw = fused_max_warps(nmax, bwd);
   const double cA = 0.5 * Nbig * (Nbig - 1) * 14.0 + 45.0 * Nbig;
   const double cB = 200.0;
+  const int MT = (dim * nmax + 15) / 16, NJ = nmax / 8;
+  // tensor-core form: pair tests per lane; per positions unit; per
+  // contraction block of 16 steps and per contraction unit; latencies of a
+  // positions unit and of a contraction block (a unit's dependent chain)
+  const double cA_tc = 0.5 * Nbig * (Nbig - 1) * 8.0 + 8.0 * Nbig;
+  const double cP_tc = 40.0 * MT;
+  const double cC_tc = 2.0 * (2.0 * (3.0 * MT + 14.0 * NJ + 4.0) + 8.0);
+  const double cU_tc = 26.0 * MT;
+  const double latP = 300.0, latC = 480.0;
+  auto add_top = [&](const FusedPlan& cand) {
+    if (cand.cost < best.cost) best = cand;
+    if (top && n_top > 0) {
+      // keep the n_top cheapest candidates, sorted by model cost
+      int pos = n_top;
+      while (pos > 0 && (top[pos - 1].G == 0 || cand.cost < top[pos - 1].cost)) --pos;
+      if (pos < n_top) {
+        for (int q = n_top - 1; q > pos; --q) top[q] = top[q - 1];
+        top[pos] = cand;
+      }
+    }
+  };
   const int gmax_try = (int)std::min<long long>(64, std::max<long long>(1, tot));
   for (int G = 1; G <= gmax_try; ++G) {
     if (force_G > 0 && G != force_G) continue;
     long long ctas = 0;
     for (int q = 0; q < n_scenes; ++q) ctas += (ns[q] + std::min(G, std::max(ns[q], 1)) - 1) / std::min(G, std::max(ns[q], 1));
     const double waves = std::ceil((double)ctas / num_sms);
+    if (prec != 0) {
+      int prev_tc = 0;
+      for (int nch = 1; nch <= 6; ++nch) {
+        int tc = (T + nch - 1) / nch;
+        tc += tc & 1;
+        if (tc == prev_tc) continue;
+        prev_tc = tc;
+        if (force_tc > 0 && tc != force_tc) continue;
+        const int nkb = (tc + 15) / 16;
+        const int real_nch = (T + tc - 1) / tc;
+        for (int w = 4; w <= maxw; ++w) {
+          if (force_warps > 0 && w != force_warps) continue;
+          const double rate = std::min(4.0, w / 2.0);
+          const double p_rounds = std::ceil((double)G * nkb / w);
+          const double a_rounds = std::ceil((double)G * tc / (32.0 * w));
+          for (int nq = 1; nq <= nkb; ++nq) {
+            const size_t smem = fused_smem_bytes(dim, nmax, T, G, tc, nq, bwd, prec);
+            if (smem > smem_cap) continue;
+            const double c_rounds = std::ceil((double)G * nq / w);
+            const double kbq = std::ceil((double)nkb / nq);
+            const double tP = std::max(p_rounds * w * cP_tc / rate, p_rounds * latP);
+            const double tC = std::max(c_rounds * w * (kbq * cC_tc + cU_tc) / rate, c_rounds * kbq * latC);
+            const double per_iter = real_nch * (tP + a_rounds * w * cA_tc / rate + tC) +
+                                    (3.0 * real_nch + 2.0) * 400.0 + 24.0 * G * Nbig * dim * 4.0 / rate;
+            add_top(FusedPlan{G, w, tc, nq, smem, waves * per_iter});
+          }
+        }
+      }
+      continue;
+    }
     for (int nch = 1; nch <= 6; ++nch) {
       const int tc = (T + nch - 1) / nch;
       if (force_tc > 0 && tc != force_tc) continue;
@@ -88,18 +163,7 @@ FusedPlan plan_fused(int dim, int nmax, int T, const int* nr, const int* ns, int
         const double tq = std::ceil((double)tc / nq);
         const double per_iter = real_nch * (a_rounds * w * cA + b_rounds * w * tq * cB) / rate +
                                 (2.0 * real_nch + 2.0) * 400.0 + 24.0 * G * Nbig * dim * 4.0 / rate;
-        const double cost = waves * per_iter;
-        const FusedPlan cand{G, w, tc, nq, smem, cost};
-        if (cost < best.cost) best = cand;
-        if (top && n_top > 0) {
-          // keep the n_top cheapest candidates, sorted by model cost
-          int pos = n_top;
-          while (pos > 0 && (top[pos - 1].G == 0 || cost < top[pos - 1].cost)) --pos;
-          if (pos < n_top) {
-            for (int q = n_top - 1; q > pos; --q) top[q] = top[q - 1];
-            top[pos] = cand;
-          }
-        }
+        add_top(FusedPlan{G, w, tc, nq, smem, waves * per_iter});
       }
     }
   }
@@ -124,6 +188,16 @@ cudaError_t launch_backward(const FusedArgs& a, const BwdLaunchArgs& b, const Fu
 
 cudaError_t launch_fused(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st) {
   const int dim = a.pc.dim;
+  if (l.prec != 0) {
+#define SF_TC(P, D, NM) \
+  if (l.prec == P && dim == D && l.nmax == NM) return launch_fused_tc##P##_d##D##_n##NM(a, l, st);
+    SF_TC(1, 3, 8) SF_TC(1, 3, 16) SF_TC(1, 3, 24) SF_TC(1, 3, 32)
+    SF_TC(1, 2, 8) SF_TC(1, 2, 16) SF_TC(1, 2, 24) SF_TC(1, 2, 32)
+    SF_TC(2, 3, 8) SF_TC(2, 3, 16) SF_TC(2, 3, 24) SF_TC(2, 3, 32)
+    SF_TC(2, 2, 8) SF_TC(2, 2, 16) SF_TC(2, 2, 24) SF_TC(2, 2, 32)
+#undef SF_TC
+    return cudaErrorInvalidValue;
+  }
   if (dim == 3) {
     if (l.nmax == 8) return launch_fused_d3_n8(a, l, st);
     if (l.nmax == 16) return launch_fused_d3_n16(a, l, st);

@@ -26,25 +26,37 @@
 // Every reduction is done in a fixed order: results are bit-reproducible.
 #pragma once
 #include "sf_internal.cuh"
+#include "sf_tc.cuh"
 
 namespace sf {
 namespace fused_impl {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-// Shared-memory layout (floats). Head: basis [T][36], operators, beta.
+// Shared-memory layout (floats). Head, float32 form: basis [T][36],
+// operators, beta. Head, tensor-core form: the basis as 16-bit operand
+// tables BN [T][3][4][4] words (rows of P, Pd, Pdd by time step: per lane
+// quad t4 the rounded k pairs (2 t4, 2 t4 + 8), then their rounding
+// remainders) and BT [2][3][11][TH] words (P, Pd, Pdd transposed, pairs of
+// time steps, TH = ceil(T / 2); rounded, then the rounding remainders),
+// operators, beta.
 // Per sample: C, LAM [NMAX][DIM][12]; PG [NQ][NMAX][DIM][12] (partials of
 // F^T q, later r); MC, MR [DIM][12] (robot means); EB [TC][EP] (E of the
-// chunk, EP = NMAX*DIM + 1; also holds xi^{K-1} after the last iteration);
-// RS2 [T] (pair residual per t); RSB [NQ][NMAX] (ball residual partials).
+// chunk, EP = NMAX*DIM + 1, or NMAX*DIM + 4 in the tensor-core form where a
+// row first holds the scaled positions and its element NMAX*DIM flags an
+// active pair; also holds xi^{K-1} after the last iteration); RS2 [T] (pair
+// residual per t); RSB [NQ][NMAX] (ball residual partials); tensor-core form
+// only: CF [16 MT][4][4] words, the coefficient rows r = x * NMAX + i as MMA
+// A fragments (per lane quad t4: k pairs (2 t4, 2 t4 + 8) rounded to 16 bits,
+// then their rounding remainders), refreshed by every xi step.
 struct Lay {
   int RS, EP, TC, NQ, T, nmax, dim;
-  int C, LAM, XIB, PG, MC, MR, EB, RS2, RSB, FPP, FPR, XB, LB, GXB, U, CW, SB;
-  int head;
-  __host__ __device__ Lay(int dim_, int nmax_, int T_, int TC_, int NQ_, bool bwd = false) {
+  int C, LAM, XIB, PG, MC, MR, EB, RS2, RSB, FPP, FPR, XB, LB, GXB, U, CW, CF, SB;
+  int head, TH, bno, bto, opso, betao;
+  __host__ __device__ Lay(int dim_, int nmax_, int T_, int TC_, int NQ_, bool bwd = false, bool tcm = false) {
     dim = dim_; nmax = nmax_; T = T_; TC = TC_; NQ = NQ_;
     RS = dim * NP;
-    EP = nmax * dim + 1;
+    EP = nmax * dim + (tcm ? 4 : 1);
     C = 0;
     LAM = C + nmax * RS;
     XIB = LAM + nmax * RS;
@@ -63,8 +75,19 @@ struct Lay {
     GXB = LB + (bwd ? nmax * RS : 0);
     U = GXB + (bwd ? nmax * RS : 0);
     CW = U + (bwd ? nmax * RS : 0);
-    SB = CW + (bwd ? nmax * RS : 0);
-    head = T * BASIS_ROW + 4 * NV * NP + nmax * RS;
+    CF = CW + (bwd ? nmax * RS : 0);
+    SB = CF + (tcm ? ((dim * nmax + 15) / 16) * 256 : 0);
+    TH = (T + 1) / 2;
+    bno = 0;
+    if (tcm) {
+      bto = T * 48;
+      opso = bto + ((6 * NV * TH + 3) / 4) * 4;
+    } else {
+      bto = 0;
+      opso = T * BASIS_ROW;
+    }
+    betao = opso + 4 * NV * NP;
+    head = betao + nmax * RS;
   }
 };
 
@@ -202,8 +225,10 @@ __device__ __forceinline__ void pair_apply(const float (&pi)[DIM], const float (
   }
 }
 
-// Pair phase of one chunk [t0, t0 + TCc).
-template <int DIM, int NMAX>
+// Pair phase of one chunk [t0, t0 + TCc). With TCM (tensor-core form) the
+// scaled positions are already in the lane's chunk-buffer row, and the row's
+// element NMAX*DIM is set to 1 when some pair of the row is active.
+template <int DIM, int NMAX, bool TCM = false>
 __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G, int N, int t0, int TCc,
                            const ProblemConsts& pc, bool want_res, int warp, int nwarps, int lane) {
   constexpr int RS = DIM * NP;
@@ -217,7 +242,7 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
     float* blk = SAMP + (size_t)s * L.SB;
     const float* Cs = blk + L.C;
     float Pr[NV];
-    row_from(BASIS + (size_t)t * BASIS_ROW, Pr);
+    if (!TCM) row_from(BASIS + (size_t)t * BASIS_ROW, Pr);
     float E[NMAX][DIM];
 #pragma unroll
     for (int i = 0; i < NMAX; ++i)
@@ -229,17 +254,34 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
       // scaled positions of all robots in registers; lanes past the chunk get
       // far-apart dummies so that none of their rows tests active
       float p[NMAX][DIM];
+      if (TCM) {
+        // the row is 16-byte aligned (EP is a multiple of 4)
+        float pr[NMAX * DIM];
+        const float4* e4 = reinterpret_cast<const float4*>(ebw);
 #pragma unroll
-      for (int i = 0; i < NMAX; ++i) {
-        if (i < N) {
-          state<DIM>(Pr, Cs + i * RS, p[i]);
-#pragma unroll
-          for (int x = 0; x < DIM; ++x) p[i][x] *= (x == 2 ? pc.inv_b : pc.inv_a);
-        } else {
-#pragma unroll
-          for (int x = 0; x < DIM; ++x) p[i][x] = 0.0f;
+        for (int q = 0; q < NMAX * DIM / 4; ++q) {
+          const float4 v = e4[q];
+          pr[4 * q] = v.x; pr[4 * q + 1] = v.y; pr[4 * q + 2] = v.z; pr[4 * q + 3] = v.w;
         }
-        if (!valid) p[i][0] = 4096.0f * (float)i;
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i) {
+#pragma unroll
+          for (int x = 0; x < DIM; ++x) p[i][x] = (i < N) ? pr[i * DIM + x] : 0.0f;
+          if (!valid) p[i][0] = 4096.0f * (float)i;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i) {
+          if (i < N) {
+            state<DIM>(Pr, Cs + i * RS, p[i]);
+#pragma unroll
+            for (int x = 0; x < DIM; ++x) p[i][x] *= (x == 2 ? pc.inv_b : pc.inv_a);
+          } else {
+#pragma unroll
+            for (int x = 0; x < DIM; ++x) p[i][x] = 0.0f;
+          }
+          if (!valid) p[i][0] = 4096.0f * (float)i;
+        }
       }
       // a row of pairs (i, j > i) is tested without branches; only a row that
       // is active on some lane of the warp is walked pair by pair
@@ -263,14 +305,16 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
       // scaled positions staged once in the lane's own row of the chunk
       // buffer (which later receives E); robots in blocks of 8 reloaded
       // from there, each later robot tested against a block in one group
+      if (!TCM) {
 #pragma unroll
-      for (int i = 0; i < NMAX; ++i) {
-        if (i < N) {
-          float pi[DIM];
-          state<DIM>(Pr, Cs + i * RS, pi);
-          if (valid)
+        for (int i = 0; i < NMAX; ++i) {
+          if (i < N) {
+            float pi[DIM];
+            state<DIM>(Pr, Cs + i * RS, pi);
+            if (valid)
 #pragma unroll
-            for (int x = 0; x < DIM; ++x) ebw[i * DIM + x] = pi[x] * (x == 2 ? pc.inv_b : pc.inv_a);
+              for (int x = 0; x < DIM; ++x) ebw[i * DIM + x] = pi[x] * (x == 2 ? pc.inv_b : pc.inv_a);
+          }
         }
       }
 #pragma unroll
@@ -321,11 +365,26 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
     }
     if (valid) {
       float* eb = blk + L.EB + tl * L.EP;
+      if (TCM) {
+        // whole row in 16-byte stores (E of robots >= N is zero); the row
+        // stride is a multiple of 4 floats, scalar stores would conflict
+        float Ef[NMAX * DIM];
 #pragma unroll
-      for (int i = 0; i < NMAX; ++i)
-        if (i < N)
+        for (int i = 0; i < NMAX; ++i)
 #pragma unroll
-          for (int x = 0; x < DIM; ++x) eb[i * DIM + x] = E[i][x];
+          for (int x = 0; x < DIM; ++x) Ef[i * DIM + x] = E[i][x];
+        float4* e4 = reinterpret_cast<float4*>(eb);
+#pragma unroll
+        for (int q = 0; q < NMAX * DIM / 4; ++q)
+          e4[q] = make_float4(Ef[4 * q], Ef[4 * q + 1], Ef[4 * q + 2], Ef[4 * q + 3]);
+        eb[NMAX * DIM] = res2 > 0.0f ? 1.0f : 0.0f;
+      } else {
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i)
+          if (i < N)
+#pragma unroll
+            for (int x = 0; x < DIM; ++x) eb[i * DIM + x] = E[i][x];
+      }
       if (want_res) blk[L.RS2 + t] = res2;
     }
   }
@@ -423,6 +482,307 @@ __device__ void contract_phase(float* SAMP, const Lay& L, const float* BASIS, in
       if (want_res) {
         float* r = blk + L.RSB + tq * L.nmax + i;
         *r = first_chunk ? rb : *r + rb;
+      }
+    }
+  }
+}
+
+// ---- tensor-core form ------------------------------------------------------
+//
+// The per-sample contractions run on warp-level MMAs with 16-bit operands and
+// float32 accumulation. Rows of the coefficient operand are r = x * NMAX + i
+// (axis-major), so that (NMAX being a multiple of 8) the lane with group g
+// holds, in the accumulators, every axis of robots i = g (mod 8): the ball
+// projections need no data exchange.
+
+// Writes coefficient row r (11 values c, k >= 11 zero) into CF: per lane
+// quad t4 the words {hi(2 t4), hi(2 t4 + 8), lo(2 t4), lo(2 t4 + 8)}, each
+// packing k and k + 1 (hi = rounded to 16 bits, lo = rounding remainder).
+template <int PREC>
+__device__ __forceinline__ void cf_write_row(float* CF, int r, const float* c) {
+  uint4* row = reinterpret_cast<uint4*>(CF + r * 16);
+#pragma unroll
+  for (int t4 = 0; t4 < 4; ++t4) {
+    const int k0 = 2 * t4, k1 = 2 * t4 + 8;
+    const float a0 = c[k0], a1 = c[k0 + 1];
+    const float b0 = k1 < NV ? c[k1] : 0.0f, b1 = k1 + 1 < NV ? c[k1 + 1] : 0.0f;
+    uint4 w;
+    w.x = tc::pack2<PREC>(a0, a1);
+    w.y = tc::pack2<PREC>(b0, b1);
+    w.z = tc::pack2<PREC>(a0 - tc::round16<PREC>(a0), a1 - tc::round16<PREC>(a1));
+    w.w = tc::pack2<PREC>(b0 - tc::round16<PREC>(b0), b1 - tc::round16<PREC>(b1));
+    row[t4] = w;
+  }
+}
+
+// A fragments (rounded and remainder) of coefficient rows 16 mt .. 16 mt + 15.
+__device__ __forceinline__ void cf_frag(const float* CF, int mt, int g, int t4, uint32_t (&hi)[4],
+                                        uint32_t (&lo)[4]) {
+  const uint4 r0 = *reinterpret_cast<const uint4*>(CF + (16 * mt + g) * 16 + 4 * t4);
+  const uint4 r1 = *reinterpret_cast<const uint4*>(CF + (16 * mt + g + 8) * 16 + 4 * t4);
+  hi[0] = r0.x; hi[1] = r1.x; hi[2] = r0.y; hi[3] = r1.y;
+  lo[0] = r0.z; lo[1] = r1.z; lo[2] = r0.w; lo[3] = r1.w;
+}
+
+// CF of every sample from C (rows of robots >= N and padding rows zero).
+template <int DIM, int NMAX, int PREC>
+__device__ void cf_prepare(float* SAMP, const Lay& L, int G, int N, int tid, int nthr) {
+  constexpr int RS = DIM * NP;
+  constexpr int ROWS = ((DIM * NMAX + 15) / 16) * 16;
+  for (int v = tid; v < G * ROWS; v += nthr) {
+    const int s = v / ROWS, r = v % ROWS;
+    float* blk = SAMP + (size_t)s * L.SB;
+    float c[NV];
+    const int x = r / NMAX, i = r % NMAX;
+    const bool live = r < DIM * NMAX && i < N;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) c[k] = live ? blk[L.C + i * RS + x * NP + k] : 0.0f;
+    cf_write_row<PREC>(blk + L.CF, r, c);
+  }
+}
+
+// acc[0..1] += A (16 x 8: rows r, time steps (2 t4, 2 t4 + 1) in the low /
+// high half of a0 (row g) and a1 (row g + 8)) times the 8 x 16 basis block
+// of words b[nn] (columns k = 8 nn + g). SPLIT adds the products of the
+// operands' rounding remainders (three-term form), for bf16 operands.
+template <int PREC, bool SPLIT>
+__device__ __forceinline__ void resid_mma(float (&acc)[2][4], float v00, float v01, float v10, float v11,
+                                          const uint32_t (&bh)[2], const uint32_t (&bl)[2]) {
+  const uint32_t a0 = tc::pack2<PREC>(v00, v01), a1 = tc::pack2<PREC>(v10, v11);
+  if (SPLIT) {
+    const uint32_t l0 = tc::pack2<PREC>(v00 - tc::round16<PREC>(v00), v01 - tc::round16<PREC>(v01));
+    const uint32_t l1 = tc::pack2<PREC>(v10 - tc::round16<PREC>(v10), v11 - tc::round16<PREC>(v11));
+#pragma unroll
+    for (int nn = 0; nn < 2; ++nn) {
+      tc::mma8<PREC>(acc[nn], l0, l1, bh[nn]);
+      tc::mma8<PREC>(acc[nn], a0, a1, bl[nn]);
+    }
+  }
+#pragma unroll
+  for (int nn = 0; nn < 2; ++nn) tc::mma8<PREC>(acc[nn], a0, a1, bh[nn]);
+}
+
+// Positions of one chunk: p = P c for every (sample, robot, axis, t), scaled
+// by M_a^-1 and written to the chunk-buffer rows (the pair phase's input).
+// Three products (rounded c with rounded P, c's remainder with rounded P,
+// rounded c with P's remainder) recover about 16 bits of the operands.
+// Unit = (sample, block of 16 time steps); one warp per unit.
+template <int DIM, int NMAX, int PREC>
+__device__ void tc_positions_phase(float* SAMP, const Lay& L, const uint32_t* BN, int G, int N, int t0, int TCc,
+                                   const ProblemConsts& pc, int warp, int nwarps, int lane) {
+  constexpr int MT = (DIM * NMAX + 15) / 16;
+  const int g = lane >> 2, t4 = lane & 3;
+  const int nkb = (TCc + 15) >> 4;
+  for (int u = warp; u < G * nkb; u += nwarps) {
+    const int s = u / nkb, kb = u - s * nkb;
+    float* blk = SAMP + (size_t)s * L.SB;
+    uint32_t ah[MT][4], al[MT][4];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) cf_frag(blk + L.CF, mt, g, t4, ah[mt], al[mt]);
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+      const int tl = 16 * kb + 8 * nt + g;   // this lane's time step in the B operand
+      uint4 bw = make_uint4(0u, 0u, 0u, 0u);
+      if (tl < TCc) bw = *reinterpret_cast<const uint4*>(BN + (size_t)(t0 + tl) * 48 + 4 * t4);
+      const uint2 bh = make_uint2(bw.x, bw.y), bl = make_uint2(bw.z, bw.w);
+      const int to = 16 * kb + 8 * nt + 2 * t4;   // time step of d0 (d1: to + 1)
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) {
+        float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        tc::mma16<PREC>(d, al[mt], bh.x, bh.y);
+        tc::mma16<PREC>(d, ah[mt], bl.x, bl.y);
+        tc::mma16<PREC>(d, ah[mt], bh.x, bh.y);
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const int rb = 16 * mt + 8 * h2;
+          if (rb < DIM * NMAX) {
+            const int x = rb / NMAX, i = rb % NMAX + g;
+            const float sc = x == 2 ? pc.inv_b : pc.inv_a;
+            if (i < N) {
+              float* e = blk + L.EB + i * DIM + x;
+              if (to < TCc) e[to * L.EP] = d[2 * h2] * sc;
+              if (to + 1 < TCc) e[(to + 1) * L.EP] = d[2 * h2 + 1] * sc;
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+// Contraction phase of one chunk in the tensor-core form. Per unit (sample,
+// range q of 16-step blocks) and 8 time steps:
+//   V^T = C^T Pd^T, A^T = C^T Pdd^T            (m16n8k16, rows (axis, robot))
+//   ball test on the accumulators; if some lane of the warp is outside a
+//   ball, q = e - v in place and g += q Pd (m16n8k8 with the accumulator
+//   reused as the A operand: residual form, only small values in 16 bits)
+//   g += E P when a pair of the time steps is active (E from the chunk buffer)
+// g goes to the partial PG[q] like the float32 form.
+template <int DIM, int NMAX, int PREC>
+__device__ void tc_contract_phase(float* SAMP, const Lay& L, const uint32_t* BN, const uint32_t* BT, int G, int N,
+                                  int t0, int TCc, bool first_chunk, const ProblemConsts& pc, bool want_res,
+                                  int warp, int nwarps, int lane) {
+  constexpr int RS = DIM * NP;
+  constexpr int MT = (DIM * NMAX + 15) / 16;
+  constexpr int NJ = NMAX / 8;
+  constexpr bool SPLIT4 = PREC == 1;   // bf16: three-term residual products too
+  const int g = lane >> 2, t4 = lane & 3;
+  const int nkb = (TCc + 15) >> 4;
+  const int NQ = L.NQ;
+  const int kbq = (nkb + NQ - 1) / NQ;
+  const int TH = L.TH;
+  for (int u = warp; u < G * NQ; u += nwarps) {
+    const int s = u / NQ, q = u - s * NQ;
+    const int kb0 = q * kbq, kb1 = min(nkb, kb0 + kbq);
+    float* blk = SAMP + (size_t)s * L.SB;
+    uint32_t ah[MT][4], al[MT][4];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) cf_frag(blk + L.CF, mt, g, t4, ah[mt], al[mt]);
+    float acc[MT][2][4];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+      for (int nn = 0; nn < 2; ++nn)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[mt][nn][r] = 0.0f;
+    float rb[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) rb[j] = 0.0f;
+    for (int kb = kb0; kb < kb1; ++kb) {
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const int tl = 16 * kb + 8 * nt + g;
+        const int to = 16 * kb + 8 * nt + 2 * t4;
+        // BT word of time steps t0 + to, + 1 (clamped: past the chunk the
+        // other operand is zero)
+        const int tw = min((t0 + to) >> 1, L.TH - 1);
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {    // velocity, acceleration
+          if (b == 0 ? !pc.use_v : !pc.use_a) continue;
+          uint4 bw = make_uint4(0u, 0u, 0u, 0u);
+          if (tl < TCc) bw = *reinterpret_cast<const uint4*>(BN + ((size_t)(t0 + tl) * 3 + 1 + b) * 16 + 4 * t4);
+          float D[MT][4];
+#pragma unroll
+          for (int mt = 0; mt < MT; ++mt) {
+            D[mt][0] = D[mt][1] = D[mt][2] = D[mt][3] = 0.0f;
+            tc::mma16<PREC>(D[mt], al[mt], bw.x, bw.y);
+            tc::mma16<PREC>(D[mt], ah[mt], bw.z, bw.w);
+            tc::mma16<PREC>(D[mt], ah[mt], bw.x, bw.y);
+          }
+          const float rmax = b == 0 ? pc.v_max : pc.a_max;
+          const float r2 = rmax * rmax;
+          bool out = false;
+#pragma unroll
+          for (int j = 0; j < NJ; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              float n2 = 0.0f;
+#pragma unroll
+              for (int x = 0; x < DIM; ++x) {
+                const int base = x * NMAX + 8 * j;
+                const float v = D[base / 16][2 * ((base / 8) & 1) + h];
+                n2 = fmaf(v, v, n2);
+              }
+              out |= n2 > r2;
+            }
+          if (__any_sync(FULL, out)) {
+#pragma unroll
+            for (int j = 0; j < NJ; ++j)
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                float v[DIM], qb[DIM], rl = 0.0f;
+#pragma unroll
+                for (int x = 0; x < DIM; ++x) {
+                  const int base = x * NMAX + 8 * j;
+                  v[x] = D[base / 16][2 * ((base / 8) & 1) + h];
+                }
+                ball_residual<DIM>(v, rmax, qb, rl);
+#pragma unroll
+                for (int x = 0; x < DIM; ++x) {
+                  const int base = x * NMAX + 8 * j;
+                  D[base / 16][2 * ((base / 8) & 1) + h] = qb[x];
+                }
+                rb[j] += rl;
+              }
+            uint32_t bh[2], bl[2];
+#pragma unroll
+            for (int nn = 0; nn < 2; ++nn) {
+              const int k = 8 * nn + g;
+              bh[nn] = k < NV ? BT[((1 + b) * NV + k) * TH + tw] : 0u;
+              bl[nn] = (SPLIT4 && k < NV) ? BT[((4 + b) * NV + k) * TH + tw] : 0u;
+            }
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt)
+              resid_mma<PREC, SPLIT4>(acc[mt], D[mt][0], D[mt][1], D[mt][2], D[mt][3], bh, bl);
+          }
+        }
+        // pair residuals E of time steps to, to + 1
+        const float* eb = blk + L.EB;
+        bool ea = false;
+        if (to < TCc) ea |= eb[to * L.EP + NMAX * DIM] != 0.0f;
+        if (to + 1 < TCc) ea |= eb[(to + 1) * L.EP + NMAX * DIM] != 0.0f;
+        if (__any_sync(FULL, ea)) {
+          uint32_t bh[2], bl[2];
+#pragma unroll
+          for (int nn = 0; nn < 2; ++nn) {
+            const int k = 8 * nn + g;
+            bh[nn] = k < NV ? BT[k * TH + tw] : 0u;
+            bl[nn] = (SPLIT4 && k < NV) ? BT[(3 * NV + k) * TH + tw] : 0u;
+          }
+#pragma unroll
+          for (int mt = 0; mt < MT; ++mt) {
+            float e[2][2];
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+              const int rbase = 16 * mt + 8 * h2;
+              e[h2][0] = e[h2][1] = 0.0f;
+              if (rbase < DIM * NMAX) {
+                const int x = rbase / NMAX, i = rbase % NMAX + g;
+                if (i < N) {
+                  if (to < TCc) e[h2][0] = eb[to * L.EP + i * DIM + x];
+                  if (to + 1 < TCc) e[h2][1] = eb[(to + 1) * L.EP + i * DIM + x];
+                }
+              }
+            }
+            resid_mma<PREC, SPLIT4>(acc[mt], e[0][0], e[0][1], e[1][0], e[1][1], bh, bl);
+          }
+        }
+      }
+    }
+    // partial of F^T q of this range: acc rows (axis, robot), columns k
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+      for (int h2 = 0; h2 < 2; ++h2) {
+        const int rbase = 16 * mt + 8 * h2;
+        if (rbase < DIM * NMAX) {
+          const int x = rbase / NMAX, i = rbase % NMAX + g;
+          if (i < N) {
+            float* pg = blk + L.PG + q * NMAX * RS + i * RS + x * NP;
+#pragma unroll
+            for (int nn = 0; nn < 2; ++nn)
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const int k = 8 * nn + 2 * t4 + h;
+                if (k < NV) {
+                  const float v = acc[mt][nn][2 * h2 + h];
+                  pg[k] = first_chunk ? v : pg[k] + v;
+                }
+              }
+          }
+        }
+      }
+    if (want_res) {
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        float r = rb[j];
+        r += __shfl_xor_sync(FULL, r, 1);
+        r += __shfl_xor_sync(FULL, r, 2);
+        const int i = g + 8 * j;
+        if (t4 == 0 && i < N) {
+          float* p = blk + L.RSB + q * NMAX + i;
+          *p = first_chunk ? r : *p + r;
+        }
       }
     }
   }
@@ -530,9 +890,10 @@ struct Cta {
   int N, G, robot_off, gsample0;
   long long per_sample, coef0;
   float *BASIS, *OPS, *BETA, *SAMP;
+  uint32_t *BN, *BT;
   int tid, nthr, warp, lane, nwarps;
-  __device__ Cta(const SceneDesc* sc, int n_scenes, int T, int tc, int nq, bool bwd, float* sm)
-      : L(DIM, NMAX, T, tc, nq, bwd) {
+  __device__ Cta(const SceneDesc* sc, int n_scenes, int T, int tc, int nq, bool bwd, float* sm, bool tcm = false)
+      : L(DIM, NMAX, T, tc, nq, bwd, tcm) {
     int sidx = 0;
     for (int q = 1; q < n_scenes; ++q) {
       if (sc[q].cta_begin <= (int)blockIdx.x) sidx = q;
@@ -546,9 +907,11 @@ struct Cta {
     gsample0 = sc[sidx].sample_off + s_first;
     per_sample = (long long)DIM * N * NV;
     coef0 = sc[sidx].coef_off + (long long)s_first * per_sample;
-    BASIS = sm;
-    OPS = sm + T * BASIS_ROW;
-    BETA = OPS + 4 * NV * NP;
+    BASIS = tcm ? nullptr : sm;
+    BN = tcm ? reinterpret_cast<uint32_t*>(sm + L.bno) : nullptr;
+    BT = tcm ? reinterpret_cast<uint32_t*>(sm + L.bto) : nullptr;
+    OPS = sm + L.opso;
+    BETA = sm + L.betao;
     SAMP = sm + L.head;
     tid = threadIdx.x;
     nthr = blockDim.x;
@@ -563,14 +926,51 @@ struct Cta {
   __device__ float* blk(int s) const { return SAMP + (size_t)s * L.SB; }
 };
 
+// 16-bit operand tables of the tensor-core form from the float32 basis
+// [T][36] (P, Pd, Pdd rows of 12): BN word (t, m, t4, e) packs k0 = 2 t4 +
+// 8 (e & 1) and k0 + 1 of matrix m, rounded (e < 2) or the rounding
+// remainder (e >= 2); BT word (l, m, k, t / 2) packs time steps t and t + 1
+// of column k, rounded (l = 0) or the rounding remainder (l = 1). Entries
+// past T or past k = 10 are zero.
+template <int PREC>
+__device__ void tc_tables(const Lay& L, int T, const float* gb, uint32_t* BN, uint32_t* BT, int tid, int nthr) {
+  for (int v = tid; v < T * 48; v += nthr) {
+    const int t = v / 48, m = (v >> 4) % 3, t4 = (v >> 2) & 3, e = v & 3;
+    const int k0 = 2 * t4 + 8 * (e & 1);
+    const float* row = gb + (size_t)t * BASIS_ROW + m * NP;
+    float x0 = k0 < NV ? row[k0] : 0.0f;
+    float x1 = k0 + 1 < NV ? row[k0 + 1] : 0.0f;
+    if (e >= 2) {
+      x0 -= tc::round16<PREC>(x0);
+      x1 -= tc::round16<PREC>(x1);
+    }
+    BN[v] = tc::pack2<PREC>(x0, x1);
+  }
+  const int TH = L.TH;
+  for (int v = tid; v < 6 * NV * TH; v += nthr) {
+    const int l = v / (3 * NV * TH), m = (v / (NV * TH)) % 3, k = (v / TH) % NV, t = 2 * (v % TH);
+    float x0 = t < T ? gb[(size_t)t * BASIS_ROW + m * NP + k] : 0.0f;
+    float x1 = t + 1 < T ? gb[(size_t)(t + 1) * BASIS_ROW + m * NP + k] : 0.0f;
+    if (l == 1) {
+      x0 -= tc::round16<PREC>(x0);
+      x1 -= tc::round16<PREC>(x1);
+    }
+    BT[v] = tc::pack2<PREC>(x0, x1);
+  }
+}
+
 // Basis table, operators of this N and beta_i = R1 b_i + (R0 - R1) bbar.
-template <int DIM, int NMAX>
+template <int DIM, int NMAX, int PREC = 0>
 __device__ void prologue(const Cta<DIM, NMAX>& c, int T, const float4* basis, const float* ops,
                          const float* start, const float* goal, const float* start_va, const float* goal_va) {
   constexpr int RS = DIM * NP;
-  const float4* b4 = basis;
-  float4* s4 = reinterpret_cast<float4*>(c.BASIS);
-  for (int v = c.tid; v < T * 9; v += c.nthr) s4[v] = b4[v];
+  if constexpr (PREC == 0) {
+    const float4* b4 = basis;
+    float4* s4 = reinterpret_cast<float4*>(c.BASIS);
+    for (int v = c.tid; v < T * 9; v += c.nthr) s4[v] = b4[v];
+  } else {
+    tc_tables<PREC>(c.L, T, reinterpret_cast<const float*>(basis), c.BN, c.BT, c.tid, c.nthr);
+  }
   const float* gops = ops + (size_t)c.N * OPS_STRIDE;
   for (int v = c.tid; v < 4 * NV * NP; v += c.nthr) c.OPS[v] = gops[v];
   const int N = c.N;
@@ -647,7 +1047,7 @@ __device__ void store_state(const Cta<DIM, NMAX>& c, float* xi_dst, float* lam_d
 // One iteration of f_FP on every sample of the CTA (time chunks, then the
 // lambda step and the xi step). keep_prev stores xi^k in the EB region for
 // the final residual. fp (when set) adds ||z^{k+1} - z^k||^2 per sample to FPR.
-template <int DIM, int NMAX>
+template <int DIM, int NMAX, int PREC = 0>
 __device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, const float* xi_bar, int it,
                               bool keep_prev, float* hist, int total_samples, bool fp) {
   constexpr int RS = DIM * NP;
@@ -658,9 +1058,18 @@ __device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, 
   const float invN = 1.0f / (float)N;
   for (int t0 = 0; t0 < T; t0 += TC) {
     const int TCc = min(TC, T - t0);
-    pair_phase<DIM, NMAX>(c.SAMP, L, c.BASIS, G, N, t0, TCc, pc, want_res, c.warp, c.nwarps, c.lane);
-    __syncthreads();
-    contract_phase<DIM>(c.SAMP, L, c.BASIS, G, N, t0, TCc, t0 == 0, pc, want_res, c.tid, c.nthr);
+    if constexpr (PREC != 0) {
+      tc_positions_phase<DIM, NMAX, PREC>(c.SAMP, L, c.BN, G, N, t0, TCc, pc, c.warp, c.nwarps, c.lane);
+      __syncthreads();
+      pair_phase<DIM, NMAX, true>(c.SAMP, L, nullptr, G, N, t0, TCc, pc, want_res, c.warp, c.nwarps, c.lane);
+      __syncthreads();
+      tc_contract_phase<DIM, NMAX, PREC>(c.SAMP, L, c.BN, c.BT, G, N, t0, TCc, t0 == 0, pc, want_res, c.warp,
+                                         c.nwarps, c.lane);
+    } else {
+      pair_phase<DIM, NMAX>(c.SAMP, L, c.BASIS, G, N, t0, TCc, pc, want_res, c.warp, c.nwarps, c.lane);
+      __syncthreads();
+      contract_phase<DIM>(c.SAMP, L, c.BASIS, G, N, t0, TCc, t0 == 0, pc, want_res, c.tid, c.nthr);
+    }
     __syncthreads();
   }
   // ---- solve phase 1: lambda step, r, robot means (and the history entry)
@@ -731,6 +1140,7 @@ __device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, 
       dx2 = fmaf(acc - cc[k], acc - cc[k], dx2);
     }
     out[NV] = 0.0f;
+    if constexpr (PREC != 0) cf_write_row<PREC>(blk + L.CF, x * NMAX + i, out);
     float4* o4 = reinterpret_cast<float4*>(blk + L.C + o);
     float4* p4 = reinterpret_cast<float4*>(blk + L.EB + o);
 #pragma unroll
@@ -761,22 +1171,27 @@ __device__ void write_checkpoint(const Cta<DIM, NMAX>& c, float* ckpt, int ck, l
   store_state<DIM, NMAX>(c, base, base + total_coefs, 0);
 }
 
-template <int DIM, int NMAX, int MAXT>
+// PREC 0: float32 form; 1 / 2: tensor-core form with bf16 / fp16 operands.
+template <int DIM, int NMAX, int MAXT, int PREC>
 __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constant__ FusedArgs A) {
   extern __shared__ float4 smem4[];
   float* sm = reinterpret_cast<float*>(smem4);
   const ProblemConsts& pc = A.pc;
   const int T = pc.T;
-  const Cta<DIM, NMAX> c(A.sc, A.n_scenes, T, A.tc, A.nq, false, sm);
+  const Cta<DIM, NMAX> c(A.sc, A.n_scenes, T, A.tc, A.nq, false, sm, PREC != 0);
   if (c.G <= 0) return;
   const Lay& L = c.L;
   const int N = c.N, G = c.G;
   const bool fp = A.fp_res2 != nullptr;
 
-  prologue<DIM, NMAX>(c, T, A.basis, A.ops, A.start, A.goal, A.start_va, A.goal_va);
+  prologue<DIM, NMAX, PREC>(c, T, A.basis, A.ops, A.start, A.goal, A.start_va, A.goal_va);
   load_state<DIM, NMAX>(c, A.xi0, A.lam0, A.xi_bar, A.xi_bar);
   for (int s = c.tid; s < G; s += c.nthr) c.blk(s)[L.FPR] = 0.0f;
   __syncthreads();
+  if constexpr (PREC != 0) {
+    cf_prepare<DIM, NMAX, PREC>(c.SAMP, L, G, N, c.tid, c.nthr);
+    __syncthreads();
+  }
 
   // checkpoints: (xi, lambda) at iterations 0, ck, 2 ck, ...; after them a
   // tail holding every iterate of the last segment (last_ck .. K), so that
@@ -787,7 +1202,7 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
   for (int it = 0; it < pc.K; ++it) {
     if (A.ckpt && it % A.ck_every == 0) write_checkpoint<DIM, NMAX>(c, A.ckpt, it / A.ck_every, A.total_coefs);
     if (tail && it >= last_ck) write_checkpoint<DIM, NMAX>(c, tail, it - last_ck, A.total_coefs);
-    fwd_iteration<DIM, NMAX>(c, pc, A.xi_bar, it, it == pc.K - 1, A.hist, A.total_samples, fp);
+    fwd_iteration<DIM, NMAX, PREC>(c, pc, A.xi_bar, it, it == pc.K - 1, A.hist, A.total_samples, fp);
   }
   if (tail) write_checkpoint<DIM, NMAX>(c, tail, pc.K - last_ck, A.total_coefs);
 
@@ -799,7 +1214,8 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
     if (rem / RS >= N) c.blk(s)[L.EB + rem] = 0.0f;
   }
   __syncthreads();
-  residual_phase<DIM, NMAX>(c.SAMP, L, c.BASIS, G, N, T, pc, c.warp, c.nwarps, c.lane);
+  const float* rbasis = PREC == 0 ? c.BASIS : reinterpret_cast<const float*>(A.basis);
+  residual_phase<DIM, NMAX>(c.SAMP, L, rbasis, G, N, T, pc, c.warp, c.nwarps, c.lane);
   __syncthreads();
   for (int s = c.tid; s < G; s += c.nthr) {
     const float* blk = c.blk(s);
@@ -813,9 +1229,9 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
   store_state<DIM, NMAX>(c, A.xi_out, A.lam_out, 0);
 }
 
-template <int DIM, int NMAX, int MAXT>
+template <int DIM, int NMAX, int MAXT, int PREC = 0>
 cudaError_t launch_t(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st) {
-  auto k = fused_fwd_kernel<DIM, NMAX, MAXT>;
+  auto k = fused_fwd_kernel<DIM, NMAX, MAXT, PREC>;
   if (l.warps * 32 > MAXT) return cudaErrorInvalidConfiguration;
   k<<<l.n_ctas, l.warps * 32, l.smem, st>>>(a);
   return cudaGetLastError();

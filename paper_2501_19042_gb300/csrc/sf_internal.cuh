@@ -144,11 +144,12 @@ struct FusedLaunch {
   int n_ctas;
   int tc, nq;   // time chunk, contraction ranges
   size_t smem;  // dynamic shared memory bytes
+  int prec;     // 0 float32 form, 1 / 2 tensor-core form with bf16 / fp16 operands
 };
-size_t fused_smem_bytes(int dim, int nmax, int T, int gmax, int tc, int nq, bool bwd = false);
+size_t fused_smem_bytes(int dim, int nmax, int T, int gmax, int tc, int nq, bool bwd = false, int prec = 0);
 cudaError_t launch_fused(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st);
 int fused_max_warps(int nmax, bool bwd);
-cudaError_t prepare_kernels(int dim, int smem);
+cudaError_t prepare_kernels(int dim, int smem, int prec);
 
 // Launch shape of the fused kernel for one group of scenes: samples per CTA,
 // warps, time chunk, contraction ranges (cost model over the candidates,
@@ -160,7 +161,7 @@ struct FusedPlan {
 };
 FusedPlan plan_fused(int dim, int nmax, int T, const int* n_robots, const int* n_samples, int n_scenes,
                      int num_sms, size_t smem_cap, int force_G, int force_warps, int force_tc,
-                     bool bwd = false, FusedPlan* top = nullptr, int n_top = 0);
+                     bool bwd = false, FusedPlan* top = nullptr, int n_top = 0, int prec = 0);
 
 // Backward launch: everything the adjoint kernel needs besides the scene
 // table (which it shares with FusedArgs).

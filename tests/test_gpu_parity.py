@@ -92,6 +92,20 @@ def test_n32_t120(sfmod, oracle_lib):
     _check(out, ref)
 
 
+def test_n32_t120_full_size_sampled(sfmod, oracle_lib):
+    """The precision workload at full size in float32 (N=32, S=2048, T=120,
+    K=200, one launch); 12 sampled outputs against the oracle one by one."""
+    sc = si.scene(si.config_n32_3d(), 3)
+    out = _gpu_run(sfmod, sc, RHO_3D, 200)
+    idx = np.array([0, 1, 2, 3, 250, 511, 777, 1024, 1500, 1901, 2046, 2047])
+    ref = run_oracle(oracle_lib, sc, RHO_3D, 200, idx=idx)
+    err = rel_l2(out.xi.double().cpu().numpy()[idx], ref["xi"])
+    dres = np.abs(out.residual.double().cpu().numpy()[idx] - ref["rp_final"])
+    assert err.max() <= TOL_XI_REL, err
+    assert dres.max() <= TOL_RESID_ABS, dres
+    assert torch.isfinite(out.xi).all() and torch.isfinite(out.residual).all()
+
+
 @pytest.mark.parametrize("N,T", [(1, 50), (2, 33), (5, 64), (9, 31), (17, 97)])
 def test_edge_sizes(sfmod, oracle_lib, N, T):
     """Single robot (no pairs), two robots, robot counts off the block size,
