@@ -57,7 +57,6 @@ sf_status cuda_fail(sf_handle* h, cudaError_t e, const char* where) {
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
-int nmax_bucket(int N) { return N <= 8 ? 8 : (N <= 16 ? 16 : (N <= 24 ? 24 : 32)); }
 int bucket_index(int N) { return N <= 8 ? 0 : (N <= 16 ? 1 : (N <= 24 ? 2 : 3)); }
 constexpr int kBuckets = 4;
 constexpr int kBucketNmax[kBuckets] = {8, 16, 24, 32};
@@ -125,6 +124,19 @@ long long total_coefs(const sf_handle* h, const sf_batch* b) {
   return c;
 }
 
+// Words of one activity-mask slot (one iteration of every sample): per
+// sample and time step a row of mask_words(bucket N_max) words.
+long long mask_slot_words(const sf_handle* h, const sf_batch* b) {
+  long long w = 0;
+  for (int q = 0; q < b->n_scenes; ++q)
+    w += (long long)b->n_samples[q] * h->pb.T * mask_words(kBucketNmax[bucket_index(b->n_robots[q])]);
+  return w;
+}
+
+// Floats of a buffer of `n_states` (xi, lambda) states, rounded up to 16 bytes
+// (the activity masks follow it).
+long long states_floats_aligned(long long n_states, long long coefs) { return (n_states * 2 * coefs + 3) / 4 * 4; }
+
 struct LaunchGroup {
   FusedArgs a;
   FusedLaunch l;
@@ -145,17 +157,18 @@ sf_status build_groups(sf_handle* h, const sf_batch* b, int K, long long S, cons
   const int dim = h->pb.dim, T = h->pb.T;
   const ProblemConsts pc = consts(h->pb, K);
   const long long tot = total_coefs(h, b);
-  struct Item { int scene; long long roff, soff, coff; };
+  struct Item { int scene; long long roff, soff, coff, moff; };
   std::vector<Item> items[kBuckets];
   {
-    long long roff = 0, soff = 0, coff = 0;
+    long long roff = 0, soff = 0, coff = 0, moff = 0;
     for (int sc = 0; sc < b->n_scenes; ++sc) {
       const int N = b->n_robots[sc], Ss = b->n_samples[sc];
       const int bk = bucket_index(N);
-      if (Ss > 0) items[bk].push_back({sc, roff, soff, coff});
+      if (Ss > 0) items[bk].push_back({sc, roff, soff, coff, moff});
       roff += N;
       soff += Ss;
       coff += (long long)Ss * dim * N * NV;
+      moff += (long long)Ss * T * mask_words(kBucketNmax[bk]);
     }
   }
   for (int bk = 0; bk < kBuckets; ++bk) {
@@ -203,6 +216,11 @@ sf_status build_groups(sf_handle* h, const sf_batch* b, int K, long long S, cons
       a.ck_every = std::max(1, h->pb.checkpoint_every);
       a.total_coefs = tot;
       a.fp_res2 = rq.fp_res2;
+      if (rq.ckpt && !rq.backward) {
+        const long long ck = a.ck_every, nck = (K + ck - 1) / ck;
+        a.amask = reinterpret_cast<unsigned*>(rq.ckpt + states_floats_aligned(nck + ck + 1, tot));
+        a.amask_slot = mask_slot_words(h, b);
+      }
       int ctas = 0, gmax = 1;
       a.n_scenes = (int)(last - first);
       for (size_t q = first; q < last; ++q) {
@@ -215,6 +233,7 @@ sf_status build_groups(sf_handle* h, const sf_batch* b, int K, long long S, cons
         d.robot_off = (int)it.roff;
         d.sample_off = (int)it.soff;
         d.coef_off = it.coff;
+        d.mask_off = it.moff;
         ctas += (d.S + d.G - 1) / d.G;
         gmax = std::max(gmax, d.G);
       }
@@ -383,11 +402,11 @@ size_t sf_checkpoint_bytes(const sf_handle* hc, const sf_batch* b, int K) {
   if (!h || h->pb.checkpoint_every <= 0 || K < 1) return 0;
   long long R = 0, S = 0;
   if (check_batch(h, b, &R, &S) != SF_OK) return 0;
-  const long long nck = (K + h->pb.checkpoint_every - 1) / h->pb.checkpoint_every;
-  long long coefs = 0;
-  for (int s = 0; s < b->n_scenes; ++s) coefs += (long long)b->n_samples[s] * h->pb.dim * b->n_robots[s] * NV;
-  // checkpoints, then the iterates of the last segment (up to checkpoint_every + 1)
-  return (size_t)((nck + h->pb.checkpoint_every + 1) * 2 * coefs) * sizeof(float);
+  const long long ck = h->pb.checkpoint_every;
+  const long long nck = (K + ck - 1) / ck;
+  // checkpoints, the iterates of the last segment (up to checkpoint_every + 1),
+  // then the activity masks of the last segment's iterations
+  return (size_t)(states_floats_aligned(nck + ck + 1, total_coefs(h, b)) + ck * mask_slot_words(h, b)) * 4;
 }
 
 sf_status sf_project(sf_handle* h, void* stream, const sf_batch* b, int K, int form, const float* xi0,
@@ -498,7 +517,9 @@ size_t sf_backward_workspace_bytes(const sf_handle* hc, const sf_batch* b, int K
   if (!h || h->pb.checkpoint_every <= 0 || K < 1) return 0;
   long long R = 0, S = 0;
   if (check_batch(h, b, &R, &S) != SF_OK) return 0;
-  return (size_t)(h->pb.checkpoint_every + 1) * 2 * (size_t)total_coefs(h, b) * sizeof(float);
+  // ring of states, then the activity masks of the recomputed segment
+  const long long ck = h->pb.checkpoint_every;
+  return (size_t)(states_floats_aligned(ck + 1, total_coefs(h, b)) + ck * mask_slot_words(h, b)) * 4;
 }
 
 sf_status sf_project_backward(sf_handle* h, void* stream, const sf_batch* b, int K, int init_from_xi_bar,
@@ -523,6 +544,12 @@ sf_status sf_project_backward(sf_handle* h, void* stream, const sf_batch* b, int
   rq.bwd.ck_every = h->pb.checkpoint_every;
   rq.bwd.total_coefs = total_coefs(h, b);
   rq.bwd.ring = reinterpret_cast<float*>(workspace);
+  {
+    const long long ck = h->pb.checkpoint_every, nck = (K + ck - 1) / ck, tot = rq.bwd.total_coefs;
+    rq.bwd.tail_mask = reinterpret_cast<const unsigned*>(rq.bwd.ckpt + states_floats_aligned(nck + ck + 1, tot));
+    rq.bwd.ring_mask = reinterpret_cast<unsigned*>(rq.bwd.ring + states_floats_aligned(ck + 1, tot));
+    rq.bwd.mask_slot = mask_slot_words(h, b);
+  }
   rq.bwd.g_xi = g_xi;
   rq.bwd.g_lam = g_lam;
   rq.bwd.g_fp = g_fp;

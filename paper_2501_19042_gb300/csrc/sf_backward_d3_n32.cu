@@ -1,4 +1,5 @@
-// Adjoint kernel instantiated for dim = 3, up to 32 robots.
+// Adjoint kernel and the mask-writing training forward, instantiated for
+// dim = 3, up to 32 robots.
 #include <cstring>
 
 #include "sf_backward_kernel.cuh"
@@ -21,6 +22,9 @@ cudaError_t launch_bwd_d3_n32(const FusedArgs& a, const BwdLaunchArgs& b, const 
   x.ck_every = b.ck_every;
   x.total_coefs = b.total_coefs;
   x.ring = b.ring;
+  x.tail_mask = b.tail_mask;
+  x.ring_mask = b.ring_mask;
+  x.mask_slot = b.mask_slot;
   x.g_xi = b.g_xi;
   x.g_lam = b.g_lam;
   x.g_fp = b.g_fp;
@@ -37,6 +41,15 @@ cudaError_t launch_bwd_d3_n32(const FusedArgs& a, const BwdLaunchArgs& b, const 
 }
 cudaError_t prepare_bwd_d3_n32(int smem) {
   return cudaFuncSetAttribute(fused_impl::fused_bwd_kernel<3, 32, 256>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+// Forward with checkpoints (training): also writes the activity masks of
+// the last checkpoint segment for this adjoint.
+cudaError_t launch_fused_train_d3_n32(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st) {
+  return fused_impl::launch_t<3, 32, 384, 0, true>(a, l, st);
+}
+cudaError_t prepare_fused_train_d3_n32(int smem) {
+  return cudaFuncSetAttribute(fused_impl::fused_fwd_kernel<3, 32, 384, 0, true>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 }  // namespace sf

@@ -41,6 +41,9 @@ struct BwdArgs {
   int ck_every;
   long long total_coefs;
   float* ring;             // [ck_every + 1][2][total_coefs]
+  const unsigned* tail_mask;   // activity masks of the last segment [ck_every][mask_slot]
+  unsigned* ring_mask;         // activity masks of a recomputed segment [ck_every][mask_slot]
+  long long mask_slot;
   const float* g_xi;       // dL/dxi^K or null
   const float* g_lam;      // dL/dlambda^K or null
   const float* g_fp;       // per-sample weight of sum ||z^{k+1} - z^k||^2, or null
@@ -56,100 +59,85 @@ struct BwdArgs {
 
 // Pair rows of the adjoint for one chunk: Delta_bar = (J_e - I)^T (u_i - u_j)
 // with u = positions of g_bar, added to E_bar_i and subtracted from E_bar_j
-// in the chunk buffer.
+// in the chunk buffer. Only the rows the forward iteration recorded as active
+// (activity masks, slot mk) are visited: inactive rows have J_e = I.
 template <int DIM, int NMAX>
-__device__ void adj_pair_phase(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, int t0, int TCc) {
+__device__ void adj_pair_phase(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, int t0, int TCc,
+                               const unsigned* mk) {
   constexpr int RS = DIM * NP;
+  constexpr int MW = mask_words(NMAX), PW = mask_pair_words(NMAX);
   const Lay& L = c.L;
   const int N = c.N;
   const int nA = c.G * TCc;
-  for (int base = c.warp * 32; base < nA; base += c.nwarps * 32) {
-    const int u = base + c.lane;
-    const bool valid = u < nA;
-    const int s = valid ? u / TCc : 0;
-    const int tl = valid ? u - s * TCc : 0;
+  for (int u = c.tid; u < nA; u += c.nthr) {
+    const int s = u / TCc;
+    const int tl = u - s * TCc;
     const int t = t0 + tl;
     float* blk = c.blk(s);
+    float* eb = blk + L.EB + tl * L.EP;
+    for (int q = 0; q < N * DIM; ++q) eb[q] = 0.0f;
+    const uint4* m4 = reinterpret_cast<const uint4*>(mk + ((size_t)s * L.T + t) * MW);
+    unsigned w[(PW + 3) / 4 * 4];
+#pragma unroll
+    for (int q = 0; q < (PW + 3) / 4; ++q) {
+      const uint4 v = m4[q];
+      w[4 * q] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w;
+    }
+    unsigned any = 0u;
+#pragma unroll
+    for (int q = 0; q < PW; ++q) any |= w[q];
+    if (!any) continue;
     float Pr[NV];
     row_from(c.BASIS + (size_t)t * BASIS_ROW, Pr);
-    float* eb = blk + L.EB + tl * L.EP;
-    if (valid)
-      for (int q = 0; q < N * DIM; ++q) eb[q] = 0.0f;
-    // scaled positions of xi^k (far-apart dummies past the chunk); rows of
-    // pairs are tested without branches, the positions of g_bar are formed
-    // only when some row of the warp is active
-    float p[NMAX][DIM];
 #pragma unroll
-    for (int i = 0; i < NMAX; ++i) {
-      if (i < N) {
-        state<DIM>(Pr, blk + L.C + i * RS, p[i]);
+    for (int q = 0; q < PW; ++q) {
+      unsigned m = w[q];
+      while (m) {
+        int idx = q * 32 + __ffs(m) - 1;
+        m &= m - 1;
+        // row-major upper triangle: row i holds NMAX - 1 - i pairs
+        int i = 0;
+        while (idx >= NMAX - 1 - i) {
+          idx -= NMAX - 1 - i;
+          ++i;
+        }
+        const int j = i + 1 + idx;
+        float pi[DIM], pj[DIM], ui[DIM], uj[DIM];
+        state<DIM>(Pr, blk + L.C + i * RS, pi);
+        state<DIM>(Pr, blk + L.C + j * RS, pj);
+        state<DIM>(Pr, blk + L.U + i * RS, ui);
+        state<DIM>(Pr, blk + L.U + j * RS, uj);
 #pragma unroll
-        for (int x = 0; x < DIM; ++x) p[i][x] *= (x == 2 ? pc.inv_b : pc.inv_a);
-      } else {
+        for (int x = 0; x < DIM; ++x) {
+          pi[x] *= (x == 2 ? pc.inv_b : pc.inv_a);
+          pj[x] *= (x == 2 ? pc.inv_b : pc.inv_a);
+        }
+        float ds[DIM];
 #pragma unroll
-        for (int x = 0; x < DIM; ++x) p[i][x] = 0.0f;
-      }
-      if (!valid) p[i][0] = 4096.0f * (float)i;
-    }
-    bool anyrow = false;
+        for (int x = 0; x < DIM; ++x) ds[x] = pi[x] - pj[x];
+        float s2 = 0.0f;
 #pragma unroll
-    for (int i = 0; i < NMAX; ++i)
+        for (int x = 0; x < DIM; ++x) s2 = fmaf(ds[x], ds[x], s2);
+        // delta = M ds; M^-2 delta = ds / (a, a, b)
+        float U[DIM], mm[DIM], d[DIM];
+        float du = 0.0f;
 #pragma unroll
-      for (int j = 0; j < NMAX; ++j)
-        if (j > i && j < N) anyrow |= scaled_d2<DIM>(p[i], p[j]) < 1.0f;
-    if (!__any_sync(FULL, anyrow)) continue;
-    float ug[NMAX][DIM];
+        for (int x = 0; x < DIM; ++x) {
+          const float ax = x == 2 ? pc.coll_b : pc.coll_a;
+          d[x] = ds[x] * ax;
+          mm[x] = ds[x] / ax;
+          U[x] = ui[x] - uj[x];
+          du = fmaf(d[x], U[x], du);
+        }
+        const bool zero = (s2 == 0.0f);
+        const float inv = rsqrtf(zero ? 1.0f : s2);
+        const float f = zero ? -1.0f : inv - 1.0f;
+        const float wgt = zero ? 0.0f : inv * inv * inv * du;
 #pragma unroll
-    for (int i = 0; i < NMAX; ++i) {
-      if (i < N) state<DIM>(Pr, blk + L.U + i * RS, ug[i]);
-      else
-#pragma unroll
-        for (int x = 0; x < DIM; ++x) ug[i][x] = 0.0f;
-    }
-#pragma unroll
-    for (int i = 0; i < NMAX; ++i) {
-      if (i + 1 < N) {
-        bool row = false;
-#pragma unroll
-        for (int j = 0; j < NMAX; ++j)
-          if (j > i && j < N) row |= scaled_d2<DIM>(p[i], p[j]) < 1.0f;
-        if (!__any_sync(FULL, row)) continue;
-#pragma unroll
-        for (int j = 0; j < NMAX; ++j) {
-          if (j > i && j < N) {
-            float ds[DIM];
-#pragma unroll
-            for (int x = 0; x < DIM; ++x) ds[x] = p[i][x] - p[j][x];
-            float s2 = 0.0f;
-#pragma unroll
-            for (int x = 0; x < DIM; ++x) s2 = fmaf(ds[x], ds[x], s2);
-            const bool act = valid && s2 < 1.0f;
-            if (__any_sync(FULL, act)) {
-              // delta = M ds; M^-2 delta = ds / (a, a, b)
-              float U[DIM], m[DIM], d[DIM];
-              float du = 0.0f;
-#pragma unroll
-              for (int x = 0; x < DIM; ++x) {
-                const float ax = x == 2 ? pc.coll_b : pc.coll_a;
-                d[x] = ds[x] * ax;
-                m[x] = ds[x] / ax;
-                U[x] = ug[i][x] - ug[j][x];
-                du = fmaf(d[x], U[x], du);
-              }
-              const bool zero = (s2 == 0.0f);
-              const float inv = rsqrtf(zero ? 1.0f : s2);
-              const float f = act ? (zero ? -1.0f : inv - 1.0f) : 0.0f;
-              const float w = (act && !zero) ? inv * inv * inv * du : 0.0f;
-              if (act) {
-#pragma unroll
-                for (int x = 0; x < DIM; ++x) {
-                  const float db = fmaf(f, U[x], -w * m[x]);
-                  eb[i * DIM + x] += db;
-                  eb[j * DIM + x] -= db;
-                }
-              }
-            }
-          }
+        for (int x = 0; x < DIM; ++x) {
+          const float db = fmaf(f, U[x], -wgt * mm[x]);
+          eb[i * DIM + x] += db;
+          eb[j * DIM + x] -= db;
         }
       }
     }
@@ -160,7 +148,8 @@ __device__ void adj_pair_phase(const Cta<DIM, NMAX>& c, const ProblemConsts& pc,
 // dL/dxi += F^T Delta_bar, per (sample, robot, range of t), into PG partials.
 template <int DIM, int NMAX>
 __device__ void adj_contract_phase(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, int t0, int TCc,
-                                   bool first_chunk) {
+                                   bool first_chunk, const unsigned* mk) {
+  constexpr int MW = mask_words(NMAX), PW = mask_pair_words(NMAX);
   constexpr int RS = DIM * NP;
   const Lay& L = c.L;
   const int N = c.N, G = c.G, NQ = L.NQ;
@@ -193,20 +182,25 @@ __device__ void adj_contract_phase(const Cta<DIM, NMAX>& c, const ProblemConsts&
       const bool live = step < trip;
       const int tl = live ? ta + step : ta;
       const float* brow = c.BASIS + (size_t)(t0 + tl) * BASIS_ROW;
-      float P[NV], Pd[NV], Pdd[NV];
-      row_from(brow, P);
-      row_from(brow + NP, Pd);
-      row_from(brow + 2 * NP, Pdd);
       float e[DIM], vb[DIM], ab[DIM];
       const float* ebp = blk + L.EB + tl * L.EP + i * DIM;
 #pragma unroll
       for (int x = 0; x < DIM; ++x) { e[x] = live ? ebp[x] : 0.0f; vb[x] = 0.0f; ab[x] = 0.0f; }
-      if (pc.use_v) {
+      // ball rows outside their ball in the forward iteration (activity masks)
+      bool vact = false, aact = false;
+      if (live) {
+        const unsigned* mb = mk + ((size_t)s * L.T + t0 + tl) * MW + PW;
+        vact = (mb[i >> 5] >> (i & 31)) & 1u;
+        aact = (mb[(NMAX + i) >> 5] >> ((NMAX + i) & 31)) & 1u;
+      }
+      if (pc.use_v && __any_sync(FULL, vact)) {
+        float Pd[NV];
+        row_from(brow + NP, Pd);
         float v[DIM], n2 = 0.0f;
 #pragma unroll
         for (int x = 0; x < DIM; ++x) { v[x] = dot_reg(Pd, cc[x]); n2 = fmaf(v[x], v[x], n2); }
-        const bool act = live && n2 > pc.v_max * pc.v_max;
-        if (__any_sync(FULL, act)) {
+        const bool act = vact;
+        {
           float U[DIM], du = 0.0f;
 #pragma unroll
           for (int x = 0; x < DIM; ++x) { U[x] = dot_reg(Pd, gb[x]); du = fmaf(v[x], U[x], du); }
@@ -216,12 +210,14 @@ __device__ void adj_contract_phase(const Cta<DIM, NMAX>& c, const ProblemConsts&
           for (int x = 0; x < DIM; ++x) vb[x] = act ? fmaf(rr - 1.0f, U[x], -rr * inv * inv * du * v[x]) : 0.0f;
         }
       }
-      if (pc.use_a) {
+      if (pc.use_a && __any_sync(FULL, aact)) {
+        float Pdd[NV];
+        row_from(brow + 2 * NP, Pdd);
         float a[DIM], n2 = 0.0f;
 #pragma unroll
         for (int x = 0; x < DIM; ++x) { a[x] = dot_reg(Pdd, cc[x]); n2 = fmaf(a[x], a[x], n2); }
-        const bool act = live && n2 > pc.a_max * pc.a_max;
-        if (__any_sync(FULL, act)) {
+        const bool act = aact;
+        {
           float U[DIM], du = 0.0f;
 #pragma unroll
           for (int x = 0; x < DIM; ++x) { U[x] = dot_reg(Pdd, gb[x]); du = fmaf(a[x], U[x], du); }
@@ -238,12 +234,17 @@ __device__ void adj_contract_phase(const Cta<DIM, NMAX>& c, const ProblemConsts&
         nb |= (vb[x] != 0.0f) || (ab[x] != 0.0f);
       }
       if (__any_sync(FULL, ne)) {
+        float P[NV];
+        row_from(brow, P);
 #pragma unroll
         for (int x = 0; x < DIM; ++x)
 #pragma unroll
           for (int k = 0; k < NV; ++k) g2[x][k] = fmaf(P[k], e[x], g2[x][k]);
       }
       if (__any_sync(FULL, nb)) {
+        float Pd[NV], Pdd[NV];
+        row_from(brow + NP, Pd);
+        row_from(brow + 2 * NP, Pdd);
 #pragma unroll
         for (int x = 0; x < DIM; ++x)
 #pragma unroll
@@ -271,7 +272,8 @@ __device__ __forceinline__ const float* ring_lam(const float* ring, int j, long 
 // Adjoint of iteration k (z^k -> z^{k+1}); XB, LB hold dL/dz^{k+1} on entry
 // and dL/dz^k on exit.
 template <int DIM, int NMAX>
-__device__ void adjoint_step(const Cta<DIM, NMAX>& c, const BwdArgs& A, const float* ring, int j) {
+__device__ void adjoint_step(const Cta<DIM, NMAX>& c, const BwdArgs& A, const float* ring, int j,
+                             const unsigned* mslot) {
   constexpr int RS = DIM * NP;
   const Lay& L = c.L;
   const ProblemConsts& pc = A.pc;
@@ -339,9 +341,9 @@ __device__ void adjoint_step(const Cta<DIM, NMAX>& c, const BwdArgs& A, const fl
   // (3) time-domain adjoint of the alpha / beta / d steps, in chunks
   for (int t0 = 0; t0 < T; t0 += L.TC) {
     const int TCc = min(L.TC, T - t0);
-    adj_pair_phase<DIM, NMAX>(c, pc, t0, TCc);
+    adj_pair_phase<DIM, NMAX>(c, pc, t0, TCc, mslot + c.mask0);
     __syncthreads();
-    adj_contract_phase<DIM, NMAX>(c, pc, t0, TCc, t0 == 0);
+    adj_contract_phase<DIM, NMAX>(c, pc, t0, TCc, t0 == 0, mslot + c.mask0);
     __syncthreads();
   }
   // (4) dL/dxi^k = Wop^T xb + F^T Delta_bar; fixed-point term w.r.t. z^k
@@ -402,21 +404,25 @@ __global__ void __launch_bounds__(MAXT, 1) fused_bwd_kernel(const __grid_constan
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int kb = seg * ck, ke = min(K, kb + ck);
     const float* rg = ring;
+    const unsigned* mg = A.ring_mask;
     if (seg == nseg - 1) {
       rg = tail;
+      mg = A.tail_mask;
     } else {
       const float* cx = A.ckpt + (size_t)seg * 2 * tot;
       load_state<DIM, NMAX>(c, cx, cx + tot, nullptr, A.xi_bar);
       __syncthreads();
       store_state<DIM, NMAX>(c, ring, ring + tot, 0);
       for (int k = kb; k < ke; ++k) {
-        fwd_iteration<DIM, NMAX>(c, pc, A.xi_bar, k, false, nullptr, 0, false);
+        fwd_iteration<DIM, NMAX, 0, true>(c, pc, A.xi_bar, k, false, nullptr, 0, false,
+                                          A.ring_mask + (size_t)(k - kb) * A.mask_slot);
         float* slot = ring + (size_t)(k - kb + 1) * 2 * tot;
         store_state<DIM, NMAX>(c, slot, slot + tot, 0);
       }
     }
     __syncthreads();
-    for (int k = ke - 1; k >= kb; --k) adjoint_step<DIM, NMAX>(c, A, rg, k - kb);
+    for (int k = ke - 1; k >= kb; --k)
+      adjoint_step<DIM, NMAX>(c, A, rg, k - kb, mg + (size_t)(k - kb) * A.mask_slot);
   }
   for (int v = c.tid; v < G * DIM * N * NV; v += c.nthr) {
     const int s = v / (DIM * N * NV), rem = v % (DIM * N * NV);

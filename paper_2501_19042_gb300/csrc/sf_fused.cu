@@ -10,6 +10,7 @@ namespace sf {
 
 #define SF_DECL(D, NM)                                                                                   \
   cudaError_t launch_fused_d##D##_n##NM(const FusedArgs&, const FusedLaunch&, cudaStream_t);           \
+  cudaError_t launch_fused_train_d##D##_n##NM(const FusedArgs&, const FusedLaunch&, cudaStream_t);     \
   cudaError_t launch_bwd_d##D##_n##NM(const FusedArgs&, const BwdLaunchArgs&, const FusedLaunch&,      \
                                       cudaStream_t);
 #define SF_DECL_TC(D, NM)                                                                          \
@@ -21,6 +22,7 @@ SF_DECL_TC(3, 8) SF_DECL_TC(3, 16) SF_DECL_TC(3, 24) SF_DECL_TC(3, 32)
 #undef SF_DECL
 #undef SF_DECL_TC
 #define SF_PREP(D, NM) cudaError_t prepare_fused_d##D##_n##NM(int); cudaError_t prepare_bwd_d##D##_n##NM(int); \
+  cudaError_t prepare_fused_train_d##D##_n##NM(int); \
   cudaError_t prepare_fused_tc1_d##D##_n##NM(int); cudaError_t prepare_fused_tc2_d##D##_n##NM(int);
 SF_PREP(2, 8) SF_PREP(2, 16) SF_PREP(2, 24) SF_PREP(2, 32) SF_PREP(3, 8) SF_PREP(3, 16) SF_PREP(3, 24) SF_PREP(3, 32)
 #undef SF_PREP
@@ -48,11 +50,15 @@ cudaError_t prepare_kernels(int dim, int smem, int prec) {
   if (dim == 3) {
     chk(prepare_fused_d3_n8(smem)); chk(prepare_fused_d3_n16(smem)); chk(prepare_fused_d3_n24(smem));
     chk(prepare_fused_d3_n32(smem));
+    chk(prepare_fused_train_d3_n8(smem)); chk(prepare_fused_train_d3_n16(smem));
+    chk(prepare_fused_train_d3_n24(smem)); chk(prepare_fused_train_d3_n32(smem));
     chk(prepare_bwd_d3_n8(smem)); chk(prepare_bwd_d3_n16(smem)); chk(prepare_bwd_d3_n24(smem));
     chk(prepare_bwd_d3_n32(smem));
   } else {
     chk(prepare_fused_d2_n8(smem)); chk(prepare_fused_d2_n16(smem)); chk(prepare_fused_d2_n24(smem));
     chk(prepare_fused_d2_n32(smem));
+    chk(prepare_fused_train_d2_n8(smem)); chk(prepare_fused_train_d2_n16(smem));
+    chk(prepare_fused_train_d2_n24(smem)); chk(prepare_fused_train_d2_n32(smem));
     chk(prepare_bwd_d2_n8(smem)); chk(prepare_bwd_d2_n16(smem)); chk(prepare_bwd_d2_n24(smem));
     chk(prepare_bwd_d2_n32(smem));
   }
@@ -196,6 +202,20 @@ cudaError_t launch_fused(const FusedArgs& a, const FusedLaunch& l, cudaStream_t 
     SF_TC(2, 3, 8) SF_TC(2, 3, 16) SF_TC(2, 3, 24) SF_TC(2, 3, 32)
     SF_TC(2, 2, 8) SF_TC(2, 2, 16) SF_TC(2, 2, 24) SF_TC(2, 2, 32)
 #undef SF_TC
+    return cudaErrorInvalidValue;
+  }
+  if (a.amask) {
+    if (dim == 3) {
+      if (l.nmax == 8) return launch_fused_train_d3_n8(a, l, st);
+      if (l.nmax == 16) return launch_fused_train_d3_n16(a, l, st);
+      if (l.nmax == 24) return launch_fused_train_d3_n24(a, l, st);
+      if (l.nmax == 32) return launch_fused_train_d3_n32(a, l, st);
+    } else if (dim == 2) {
+      if (l.nmax == 8) return launch_fused_train_d2_n8(a, l, st);
+      if (l.nmax == 16) return launch_fused_train_d2_n16(a, l, st);
+      if (l.nmax == 24) return launch_fused_train_d2_n24(a, l, st);
+      if (l.nmax == 32) return launch_fused_train_d2_n32(a, l, st);
+    }
     return cudaErrorInvalidValue;
   }
   if (dim == 3) {

@@ -227,10 +227,14 @@ __device__ __forceinline__ void pair_apply(const float (&pi)[DIM], const float (
 
 // Pair phase of one chunk [t0, t0 + TCc). With TCM (tensor-core form) the
 // scaled positions are already in the lane's chunk-buffer row, and the row's
-// element NMAX*DIM is set to 1 when some pair of the row is active.
-template <int DIM, int NMAX, bool TCM = false>
+// element NMAX*DIM is set to 1 when some pair of the row is active. With
+// MASKS the lane's activity-mask row (mk + (s T + t) mask_words) is cleared
+// and the bit of every active pair row is set.
+template <int DIM, int NMAX, bool TCM = false, bool MASKS = false>
 __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G, int N, int t0, int TCc,
-                           const ProblemConsts& pc, bool want_res, int warp, int nwarps, int lane) {
+                           const ProblemConsts& pc, bool want_res, int warp, int nwarps, int lane,
+                           unsigned* mk = nullptr) {
+  constexpr int MW = mask_words(NMAX);
   constexpr int RS = DIM * NP;
   const int nA = G * TCc;
   for (int base = warp * 32; base < nA; base += nwarps * 32) {
@@ -250,6 +254,18 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
       for (int x = 0; x < DIM; ++x) E[i][x] = 0.0f;
     float res2 = 0.0f;
     float* ebw = blk + L.EB + tl * L.EP;   // this lane's row of the chunk buffer
+    unsigned* mrow = MASKS ? mk + ((size_t)s * L.T + t) * MW : nullptr;
+    if (MASKS && valid) {
+#pragma unroll
+      for (int q = 0; q < MW / 4; ++q) reinterpret_cast<uint4*>(mrow)[q] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    // records pair row (i, j) of this lane as active
+    auto mark = [&](int i, int j, bool act) {
+      if (MASKS && valid && act) {
+        const int b = pair_bit(NMAX, i, j);
+        atomicOr(mrow + (b >> 5), 1u << (b & 31));
+      }
+    };
     if (NMAX <= 16) {
       // scaled positions of all robots in registers; lanes past the chunk get
       // far-apart dummies so that none of their rows tests active
@@ -295,9 +311,13 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
           if (__any_sync(FULL, row)) {
 #pragma unroll
             for (int j = 0; j < NMAX; ++j)
-              if (j > i && j < N)
-                if (__any_sync(FULL, scaled_d2<DIM>(p[i], p[j]) < 1.0f))
+              if (j > i && j < N) {
+                const bool act = scaled_d2<DIM>(p[i], p[j]) < 1.0f;
+                if (__any_sync(FULL, act)) {
+                  mark(i, j, act);
                   pair_apply_scaled<DIM>(p[i], p[j], E[i], E[j], pc, res2);
+                }
+              }
           }
         }
       }
@@ -338,9 +358,13 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
             for (int a = 0; a < 8; ++a)
 #pragma unroll
               for (int b = 0; b < 8; ++b)
-                if (b > a && I0 + b < N)
-                  if (__any_sync(FULL, scaled_d2<DIM>(pI[a], pI[b]) < 1.0f))
+                if (b > a && I0 + b < N) {
+                  const bool act = scaled_d2<DIM>(pI[a], pI[b]) < 1.0f;
+                  if (__any_sync(FULL, act)) {
+                    mark(I0 + a, I0 + b, act);
                     pair_apply_scaled<DIM>(pI[a], pI[b], E[I0 + a], E[I0 + b], pc, res2);
+                  }
+                }
           }
 #pragma unroll
           for (int j = 0; j < NMAX; ++j) {
@@ -354,9 +378,13 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
               for (int a = 0; a < 8; ++a) grp |= scaled_d2<DIM>(pI[a], pj) < 1.0f;
               if (__any_sync(FULL, grp)) {
 #pragma unroll
-                for (int a = 0; a < 8; ++a)
-                  if (__any_sync(FULL, scaled_d2<DIM>(pI[a], pj) < 1.0f))
+                for (int a = 0; a < 8; ++a) {
+                  const bool act = scaled_d2<DIM>(pI[a], pj) < 1.0f;
+                  if (__any_sync(FULL, act)) {
+                    mark(I0 + a, j, act);
                     pair_apply_scaled<DIM>(pI[a], pj, E[I0 + a], E[j], pc, res2);
+                  }
+                }
               }
             }
           }
@@ -392,10 +420,12 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
 
 // Contraction phase of one chunk: F^T of the residual per (sample, robot).
 // Each 11-term group P[t] E, Pd[t] qv, Pdd[t] qa is skipped when it is zero
-// on every lane of the warp (inactive rows contribute exactly 0).
-template <int DIM>
+// on every lane of the warp (inactive rows contribute exactly 0). With MASKS
+// the ball rows outside their ball set their bits in the activity masks.
+template <int DIM, int NMAX = 0, bool MASKS = false>
 __device__ void contract_phase(float* SAMP, const Lay& L, const float* BASIS, int G, int N, int t0, int TCc,
-                               bool first_chunk, const ProblemConsts& pc, bool want_res, int tid, int nthr) {
+                               bool first_chunk, const ProblemConsts& pc, bool want_res, int tid, int nthr,
+                               unsigned* mk = nullptr) {
   const int RS = DIM * NP;
   const int NQ = L.NQ;
   const int nB = NQ * G * N;
@@ -440,17 +470,33 @@ __device__ void contract_phase(float* SAMP, const Lay& L, const float* BASIS, in
         qa[x] = 0.0f;
       }
       float rl = 0.0f;
+      unsigned* mball = nullptr;
+      if (MASKS)
+        mball = mk + ((size_t)s * L.T + t0 + tl) * mask_words(NMAX) + mask_pair_words(NMAX);
       if (pc.use_v) {
         float v[DIM];
 #pragma unroll
         for (int x = 0; x < DIM; ++x) v[x] = dot_reg(Pd, c[x]);
         ball_residual<DIM>(v, pc.v_max, qv, rl);
+        if (MASKS) {
+          float n2 = 0.0f;
+#pragma unroll
+          for (int x = 0; x < DIM; ++x) n2 = fmaf(v[x], v[x], n2);
+          if (live && n2 > pc.v_max * pc.v_max) atomicOr(mball + (i >> 5), 1u << (i & 31));
+        }
       }
       if (pc.use_a) {
         float a[DIM];
 #pragma unroll
         for (int x = 0; x < DIM; ++x) a[x] = dot_reg(Pdd, c[x]);
         ball_residual<DIM>(a, pc.a_max, qa, rl);
+        if (MASKS) {
+          float n2 = 0.0f;
+#pragma unroll
+          for (int x = 0; x < DIM; ++x) n2 = fmaf(a[x], a[x], n2);
+          const int b = NMAX + i;
+          if (live && n2 > pc.a_max * pc.a_max) atomicOr(mball + (b >> 5), 1u << (b & 31));
+        }
       }
       if (live) rb += rl;
       if (__any_sync(FULL, ne)) {
@@ -888,7 +934,7 @@ template <int DIM, int NMAX>
 struct Cta {
   Lay L;
   int N, G, robot_off, gsample0;
-  long long per_sample, coef0;
+  long long per_sample, coef0, mask0;
   float *BASIS, *OPS, *BETA, *SAMP;
   uint32_t *BN, *BT;
   int tid, nthr, warp, lane, nwarps;
@@ -907,6 +953,7 @@ struct Cta {
     gsample0 = sc[sidx].sample_off + s_first;
     per_sample = (long long)DIM * N * NV;
     coef0 = sc[sidx].coef_off + (long long)s_first * per_sample;
+    mask0 = sc[sidx].mask_off + (long long)s_first * T * mask_words(NMAX);
     BASIS = tcm ? nullptr : sm;
     BN = tcm ? reinterpret_cast<uint32_t*>(sm + L.bno) : nullptr;
     BT = tcm ? reinterpret_cast<uint32_t*>(sm + L.bto) : nullptr;
@@ -1047,9 +1094,9 @@ __device__ void store_state(const Cta<DIM, NMAX>& c, float* xi_dst, float* lam_d
 // One iteration of f_FP on every sample of the CTA (time chunks, then the
 // lambda step and the xi step). keep_prev stores xi^k in the EB region for
 // the final residual. fp (when set) adds ||z^{k+1} - z^k||^2 per sample to FPR.
-template <int DIM, int NMAX, int PREC = 0>
+template <int DIM, int NMAX, int PREC = 0, bool MASKS = false>
 __device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, const float* xi_bar, int it,
-                              bool keep_prev, float* hist, int total_samples, bool fp) {
+                              bool keep_prev, float* hist, int total_samples, bool fp, unsigned* mslot = nullptr) {
   constexpr int RS = DIM * NP;
   const Lay& L = c.L;
   const int T = pc.T, N = c.N, G = c.G, TC = L.TC;
@@ -1065,6 +1112,13 @@ __device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, 
       __syncthreads();
       tc_contract_phase<DIM, NMAX, PREC>(c.SAMP, L, c.BN, c.BT, G, N, t0, TCc, t0 == 0, pc, want_res, c.warp,
                                          c.nwarps, c.lane);
+    } else if (MASKS && mslot != nullptr) {
+      unsigned* mk = mslot + c.mask0;
+      pair_phase<DIM, NMAX, false, true>(c.SAMP, L, c.BASIS, G, N, t0, TCc, pc, want_res, c.warp, c.nwarps,
+                                         c.lane, mk);
+      __syncthreads();
+      contract_phase<DIM, NMAX, true>(c.SAMP, L, c.BASIS, G, N, t0, TCc, t0 == 0, pc, want_res, c.tid, c.nthr,
+                                      mk);
     } else {
       pair_phase<DIM, NMAX>(c.SAMP, L, c.BASIS, G, N, t0, TCc, pc, want_res, c.warp, c.nwarps, c.lane);
       __syncthreads();
@@ -1172,7 +1226,9 @@ __device__ void write_checkpoint(const Cta<DIM, NMAX>& c, float* ckpt, int ck, l
 }
 
 // PREC 0: float32 form; 1 / 2: tensor-core form with bf16 / fp16 operands.
-template <int DIM, int NMAX, int MAXT, int PREC>
+// MASKS (float32 form with checkpoints): the iterations of the last
+// checkpoint segment also write their activity masks for the adjoint.
+template <int DIM, int NMAX, int MAXT, int PREC, bool MASKS = false>
 __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constant__ FusedArgs A) {
   extern __shared__ float4 smem4[];
   float* sm = reinterpret_cast<float*>(smem4);
@@ -1202,7 +1258,8 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
   for (int it = 0; it < pc.K; ++it) {
     if (A.ckpt && it % A.ck_every == 0) write_checkpoint<DIM, NMAX>(c, A.ckpt, it / A.ck_every, A.total_coefs);
     if (tail && it >= last_ck) write_checkpoint<DIM, NMAX>(c, tail, it - last_ck, A.total_coefs);
-    fwd_iteration<DIM, NMAX, PREC>(c, pc, A.xi_bar, it, it == pc.K - 1, A.hist, A.total_samples, fp);
+    unsigned* ms = (MASKS && A.amask && it >= last_ck) ? A.amask + (size_t)(it - last_ck) * A.amask_slot : nullptr;
+    fwd_iteration<DIM, NMAX, PREC, MASKS>(c, pc, A.xi_bar, it, it == pc.K - 1, A.hist, A.total_samples, fp, ms);
   }
   if (tail) write_checkpoint<DIM, NMAX>(c, tail, pc.K - last_ck, A.total_coefs);
 
@@ -1229,9 +1286,9 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
   store_state<DIM, NMAX>(c, A.xi_out, A.lam_out, 0);
 }
 
-template <int DIM, int NMAX, int MAXT, int PREC = 0>
+template <int DIM, int NMAX, int MAXT, int PREC = 0, bool MASKS = false>
 cudaError_t launch_t(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st) {
-  auto k = fused_fwd_kernel<DIM, NMAX, MAXT, PREC>;
+  auto k = fused_fwd_kernel<DIM, NMAX, MAXT, PREC, MASKS>;
   if (l.warps * 32 > MAXT) return cudaErrorInvalidConfiguration;
   k<<<l.n_ctas, l.warps * 32, l.smem, st>>>(a);
   return cudaGetLastError();

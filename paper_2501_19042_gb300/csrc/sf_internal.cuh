@@ -45,7 +45,19 @@ struct SceneDesc {
   int robot_off;   // row offset into start / goal
   int sample_off;  // global index of the scene's first sample
   long long coef_off;  // float offset of the scene's first sample in coefficient arrays
+  long long mask_off;  // word offset of the scene's first sample in an activity-mask slot
 };
+
+// Activity masks (written by forward iterations that feed the adjoint): per
+// (sample, t) a row of mask_words(NMAX) words, first the pair rows (bit
+// pair_bit(i, j) for i < j, row-major over the upper triangle of NMAX x NMAX),
+// then the ball rows (bit i: velocity of robot i outside its ball, bit NMAX + i:
+// acceleration), zero-padded to a multiple of 4 words.
+__host__ __device__ constexpr int mask_pair_words(int nmax) { return (nmax * (nmax - 1) / 2 + 31) / 32; }
+__host__ __device__ constexpr int mask_words(int nmax) {
+  return ((mask_pair_words(nmax) + (2 * nmax + 31) / 32) + 3) / 4 * 4;
+}
+__host__ __device__ constexpr int pair_bit(int nmax, int i, int j) { return i * nmax - i * (i + 1) / 2 + (j - i - 1); }
 
 // Bounded-wait / status words latched on the device.
 enum : int { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
@@ -85,6 +97,8 @@ struct FusedArgs {
   int ck_every;            // checkpoint period
   long long total_coefs;
   float* fp_res2;          // [total samples] sum_k ||z^{k+1} - z^k||^2, or null
+  unsigned* amask;         // activity masks of the last checkpoint segment [ck_every][slot], or null
+  long long amask_slot;    // words per mask slot (one iteration, all samples)
   SceneDesc sc[MAX_SCENES_PER_LAUNCH];
 };
 
@@ -170,6 +184,9 @@ struct BwdLaunchArgs {
   int ck_every;
   long long total_coefs;
   float* ring;
+  const unsigned* tail_mask;   // masks of the last segment, written by the training forward
+  unsigned* ring_mask;         // masks of a recomputed segment [ck_every][slot]
+  long long mask_slot;
   const float* g_xi;
   const float* g_lam;
   const float* g_fp;
