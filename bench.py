@@ -33,6 +33,9 @@ RHO = 0.1
 METRIC = "SF-projected samples/s (16 robots 3D, residual<=1e-3), chosen vs plain form"
 UNIT = "samples/s"
 FP32_LANES_PER_SM = 128
+DTYPES = {"fp32": "f32",
+          "bf16": "bf16 tensor-core products (three-term), f32 accumulation and element-wise work",
+          "fp16": "fp16 tensor-core products, f32 accumulation and element-wise work"}
 
 
 def ops_per_sample_iter(N: int, T: int, dim: int, nv: int = 11, use_v: bool = True, use_a: bool = True):
@@ -135,7 +138,7 @@ def run_gpu(args):
     sc = si.scene(spec, 1 + rank)
     S, K = spec.n_samples, spec.K
     f = P.SafetyFilter(dim=spec.dim, T=spec.T, rho=RHO, coll_a=spec.coll, v_max=spec.v_max, a_max=spec.a_max,
-                       max_robots=spec.n_robots, t_final=spec.t_final, device=dev.index)
+                       max_robots=spec.n_robots, t_final=spec.t_final, precision=args.precision, device=dev.index)
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
     xb, st, gl = t(sc.xi_bar), t(sc.start), t(sc.goal)
     stream = torch.cuda.current_stream(dev)
@@ -210,7 +213,7 @@ def run_gpu(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded swarm generator)",
+            "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic (seeded swarm generator)",
             "impl": "gb300", "form": args.form,
             "config": {"workload": workload_name(spec), "global_batch": world * S, "per_gpu_samples": S,
                        "parallelism": f"independent sample batches on {world} GPU(s)",
@@ -426,6 +429,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--form", default="fused", choices=["fused", "plain"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"],
+                    help="contraction precision of the timed forward (the metric is quoted in fp32)")
     ap.add_argument("--cpu-samples", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-diff", action="store_true")
