@@ -121,6 +121,7 @@ class ClockSampler:
 def run_gpu(args):
     import torch
     import paper_2501_19042_gb300 as P
+    from paper_2501_19042_gb300.sharding import max_over_ranks
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -173,10 +174,7 @@ def run_gpu(args):
     clocks = clk.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, stops)]
     ms = float(np.mean(step_ms))
-    if dist is not None:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, device=dev)
     f.sync_status()
 
     # residual condition of the metric
@@ -194,10 +192,7 @@ def run_gpu(args):
         f.project_host(hx, hs, hg, K, form=args.form, out=hout)
     barrier()
     e2e_s = (time.perf_counter() - t1) / e2e_steps
-    if dist is not None:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(e2e_s, device=dev)
     h2d = (hx.numel() + hs.numel() + hg.numel()) * 4
     d2h = (2 * hx.numel() + S) * 4
 
