@@ -96,9 +96,9 @@ typedef struct {
   double coll_b;
   double v_max;        /* velocity bound (norm); <= 0 disables the block */
   double a_max;        /* acceleration bound (norm); <= 0 disables the block */
-  int use_workspace;   /* Eq. (workspace_con); must be 0 in this build */
-  double ws_center[3];
-  double ws_a, ws_b;
+  int use_workspace;   /* 1: every position stays in the workspace spheroid of Eq. (workspace_con) */
+  double ws_center[3]; /* its centre p_w (first dim entries used) */
+  double ws_a, ws_b;   /* its semi-axes (a_w, a_w, b_w), > 0 when use_workspace (ws_b unused in 2D) */
   int max_robots;      /* largest N of any scene used with the handle, 1..SF_MAX_ROBOTS */
   int precision;       /* sf_precision */
   int checkpoint_every;/* k of the checkpointed backward; 0 = no gradient support */

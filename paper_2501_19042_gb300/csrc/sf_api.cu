@@ -78,6 +78,16 @@ ProblemConsts consts(const sf_problem& pb, int K) {
   c.use_a = pb.a_max > 0.0;
   c.v_max = (float)(c.use_v ? pb.v_max : 0.0);
   c.a_max = (float)(c.use_a ? pb.a_max : 0.0);
+  c.use_w = pb.use_workspace ? 1 : 0;
+  for (int x = 0; x < 3; ++x) {
+    const double wa = x == 2 ? pb.ws_b : pb.ws_a;
+    const double ca = x == 2 ? pb.coll_b : pb.coll_a;
+    c.wc[x] = c.use_w ? (float)pb.ws_center[x] : 0.0f;
+    c.wa[x] = c.use_w ? (float)wa : 0.0f;
+    c.winv[x] = c.use_w ? (float)(1.0 / wa) : 0.0f;
+    c.wk[x] = c.use_w ? (float)(ca / wa) : 0.0f;
+    c.wo[x] = c.use_w ? (float)(pb.ws_center[x] / wa) : 0.0f;
+  }
   return c;
 }
 
@@ -314,7 +324,12 @@ sf_status sf_create(const sf_problem* pb, int device, sf_handle** out) {
   if (pb->max_robots < 1 || pb->max_robots > SF_MAX_ROBOTS) return SF_ERR_INVALID_ARG;
   if (pb->precision < SF_PREC_FP32 || pb->precision > SF_PREC_FP16) return SF_ERR_INVALID_ARG;
   if (pb->checkpoint_every < 0) return SF_ERR_INVALID_ARG;
-  if (pb->use_workspace) return SF_ERR_UNSUPPORTED;
+  if (pb->use_workspace != 0 && pb->use_workspace != 1) return SF_ERR_INVALID_ARG;
+  if (pb->use_workspace) {
+    if (!finite_pos(pb->ws_a) || !finite_pos(pb->ws_b)) return SF_ERR_INVALID_ARG;
+    for (int x = 0; x < 3; ++x)
+      if (!std::isfinite(pb->ws_center[x])) return SF_ERR_INVALID_ARG;
+  }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return SF_ERR_CUDA;
 
@@ -344,7 +359,7 @@ sf_status sf_create(const sf_problem* pb, int device, sf_handle** out) {
     e = cudaMemsetAsync(h->status, 0, sizeof(int), st);
     if (e == cudaSuccess)
       e = launch_precompute(pb->T, pb->order, pb->t_final, pb->rho, pb->v_max > 0, pb->a_max > 0,
-                            pb->max_robots, h->basis, h->ops, scratch, st);
+                            pb->use_workspace, pb->max_robots, h->basis, h->ops, scratch, st);
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
   }

@@ -77,16 +77,22 @@ __device__ void adj_pair_phase(const Cta<DIM, NMAX>& c, const ProblemConsts& pc,
     float* eb = blk + L.EB + tl * L.EP;
     for (int q = 0; q < N * DIM; ++q) eb[q] = 0.0f;
     const uint4* m4 = reinterpret_cast<const uint4*>(mk + ((size_t)s * L.T + t) * MW);
-    unsigned w[(PW + 3) / 4 * 4];
+    unsigned w[MW];
 #pragma unroll
-    for (int q = 0; q < (PW + 3) / 4; ++q) {
+    for (int q = 0; q < MW / 4; ++q) {
       const uint4 v = m4[q];
       w[4 * q] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w;
     }
+    // workspace rows: bits 2 NMAX .. 3 NMAX - 1 after the pair words
+    constexpr int WB = 2 * NMAX, WW = PW + (WB >> 5);
+    unsigned long long wsm = w[WW];
+    if (WW + 1 < MW) wsm |= (unsigned long long)w[(WW + 1 < MW) ? WW + 1 : WW] << 32;
+    wsm = (wsm >> (WB & 31)) & ((NMAX == 64 ? 0ull : (1ull << NMAX)) - 1ull);
+    if (!pc.use_w) wsm = 0ull;
     unsigned any = 0u;
 #pragma unroll
     for (int q = 0; q < PW; ++q) any |= w[q];
-    if (!any) continue;
+    if (!any && !wsm) continue;
     float Pr[NV];
     row_from(c.BASIS + (size_t)t * BASIS_ROW, Pr);
 #pragma unroll
@@ -140,6 +146,28 @@ __device__ void adj_pair_phase(const Cta<DIM, NMAX>& c, const ProblemConsts& pc,
           eb[j * DIM + x] -= db;
         }
       }
+    }
+    // workspace rows outside the spheroid: e = p_w + D / sqrt(s2) with
+    // D = p - p_w, s2 = ||M_w^-1 D||^2; (J_e - I)^T u = (s2^-1/2 - 1) u -
+    // s2^-3/2 (D . u) M_w^-2 D, added to E_bar of the robot
+    while (wsm) {
+      const int i = __ffsll((long long)wsm) - 1;
+      wsm &= wsm - 1ull;
+      float pi[DIM], ui[DIM];
+      state<DIM>(Pr, blk + L.C + i * RS, pi);
+      state<DIM>(Pr, blk + L.U + i * RS, ui);
+      float d[DIM], mm[DIM], s2 = 0.0f, du = 0.0f;
+#pragma unroll
+      for (int x = 0; x < DIM; ++x) {
+        d[x] = pi[x] - pc.wc[x];
+        mm[x] = d[x] * pc.winv[x] * pc.winv[x];
+        s2 = fmaf(d[x], mm[x], s2);
+        du = fmaf(d[x], ui[x], du);
+      }
+      const float inv = rsqrtf(s2);
+      const float f = inv - 1.0f, wgt = inv * inv * inv * du;
+#pragma unroll
+      for (int x = 0; x < DIM; ++x) eb[i * DIM + x] += fmaf(f, ui[x], -wgt * mm[x]);
     }
   }
 }

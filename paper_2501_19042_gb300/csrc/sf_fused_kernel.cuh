@@ -225,6 +225,34 @@ __device__ __forceinline__ void pair_apply(const float (&pi)[DIM], const float (
   }
 }
 
+// Workspace row of one robot from its collision-scaled position ps: when
+// outside the workspace spheroid, q = e - p = (p - p_w) (1 / sqrt(s2) - 1) is
+// added to the robot's E (the row is P c_i, like a pair row's), its square to
+// res2, and (MASKS) the row's activity bit is set.
+template <int DIM, int NMAX, bool MASKS>
+__device__ __forceinline__ void ws_row(const float (&ps)[DIM], float (&Ei)[DIM], bool valid, int i,
+                                       const ProblemConsts& pc, float& res2, unsigned* mrow) {
+  float w[DIM], s2 = 0.0f;
+#pragma unroll
+  for (int x = 0; x < DIM; ++x) {
+    w[x] = fmaf(ps[x], pc.wk[x], -pc.wo[x]);
+    s2 = fmaf(w[x], w[x], s2);
+  }
+  if (valid && s2 > 1.0f) {
+    const float f = rsqrtf(s2) - 1.0f;
+#pragma unroll
+    for (int x = 0; x < DIM; ++x) {
+      const float q = f * (w[x] * pc.wa[x]);
+      Ei[x] += q;
+      res2 = fmaf(q, q, res2);
+    }
+    if (MASKS) {
+      const int b = 2 * NMAX + i;
+      atomicOr(mrow + mask_pair_words(NMAX) + (b >> 5), 1u << (b & 31));
+    }
+  }
+}
+
 // Pair phase of one chunk [t0, t0 + TCc). With TCM (tensor-core form) the
 // scaled positions are already in the lane's chunk-buffer row, and the row's
 // element NMAX*DIM is set to 1 when some pair of the row is active. With
@@ -321,6 +349,27 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
           }
         }
       }
+      // workspace rows of every robot (Eq. workspace_con): q = e - p pulls a
+      // position outside the spheroid back to its surface
+      if (pc.use_w) {
+        bool outw = false;
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i)
+          if (i < N) {
+            float s2 = 0.0f;
+#pragma unroll
+            for (int x = 0; x < DIM; ++x) {
+              const float w = fmaf(p[i][x], pc.wk[x], -pc.wo[x]);
+              s2 = fmaf(w, w, s2);
+            }
+            outw |= valid && s2 > 1.0f;
+          }
+        if (__any_sync(FULL, outw)) {
+#pragma unroll
+          for (int i = 0; i < NMAX; ++i)
+            if (i < N) ws_row<DIM, NMAX, MASKS>(p[i], E[i], valid, i, pc, res2, mrow);
+        }
+      }
     } else {
       // scaled positions staged once in the lane's own row of the chunk
       // buffer (which later receives E); robots in blocks of 8 reloaded
@@ -388,6 +437,28 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
               }
             }
           }
+        }
+      }
+      if (pc.use_w) {
+        bool outw = false;
+        for (int i = 0; i < N; ++i) {
+          float s2 = 0.0f;
+#pragma unroll
+          for (int x = 0; x < DIM; ++x) {
+            const float w = fmaf(valid ? ebw[i * DIM + x] : 0.0f, pc.wk[x], -pc.wo[x]);
+            s2 = fmaf(w, w, s2);
+          }
+          outw |= valid && s2 > 1.0f;
+        }
+        if (__any_sync(FULL, outw)) {
+#pragma unroll
+          for (int i = 0; i < NMAX; ++i)
+            if (i < N) {
+              float pi[DIM];
+#pragma unroll
+              for (int x = 0; x < DIM; ++x) pi[x] = valid ? ebw[i * DIM + x] : 0.0f;
+              ws_row<DIM, NMAX, MASKS>(pi, E[i], valid, i, pc, res2, mrow);
+            }
         }
       }
     }
@@ -920,6 +991,17 @@ __device__ void residual_phase(float* SAMP, const Lay& L, const float* BASIS, in
 #pragma unroll
         for (int x = 0; x < DIM; ++x) {
           const float r = (an[x] - ao[x]) - q[x];
+          r2 = fmaf(r, r, r2);
+        }
+      }
+      if (pc.use_w) {
+        float po[DIM], pn[DIM], q[DIM];
+        state<DIM>(Pr, Cp + i * RS, po);
+        state<DIM>(Pr, C + i * RS, pn);
+        ws_residual<DIM>(po, pc, q, dummy);
+#pragma unroll
+        for (int x = 0; x < DIM; ++x) {
+          const float r = (pn[x] - po[x]) - q[x];
           r2 = fmaf(r, r, r2);
         }
       }

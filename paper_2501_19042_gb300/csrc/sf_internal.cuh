@@ -51,11 +51,12 @@ struct SceneDesc {
 // Activity masks (written by forward iterations that feed the adjoint): per
 // (sample, t) a row of mask_words(NMAX) words, first the pair rows (bit
 // pair_bit(i, j) for i < j, row-major over the upper triangle of NMAX x NMAX),
-// then the ball rows (bit i: velocity of robot i outside its ball, bit NMAX + i:
-// acceleration), zero-padded to a multiple of 4 words.
+// then the rows of robot i (bit i: velocity outside its ball, bit NMAX + i:
+// acceleration outside its ball, bit 2 NMAX + i: position outside the
+// workspace), zero-padded to a multiple of 4 words.
 __host__ __device__ constexpr int mask_pair_words(int nmax) { return (nmax * (nmax - 1) / 2 + 31) / 32; }
 __host__ __device__ constexpr int mask_words(int nmax) {
-  return ((mask_pair_words(nmax) + (2 * nmax + 31) / 32) + 3) / 4 * 4;
+  return ((mask_pair_words(nmax) + (3 * nmax + 31) / 32) + 3) / 4 * 4;
 }
 __host__ __device__ constexpr int pair_bit(int nmax, int i, int j) { return i * nmax - i * (i + 1) / 2 + (j - i - 1); }
 
@@ -71,6 +72,11 @@ struct ProblemConsts {
   float tie;             // e of a pair at delta = 0: (0,0,b) in 3D, (a,0) in 2D
   float v_max, a_max;
   int use_v, use_a;
+  // workspace spheroid, Eq. (workspace_con): centre, semi-axes, their inverses, and the
+  // map of collision-scaled positions ps = p M_a^-1 to workspace-scaled
+  // offsets (p - p_w) M_w^-1 = ps * wk - wo
+  int use_w;
+  float wc[3], wa[3], winv[3], wk[3], wo[3];
 };
 
 struct FusedArgs {
@@ -145,8 +151,29 @@ __device__ __forceinline__ void ball_residual(const float* v, float r, float* q,
   }
 }
 
+// Workspace block (polar form of Eq. workspace_polar, centre p_w, semi-axes
+// (a_w, a_w, b_w), d in [0, 1]): with the scaled offset s2 = ||M_w^-1 (p - p_w)||^2
+// the closed forms give e = p when s2 <= 1 and e = p_w + (p - p_w) / sqrt(s2)
+// otherwise. q = e - p (position p unscaled); |q|^2 is added to res2.
+template <int DIM>
+__device__ __forceinline__ void ws_residual(const float* p, const ProblemConsts& pc, float* q, float& res2) {
+  float d[DIM], s2 = 0.0f;
+#pragma unroll
+  for (int x = 0; x < DIM; ++x) {
+    d[x] = p[x] - pc.wc[x];
+    const float w = d[x] * pc.winv[x];
+    s2 = fmaf(w, w, s2);
+  }
+  const float f = s2 > 1.0f ? rsqrtf(s2) - 1.0f : 0.0f;
+#pragma unroll
+  for (int x = 0; x < DIM; ++x) {
+    q[x] = f * d[x];
+    res2 = fmaf(q[x], q[x], res2);
+  }
+}
+
 // ---- host-side launchers (defined in the .cu files) ------------------------
-cudaError_t launch_precompute(int T, int order, double t_final, double rho, int use_v, int use_a,
+cudaError_t launch_precompute(int T, int order, double t_final, double rho, int use_v, int use_a, int use_w,
                               int max_robots, float* basis32, float* ops32, double* scratch64,
                               cudaStream_t st);
 size_t precompute_scratch_doubles(int T, int order, int max_robots);

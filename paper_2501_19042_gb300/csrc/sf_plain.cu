@@ -104,6 +104,11 @@ __global__ void project_kernel(PlainArgs a, int it) {
         for (int x = 0; x < DIM; ++x) E[x] -= q[x];
       }
     }
+    if (a.pc.use_w) {   // workspace row of robot i (its F row is P, like the pair rows)
+      float q[DIM];
+      ws_residual<DIM>(pi, a.pc, q, r2);
+      for (int x = 0; x < DIM; ++x) E[x] += q[x];
+    }
     float v[DIM], acc[DIM], qv[DIM], qa[DIM];
     for (int x = 0; x < DIM; ++x) {
       v[x] = X[xoff(s, 1, x, i, t, DIM, N, T)];
@@ -220,6 +225,14 @@ __global__ void residual_kernel(PlainArgs a) {
         const float dnew = pn[x] - a.Q[xoff(s, 0, x, j, t, DIM, N, T)];
         const float e = (po[x] - pjo[x]) + qo[x];
         const float rr = dnew - e;
+        r2 = fmaf(rr, rr, r2);
+      }
+    }
+    if (a.pc.use_w) {
+      float q[DIM], dummy = 0.f;
+      ws_residual<DIM>(po, a.pc, q, dummy);
+      for (int x = 0; x < DIM; ++x) {
+        const float rr = pn[x] - (po[x] + q[x]);
         r2 = fmaf(rr, rr, r2);
       }
     }

@@ -69,7 +69,7 @@ __global__ void basis_kernel(int T, int order, double t_final, float* basis32, d
   }
 }
 
-__global__ void gram_kernel(int T, int use_v, int use_a, double* s64) {
+__global__ void gram_kernel(int T, int use_v, int use_a, int use_w, double* s64) {
   const int k = threadIdx.x / NV, m = threadIdx.x % NV;
   if (threadIdx.x >= NV * NV) return;
   const double* P = s64;
@@ -82,6 +82,7 @@ __global__ void gram_kernel(int T, int use_v, int use_a, double* s64) {
     q += P[t * NV + k] * P[t * NV + m];
     if (use_v) g += Pd[t * NV + k] * Pd[t * NV + m];
     if (use_a) g += Pdd[t * NV + k] * Pdd[t * NV + m];
+    if (use_w) g += P[t * NV + k] * P[t * NV + m];   // workspace rows F_w = I (x) P
   }
   Q[k * NV + m] = q;
   G[k * NV + m] = g;
@@ -181,7 +182,7 @@ size_t precompute_scratch_doubles(int T, int order, int max_robots) {
   return 3 * (size_t)T * NV + 2 * NV * NV + 8;
 }
 
-cudaError_t launch_precompute(int T, int order, double t_final, double rho, int use_v, int use_a,
+cudaError_t launch_precompute(int T, int order, double t_final, double rho, int use_v, int use_a, int use_w,
                               int max_robots, float* basis32, float* ops32, double* scratch64,
                               cudaStream_t st) {
   int* fail = reinterpret_cast<int*>(scratch64 + 3 * (size_t)T * NV + 2 * NV * NV);
@@ -190,7 +191,7 @@ cudaError_t launch_precompute(int T, int order, double t_final, double rho, int 
   e = cudaMemsetAsync(ops32, 0, sizeof(float) * (size_t)(max_robots + 1) * OPS_STRIDE, st);
   if (e != cudaSuccess) return e;
   basis_kernel<<<(T + 127) / 128, 128, 0, st>>>(T, order, t_final, basis32, scratch64);
-  gram_kernel<<<1, NV * NV, 0, st>>>(T, use_v, use_a, scratch64);
+  gram_kernel<<<1, NV * NV, 0, st>>>(T, use_v, use_a, use_w, scratch64);
   kkt_kernel<<<(max_robots + 31) / 32, 32, 0, st>>>(T, rho, max_robots, scratch64, ops32, fail);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

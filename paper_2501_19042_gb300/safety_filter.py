@@ -39,7 +39,10 @@ class SafetyFilter:
     def __init__(self, dim: int = 3, T: int = 100, rho: float = 0.1, coll_a: float = 0.5,
                  coll_b: float | None = None, v_max: float = 2.0, a_max: float = 3.0,
                  max_robots: int = 32, order: int = 10, t_final: float = 5.0,
-                 precision: str = "fp32", checkpoint_every: int = 0, device=None):
+                 precision: str = "fp32", checkpoint_every: int = 0, device=None,
+                 workspace=None):
+        """workspace: None, or (centre, a_w, b_w) of the spheroid every
+        position must stay in (Eq. workspace_con)."""
         self._lib = nat.load()
         if device is None:
             device = torch.cuda.current_device()
@@ -50,6 +53,12 @@ class SafetyFilter:
         pb.coll_b = coll_a if coll_b is None else coll_b
         pb.v_max, pb.a_max = v_max, a_max
         pb.use_workspace = 0
+        if workspace is not None:
+            centre, wa, wb = workspace
+            pb.use_workspace = 1
+            for i in range(3):
+                pb.ws_center[i] = float(centre[i]) if i < len(centre) else 0.0
+            pb.ws_a, pb.ws_b = float(wa), float(wb)
         pb.max_robots = max_robots
         pb.precision = nat.PREC[precision]
         pb.checkpoint_every = checkpoint_every

@@ -25,11 +25,16 @@ def _tsf(O, sc, rho=RHO_3D):
     return TorchSF(P, Pd, Pdd, sc.start, sc.goal, rho, sc.spec.coll, sc.spec.coll, sc.spec.v_max, sc.spec.a_max)
 
 
-def test_torch_unroll_forward_and_gradient_match_oracle_fd(oracle_lib):
+@pytest.mark.parametrize("ws", [None, ((0.1, 0.0, 0.0), 1.6, 1.0)])
+def test_torch_unroll_forward_and_gradient_match_oracle_fd(oracle_lib, ws):
+    """The FP64 unroll (with and without workspace rows) against the oracle's
+    forward and central finite differences of it."""
     O = oracle_lib
     sc = _instance()
     K = 15
-    ts = _tsf(O, sc)
+    P_, Pd_, Pdd_ = O.basis(10, sc.spec.T, sc.spec.t_final)
+    ts = TorchSF(P_, Pd_, Pdd_, sc.start, sc.goal, RHO_3D, sc.spec.coll, sc.spec.coll, sc.spec.v_max,
+                 sc.spec.a_max, workspace=ws)
     rng = np.random.default_rng(0)
     xb = torch.tensor(sc.xi_bar[:1])
     x0 = xb.clone() + torch.tensor(rng.normal(size=xb.shape) * 0.05)
@@ -38,9 +43,14 @@ def test_torch_unroll_forward_and_gradient_match_oracle_fd(oracle_lib):
     x0.requires_grad_(True)
     xbv = xb.clone().requires_grad_(True)
     xi, lam, _ = ts.unroll(x0, l0, xbv, K)
+    wkw = {} if ws is None else dict(use_workspace=True, ws_center=ws[0], ws_a=ws[1], ws_b=ws[2])
     pb = O.Problem(dim=3, n_robots=sc.spec.n_robots, T=sc.spec.T, rho=RHO_3D, coll_a=sc.spec.coll,
-                   coll_b=sc.spec.coll)
+                   coll_b=sc.spec.coll, **wkw)
     sf = O.OracleSF(pb, sc.start, sc.goal)
+    if ws is not None:   # the workspace rows are active on this input
+        P0 = np.asarray(P_)
+        pos = np.einsum("tk,dnk->ntd", P0, x0.detach()[0].numpy()) - np.asarray(ws[0])
+        assert (np.sqrt((pos[..., 0] ** 2 + pos[..., 1] ** 2) / ws[1] ** 2 + pos[..., 2] ** 2 / ws[2] ** 2) > 1).any()
     ref = sf.run(xb[0].numpy().reshape(-1), K, xi0=x0.detach()[0].numpy().reshape(-1), lam0=l0[0].numpy().reshape(-1))
     np.testing.assert_allclose(xi.detach().numpy().reshape(-1), ref["xi"], atol=1e-12)
     L = (w * xi).sum()

@@ -15,7 +15,7 @@ import torch
 
 
 class TorchSF:
-    def __init__(self, P, Pd, Pdd, start, goal, rho, a, b, v_max, a_max):
+    def __init__(self, P, Pd, Pdd, start, goal, rho, a, b, v_max, a_max, workspace=None):
         dt = torch.float64
         self.P, self.Pd, self.Pdd = (torch.as_tensor(m, dtype=dt) for m in (P, Pd, Pdd))
         self.T, self.nv = self.P.shape
@@ -24,6 +24,7 @@ class TorchSF:
         self.N, self.dim = start.shape
         self.rho, self.a, self.b = rho, a, b
         self.v_max, self.a_max = v_max, a_max
+        self.ws = workspace          # None or (centre, a_w, b_w)
         N, nv = self.N, self.nv
         pairs = [(i, j) for i in range(N) for j in range(i + 1, N)]
         self.pi = torch.tensor([p[0] for p in pairs], dtype=torch.long)
@@ -34,6 +35,8 @@ class TorchSF:
             G = G + self.Pd.T @ self.Pd
         if a_max > 0:
             G = G + self.Pdd.T @ self.Pdd
+        if workspace is not None:
+            G = G + Q                 # workspace rows I (x) P
         L = N * torch.eye(N, dtype=dt) - torch.ones((N, N), dtype=dt)
         H = torch.kron(L, Q) + torch.kron(torch.eye(N, dtype=dt), G)
         A1 = torch.stack([self.P[0], self.Pd[0], self.Pdd[0], self.P[-1], self.Pd[-1], self.Pdd[-1]])
@@ -79,6 +82,14 @@ class TorchSF:
                 nrm = torch.where(outside, n2, torch.ones_like(n2)).sqrt()
                 ev = torch.where(outside, r * v / nrm, v)
                 out[name] = ev - v
+        if self.ws is not None:
+            c = torch.tensor(np.asarray(self.ws[0], np.float64)[: self.dim], dtype=torch.float64)
+            wax = torch.tensor([self.ws[1]] * 2 + [self.ws[2]], dtype=torch.float64)[: self.dim]
+            d = p - c[None, :, None, None]
+            s2 = ((d / wax[None, :, None, None]) ** 2).sum(1, keepdim=True)
+            outside = s2 > 1
+            sc = torch.where(outside, s2, torch.ones_like(s2)).rsqrt()
+            out["ws"] = torch.where(outside, d * sc - d, torch.zeros_like(d))
         return out
 
     def Ft(self, q):
@@ -90,6 +101,8 @@ class TorchSF:
             g = g + torch.einsum("tk,sdnt->sdnk", self.Pd, q["vel"])
         if "acc" in q:
             g = g + torch.einsum("tk,sdnt->sdnk", self.Pdd, q["acc"])
+        if "ws" in q:
+            g = g + torch.einsum("tk,sdnt->sdnk", self.P, q["ws"])
         return g
 
     def step(self, xi, lam, xi_bar):
