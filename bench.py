@@ -231,6 +231,10 @@ def run_gpu(args):
             line["batching"] = batching_timing(P, dev)
         if not args.no_precision:
             line["precision"] = precision_timing(P, dev)
+        if not args.no_workspace:
+            line["workspace"] = workspace_timing(P, dev)
+        if not args.no_sweep:
+            line["sweep"] = sweep_timing(P, dev)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(spec, sc, args.cpu_samples)
         print(json.dumps(line), flush=True)
@@ -317,6 +321,90 @@ def precision_timing(P, dev, n_check: int = 64, steps: int = 3):
     return {"workload": f"3D N={spec.n_robots}, S={spec.n_samples}, T={spec.T}, K={spec.K}, sample init, "
                         f"rho={RHO}; errors vs the FP64 oracle on samples 0..{n_check - 1}",
             "oracle_seconds": t_or, "modes": modes}
+
+
+def workspace_timing(P, dev, n_check: int = 16, steps: int = 3):
+    """The bench workload (N=16 3D, S=1024, T=100, K=200, seed 1) with the
+    workspace block on: a spheroid centred at the origin with b_w = a_w / 2
+    and a_w 8 % larger than needed to hold every start and goal. Time per call
+    against the same call without the block, the median final ||r_p||, the
+    share of (sample, robot, t) positions outside the workspace in the
+    input, and errors against the FP64 oracle on samples 0..n_check-1."""
+    import torch
+    import oracle
+    spec = workload_spec()
+    sc = si.scene(spec, 1)
+    pts = np.concatenate([sc.start, sc.goal])
+    a_w = 1.08 * float(np.sqrt(pts[:, 0] ** 2 + pts[:, 1] ** 2 + (2.0 * pts[:, 2]) ** 2).max())
+    ws = ((0.0, 0.0, 0.0), a_w, a_w / 2)
+    Pm = oracle.basis(spec.order, spec.T, spec.t_final)[0]
+    pos = np.einsum("tk,sdnk->sntd", Pm, sc.xi_bar)
+    outside = float(((pos[..., 0] ** 2 + pos[..., 1] ** 2) / a_w ** 2 + pos[..., 2] ** 2 / (a_w / 2) ** 2 > 1).mean())
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    xb, st, gl = t(sc.xi_bar), t(sc.start), t(sc.goal)
+    res = {}
+    for name, w in (("without", None), ("with", ws)):
+        f = P.SafetyFilter(dim=3, T=spec.T, rho=RHO, coll_a=spec.coll, v_max=spec.v_max, a_max=spec.a_max,
+                           max_robots=spec.n_robots, t_final=spec.t_final, workspace=w, device=dev.index)
+        out = f.project(xb, st, gl, spec.K)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            f.project(xb, st, gl, spec.K, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        res[name] = (a.elapsed_time(b) / steps, out)
+    oracle.build()
+    pb = oracle.Problem(dim=3, n_robots=spec.n_robots, T=spec.T, order=spec.order, t_final=spec.t_final,
+                        rho=RHO, coll_a=spec.coll, coll_b=spec.coll, v_max=spec.v_max, a_max=spec.a_max,
+                        use_workspace=True, ws_center=ws[0], ws_a=ws[1], ws_b=ws[2])
+    ref = oracle.run_batch(pb, sc.start, sc.goal, sc.xi_bar[:n_check], K=spec.K, n_threads=os.cpu_count() or 1)
+    ms, out = res["with"]
+    xi = out.xi[:n_check].double().cpu().numpy().reshape(n_check, -1)
+    xr = np.asarray(ref["xi"]).reshape(n_check, -1)
+    err = np.linalg.norm(xi - xr, axis=1) / np.linalg.norm(xr, axis=1)
+    dres = np.abs(out.residual[:n_check].double().cpu().numpy() - np.asarray(ref["rp_final"]))
+    return {"workload": f"3D N={spec.n_robots}, S={spec.n_samples}, T={spec.T}, K={spec.K}, workspace spheroid "
+                        f"a_w={a_w:.3f} m, b_w={a_w / 2:.3f} m at the origin",
+            "input_positions_outside": outside, "ms": ms, "samples_per_s": spec.n_samples / (ms * 1e-3),
+            "ms_without_workspace": res["without"][0], "median_final_residual": float(out.residual.median()),
+            "xi_rel_l2_max": float(err.max()), "resid_absdiff_max": float(dres.max()),
+            "oracle_samples": n_check}
+
+
+def sweep_timing(P, dev, reps: int = 3):
+    """SF-only computation time in the layout of the paper's computation-time
+    figure: per swarm size N in {4, 8, 16} (3D, the bench's box scene, T=100),
+    time per sf_project call against the batch size (10..200 samples, K=200)
+    and against the number of iterations (K=10..400, 10 samples). CUDA
+    events, mean of `reps` calls after one warm-up call."""
+    import torch
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    out = {"workload": "3D, T=100, sample init, rho=0.1, box 8x8x4 m; per N: ms per call vs batch "
+                       "(K=200) and vs K (batch 10)", "by_N": {}}
+    for N in (4, 8, 16):
+        spec = si.config_n16_3d(n_robots=N, n_samples=200)
+        sc = si.scene(spec, 100 + N)
+        f = P.SafetyFilter(dim=3, T=spec.T, rho=RHO, coll_a=spec.coll, v_max=spec.v_max, a_max=spec.a_max,
+                           max_robots=N, t_final=spec.t_final, device=dev.index)
+        st, gl = t(sc.start), t(sc.goal)
+
+        def timed(batch, K):
+            xb = t(sc.xi_bar[:batch])
+            r = f.project(xb, st, gl, K)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                f.project(xb, st, gl, K, out=r)
+            b.record()
+            torch.cuda.synchronize()
+            return round(a.elapsed_time(b) / reps, 4)
+
+        out["by_N"][str(N)] = {"ms_vs_batch_K200": {str(bs): timed(bs, 200) for bs in (10, 25, 50, 100, 200)},
+                               "ms_vs_K_batch10": {str(K): timed(10, K) for K in (10, 50, 100, 200, 400)}}
+    return out
 
 
 def batching_timing(P, dev):
@@ -431,6 +519,8 @@ def main():
     ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--no-batching", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-workspace", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
