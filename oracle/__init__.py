@@ -84,6 +84,10 @@ def _lib_handle():
             lib.oracle_sf_kkt_size.argtypes = [C.c_void_p]
             lib.oracle_sf_kkt_size.restype = C.c_int
             lib.oracle_sf_kkt_matrix.argtypes = [C.c_void_p, _dp]
+            lib.oracle_eq_project.argtypes = [C.c_void_p, _dp, _dp]
+            lib.oracle_eq_project.restype = C.c_int
+            lib.oracle_eq_project_adjoint.argtypes = [C.c_void_p, _dp, _dp, _dp]
+            lib.oracle_eq_project_adjoint.restype = C.c_int
             lib.oracle_sf_run.argtypes = [C.c_void_p, _dp, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp, _dp]
             lib.oracle_sf_run.restype = C.c_int
             lib.oracle_sf_run_batch.argtypes = [C.POINTER(OracleProblem), _dp, _dp, _dp, _dp, C.c_int,
@@ -230,6 +234,23 @@ class OracleSF:
         out = np.zeros(out_len)
         getattr(o, name)(o.ctx, _ptr(xin), _ptr(out))
         return out
+
+    def eq_project(self, xi_in) -> np.ndarray:
+        """QP layer of the decoders: argmin ||xi - xi_in||^2 s.t. A xi = b."""
+        x = _f64(xi_in).reshape(-1)
+        out = np.zeros(self.n)
+        if self._lib.oracle_eq_project(self._h, _ptr(x), _ptr(out)) != 0:
+            raise RuntimeError("oracle_eq_project failed")
+        return out
+
+    def eq_project_adjoint(self, g):
+        """(dL/dxi_in, dL/db) of the QP layer for dL/dxi_out = g."""
+        gg = _f64(g).reshape(-1)
+        gi = np.zeros(self.n)
+        gb = np.zeros(self.pb.dim * self.pb.n_robots * 6)
+        if self._lib.oracle_eq_project_adjoint(self._h, _ptr(gg), _ptr(gi), _ptr(gb)) != 0:
+            raise RuntimeError("oracle_eq_project_adjoint failed")
+        return gi, gb
 
     def run(self, xi_bar, K: int, xi0=None, lam0=None):
         """K iterations for one sample. Returns dict with xi, lam, rp_hist,

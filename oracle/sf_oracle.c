@@ -446,6 +446,63 @@ void oracle_sf_dense_A(oracle_sf *s, double *A, double *b) {
       }
 }
 
+/* ------------------------------------------------------------------------- */
+/* The differentiable QP layer of the generative decoders (Sec. III-A / B:     */
+/* Eq. (sf_form) without the inequality constraints): the Euclidean           */
+/* projection of xi' onto {xi : A xi = b}, i.e. the solution of               */
+/*   [[I, A^T], [A, 0]] [xi; nu] = [xi'; b].                                   */
+/* A is block diagonal with the 6 x nvar block A1 per (axis, robot), so the    */
+/* system is solved per block with the oracle's own LU (not the closed form).  */
+/* The adjoint of xi' -> xi is the same solve with right-hand side [g; 0]:     */
+/* the KKT matrix is symmetric, so its inverse maps [g; 0] to                 */
+/* [dL/dxi'; dL/db].                                                           */
+/* ------------------------------------------------------------------------- */
+
+static int eq_block_solve(const oracle_sf *s, const double *top, const double *bot, double *x_out,
+                          double *nu_out) {
+  const int nv = s->nvar, kd = nv + 6;
+  double *K = (double *)calloc((size_t)kd * kd, sizeof(double));
+  double *r = (double *)malloc(sizeof(double) * (size_t)kd);
+  int *piv = (int *)malloc(sizeof(int) * (size_t)kd);
+  for (int k = 0; k < nv; ++k) K[k * kd + k] = 1.0;
+  for (int q = 0; q < 6; ++q)
+    for (int k = 0; k < nv; ++k) {
+      K[(nv + q) * kd + k] = s->A1[q * nv + k];
+      K[k * kd + nv + q] = s->A1[q * nv + k];
+    }
+  for (int k = 0; k < nv; ++k) r[k] = top[k];
+  for (int q = 0; q < 6; ++q) r[nv + q] = bot ? bot[q] : 0.0;
+  const int rc = lu_factor(K, kd, piv);
+  if (rc == 0) {
+    lu_solve(K, kd, piv, r);
+    for (int k = 0; k < nv; ++k) x_out[k] = r[k];
+    if (nu_out)
+      for (int q = 0; q < 6; ++q) nu_out[q] = r[nv + q];
+  }
+  free(K); free(r); free(piv);
+  return rc;
+}
+
+int oracle_eq_project(oracle_sf *s, const double *xi_in, double *xi_out) {
+  const int N = s->pb.n_robots, nv = s->nvar, dim = s->pb.dim;
+  for (int ax = 0; ax < dim; ++ax)
+    for (int i = 0; i < N; ++i) {
+      const int o = (ax * N + i) * nv;
+      if (eq_block_solve(s, xi_in + o, s->b + (ax * N + i) * 6, xi_out + o, NULL) != 0) return -1;
+    }
+  return 0;
+}
+
+int oracle_eq_project_adjoint(oracle_sf *s, const double *g, double *g_in, double *g_b) {
+  const int N = s->pb.n_robots, nv = s->nvar, dim = s->pb.dim;
+  for (int ax = 0; ax < dim; ++ax)
+    for (int i = 0; i < N; ++i) {
+      const int o = (ax * N + i) * nv;
+      if (eq_block_solve(s, g + o, NULL, g_in + o, g_b ? g_b + (ax * N + i) * 6 : NULL) != 0) return -1;
+    }
+  return 0;
+}
+
 int oracle_sf_kkt_size(oracle_sf *s) { return s->kdim; }
 
 void oracle_sf_kkt_matrix(oracle_sf *s, double *K) { build_kkt(s, K); }

@@ -105,6 +105,12 @@ int oracle_sf_dense_F(oracle_sf *s, double *F);
 void oracle_sf_dense_A(oracle_sf *s, double *A, double *b);
 /* The KKT matrix of one axis, [[I + rho F_ax^T F_ax, A_ax^T], [A_ax, 0]], size
  * (N*nvar + 6N)^2, as factored by the oracle. */
+/* QP layer of the decoders (Sec. III-A / B): xi_out = argmin ||xi - xi_in||^2
+ * subject to A xi = b (boundary conditions of every robot); layout
+ * [dim][N][nvar]. The adjoint maps dL/dxi_out = g to dL/dxi_in (g_in) and
+ * dL/db (g_b, [dim][N][6], may be NULL). Return 0, or -1 on a singular block. */
+int oracle_eq_project(oracle_sf *s, const double *xi_in, double *xi_out);
+int oracle_eq_project_adjoint(oracle_sf *s, const double *g, double *g_in, double *g_b);
 int oracle_sf_kkt_size(oracle_sf *s);
 void oracle_sf_kkt_matrix(oracle_sf *s, double *K);
 
