@@ -235,6 +235,8 @@ def run_gpu(args):
             line["workspace"] = workspace_timing(P, dev)
         if not args.no_sweep:
             line["sweep"] = sweep_timing(P, dev)
+        if not args.no_qp:
+            line["qp_layer"] = qp_layer_timing(P, dev)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(spec, sc, args.cpu_samples)
         print(json.dumps(line), flush=True)
@@ -407,6 +409,46 @@ def sweep_timing(P, dev, reps: int = 3):
     return out
 
 
+def qp_layer_timing(P, dev, n_samples: int = 65536, reps: int = 20):
+    """The decoders' QP layer (sf_eq_project) on a batch of decoder outputs:
+    N=16 robots 3D, 65,536 samples (3.1M coefficient rows of 11 floats, 276
+    MB read + written per call). HBM-bound: achieved = (44 B read + 44 B
+    written) per row / CUDA-event time per call, against the measured copy
+    bandwidth; the input is larger than L2, so no flush is needed."""
+    import torch
+    spec = workload_spec()
+    sc = si.scene(si.config_n16_3d(n_samples=8), 1)     # the scene's starts and goals
+    f = P.SafetyFilter(dim=3, T=spec.T, rho=RHO, coll_a=spec.coll, max_robots=spec.n_robots, device=dev.index)
+    g = torch.Generator(device=dev).manual_seed(0)
+    xp = torch.randn((n_samples, 3, spec.n_robots, 11), generator=g, device=dev)
+    st = torch.as_tensor(sc.start, dtype=torch.float32, device=dev)
+    gl = torch.as_tensor(sc.goal, dtype=torch.float32, device=dev)
+    out = f.eq_project(xp, st, gl)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        f.eq_project(xp, st, gl, out=out)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    gin, _ = f.eq_project_backward(out, st, gl)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        f.eq_project_backward(out, st, gl)
+    b.record()
+    torch.cuda.synchronize()
+    ms_b = a.elapsed_time(b) / reps
+    rows = n_samples * 3 * spec.n_robots
+    gbs = rows * 88 / (ms * 1e-3) / 1e9
+    peak = float(measured_peaks().get("hbm_gbs", 6800.0))
+    return {"workload": f"3D N={spec.n_robots}, {n_samples} samples of decoder outputs ({rows} rows of 11)",
+            "ms": ms, "samples_per_s": n_samples / (ms * 1e-3), "backward_ms": ms_b,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "algorithmic_bytes_per_row": 88, "kernel": "eq_kernel"}}
+
+
 def batching_timing(P, dev):
     """The ragged batching workload: 64 scenes, N ~ U{8..32}, S ~ U{128..512},
     K=150, 3D. Aggregate: one captured graph (all robot-count groups, autotuned
@@ -521,6 +563,7 @@ def main():
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-workspace", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-qp", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

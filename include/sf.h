@@ -260,7 +260,8 @@ sf_status sf_project_train(sf_handle *h, void *stream, const sf_batch *batch, in
                            float *residual_out, float *fp_res2_out, void *checkpoints);
 
 /* Device workspace of sf_project_backward: the iterates of one checkpoint
- * segment, (checkpoint_every + 1) x 2 x total coefficients floats. */
+ * segment ((checkpoint_every + 1) x 2 x total coefficients floats), then the
+ * activity masks of that segment's iterations. */
 size_t sf_backward_workspace_bytes(const sf_handle *h, const sf_batch *batch, int K);
 
 /* Reverse mode through the K unrolled iterations of a previous
@@ -283,6 +284,29 @@ sf_status sf_project_backward(sf_handle *h, void *stream, const sf_batch *batch,
                               const float *grad_xi_out, const float *grad_lambda_out,
                               const float *grad_fp_res2, float *grad_xi0, float *grad_lambda0,
                               float *grad_xi_bar, void *workspace, size_t workspace_bytes);
+
+/* The generative decoders' differentiable QP layer (Sec. III-A / B: Eq.
+ * (sf_form) without the inequality constraints; the paper has no separate
+ * equation number). For every (sample, axis, robot) coefficient row of
+ * batch->xi_bar (here the decoder output xi'),
+ *   xi_out = argmin ||xi - xi'||^2  subject to  A1 xi = b,
+ * with A1 the boundary rows of Eq. (boundary_con) and b = (start position,
+ * start velocity, start acceleration, goal position, goal velocity, goal
+ * acceleration) of that robot and axis (velocities / accelerations 0 when
+ * start_va / goal_va are NULL). Closed form: xi_out = Pi xi' + R b with the
+ * float64-precomputed Pi = I - A1^T (A1 A1^T)^-1 A1 and R = A1^T (A1 A1^T)^-1.
+ * xi_out: device, same layout and size as xi_bar; must not alias it.
+ * Asynchronous on `stream`. Errors: SF_ERR_INVALID_ARG for a malformed batch
+ * or NULL output. */
+sf_status sf_eq_project(sf_handle *h, void *stream, const sf_batch *batch, float *xi_out);
+
+/* Adjoint of sf_eq_project: for dL/dxi_out = grad_out (device, xi_bar's
+ * layout), grad_in = dL/dxi' = Pi grad_out (Pi is symmetric) and, when
+ * grad_b is not NULL, grad_b[row][6] = dL/db = R^T grad_out per coefficient
+ * row (sample, axis, robot), in the order of b above. The batch's xi_bar is
+ * not read (it must still be a valid pointer). */
+sf_status sf_eq_project_backward(sf_handle *h, void *stream, const sf_batch *batch, const float *grad_out,
+                                 float *grad_in, float *grad_b);
 
 /* Synchronises `stream` and returns any device-side error latched by earlier
  * calls on the handle (SF_ERR_TIMEOUT, SF_ERR_NONFINITE), clearing it. */

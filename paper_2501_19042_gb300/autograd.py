@@ -42,3 +42,29 @@ def sf_unroll(sf, xi_bar, start, goal, K: int, xi0=None, lam0=None, n_robots=Non
     created with ``checkpoint_every > 0``. Returns (xi^K, lambda^K,
     fixed-point residual sum per sample, final ||r_p|| per sample)."""
     return _SFUnroll.apply(xi_bar, xi0, lam0, sf, start, goal, K, n_robots, n_samples)
+
+
+class _EqProject(torch.autograd.Function):
+    """The decoders' QP layer as a differentiable op: forward
+    ``sf_eq_project``, backward ``sf_eq_project_backward`` (dL/dxi' = Pi g).
+    The boundary values (start / goal) are conditioning inputs and get no
+    gradient here; ``SafetyFilter.eq_project_backward`` returns dL/db per row."""
+
+    @staticmethod
+    def forward(ctx, xi_prime, sf, start, goal, n_robots, n_samples):
+        out = sf.eq_project(xi_prime.detach().contiguous(), start, goal, n_robots=n_robots, n_samples=n_samples)
+        ctx.sf, ctx.nr, ctx.ns = sf, n_robots, n_samples
+        ctx.save_for_backward(start, goal)
+        return out
+
+    @staticmethod
+    def backward(ctx, g):
+        start, goal = ctx.saved_tensors
+        gin, _ = ctx.sf.eq_project_backward(g.contiguous().float(), start, goal, n_robots=ctx.nr, n_samples=ctx.ns)
+        return gin, None, None, None, None, None
+
+
+def eq_project(sf, xi_prime, start, goal, n_robots=None, n_samples=None):
+    """Differentiable projection of decoder outputs xi' onto the boundary
+    conditions (Sec. III-A / B); the layout is that of xi_bar."""
+    return _EqProject.apply(xi_prime, sf, start, goal, n_robots, n_samples)

@@ -27,6 +27,8 @@ struct sf_handle {
   bool use_tuned = true;
   cudaStream_t aux[2] = {nullptr, nullptr};        // extra streams for concurrent launch groups
   cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+  float eq_pi[sf::NV * sf::NV] = {};               // QP layer operators (host copy of slot 0)
+  float eq_r[sf::NV * 6] = {};
   std::string err;
 };
 
@@ -368,7 +370,16 @@ sf_status sf_create(const sf_problem* pb, int device, sf_handle** out) {
     sf_destroy(h);
     return e == cudaErrorInvalidValue ? SF_ERR_INVALID_ARG : SF_ERR_CUDA;
   }
-  e = prepare_kernels(pb->dim, (int)h->max_smem_optin, pb->precision);
+  {
+    // host copy of the QP layer's operators (slot 0), passed as kernel parameters
+    std::vector<float> slot(OPS_STRIDE);
+    e = cudaMemcpy(slot.data(), h->ops, sizeof(float) * OPS_STRIDE, cudaMemcpyDeviceToHost);
+    for (int r = 0; r < NV && e == cudaSuccess; ++r) {
+      for (int c = 0; c < NV; ++c) h->eq_pi[r * NV + c] = slot[OPS_S1 + r * NP + c];
+      for (int q = 0; q < 6; ++q) h->eq_r[r * 6 + q] = slot[OPS_R1 + r * 8 + q];
+    }
+  }
+  if (e == cudaSuccess) e = prepare_kernels(pb->dim, (int)h->max_smem_optin, pb->precision);
   for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
     e = cudaStreamCreateWithFlags(&h->aux[q], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join[q], cudaEventDisableTiming);
@@ -573,6 +584,73 @@ sf_status sf_project_backward(sf_handle* h, void* stream, const sf_batch* b, int
   rq.bwd.gxb = gxb;
   rq.bwd.xi0_is_xi_bar = init_from_xi_bar ? 1 : 0;
   return run_fused(h, reinterpret_cast<cudaStream_t>(stream), b, K, S, rq);
+}
+
+namespace {
+// Launches the QP layer over the batch's coefficient rows, at most
+// MAX_SCENES_PER_LAUNCH scenes per launch (rows of consecutive scenes are
+// contiguous, so each launch covers one contiguous row range).
+sf_status run_eq(sf_handle* h, cudaStream_t st, const sf_batch* b, const float* in, float* out, float* grad_b,
+                 bool backward) {
+  const int dim = h->pb.dim;
+  long long row = 0, roff = 0;
+  int q = 0;
+  while (q < b->n_scenes) {
+    EqArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.start = b->start;
+    a.goal = b->goal;
+    a.start_va = b->start_va;
+    a.goal_va = b->goal_va;
+    std::memcpy(a.Pi, h->eq_pi, sizeof(a.Pi));
+    std::memcpy(a.R, h->eq_r, sizeof(a.R));
+    a.dim = dim;
+    a.backward = backward ? 1 : 0;
+    const long long first_row = row;
+    int n = 0;
+    for (; q < b->n_scenes && n < MAX_SCENES_PER_LAUNCH; ++q, ++n) {
+      if ((long long)b->n_samples[q] * dim * b->n_robots[q] >= (1LL << 31))
+        return fail(h, SF_ERR_INVALID_ARG, "a scene has 2^31 or more coefficient rows");
+      a.sc[n].row_begin = row - first_row;
+      a.sc[n].N = b->n_robots[q];
+      a.sc[n].robot_off = (int)roff;
+      row += (long long)b->n_samples[q] * dim * b->n_robots[q];
+      roff += b->n_robots[q];
+    }
+    a.n_scenes = n;
+    a.rows = row - first_row;
+    a.in = in + first_row * NV;
+    a.out = out + first_row * NV;
+    a.grad_b = grad_b ? grad_b + first_row * 6 : nullptr;
+    const cudaError_t e = launch_eq(a, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "QP layer launch");
+    h->launches += a.rows > 0 ? 1 : 0;
+  }
+  return SF_OK;
+}
+}  // namespace
+
+sf_status sf_eq_project(sf_handle* h, void* stream, const sf_batch* b, float* xi_out) {
+  if (!h) return SF_ERR_INVALID_ARG;
+  long long R = 0, S = 0;
+  sf_status s0 = check_batch(h, b, &R, &S);
+  if (s0 != SF_OK) return s0;
+  if (S == 0) return SF_OK;
+  if (!xi_out) return fail(h, SF_ERR_INVALID_ARG, "xi_out is NULL");
+  DeviceGuard g(h->device);
+  return run_eq(h, reinterpret_cast<cudaStream_t>(stream), b, b->xi_bar, xi_out, nullptr, false);
+}
+
+sf_status sf_eq_project_backward(sf_handle* h, void* stream, const sf_batch* b, const float* grad_out,
+                                 float* grad_in, float* grad_b) {
+  if (!h) return SF_ERR_INVALID_ARG;
+  long long R = 0, S = 0;
+  sf_status s0 = check_batch(h, b, &R, &S);
+  if (s0 != SF_OK) return s0;
+  if (S == 0) return SF_OK;
+  if (!grad_out || !grad_in) return fail(h, SF_ERR_INVALID_ARG, "grad_out / grad_in is NULL");
+  DeviceGuard g(h->device);
+  return run_eq(h, reinterpret_cast<cudaStream_t>(stream), b, grad_out, grad_in, grad_b, true);
 }
 
 struct sf_graph {

@@ -249,6 +249,29 @@ struct PlainArgs {
   int* status;
 };
 size_t plain_workspace_floats(int dim, int N, int S, int T);
+
+// The decoders' QP layer (sf_eqqp.cu): per coefficient row, xi = Pi xi' + R b
+// (forward) or Pi g and R^T g (backward).
+struct EqScene {
+  long long row_begin;  // first coefficient row (sample, axis, robot) of the scene
+  int N;
+  int robot_off;
+};
+struct EqArgs {
+  const float* in;      // xi' (forward) or dL/dxi (backward), rows of 11
+  float* out;           // xi (forward) or dL/dxi' (backward)
+  float* grad_b;        // backward: dL/db [rows][6] or null
+  const float* start;
+  const float* goal;
+  const float* start_va;
+  const float* goal_va;
+  long long rows;
+  int dim, n_scenes, backward;
+  float Pi[NV * NV];    // Pi and R in the parameter space: the FMAs read them as
+  float R[NV * 6];      // constant operands (no load instruction per entry)
+  EqScene sc[MAX_SCENES_PER_LAUNCH];
+};
+cudaError_t launch_eq(const EqArgs& a, cudaStream_t st);
 cudaError_t launch_plain(const PlainArgs& a, const float* xi0, const float* lam0, cudaStream_t st);
 
 }  // namespace sf

@@ -14,6 +14,8 @@
 //     with I + rho G + rho N Q. Each is inverted by Gauss-Jordan with partial
 //     pivoting; from the inverse [[S, R], [R^T, *]] the xi step needs S, R
 //     and W = S rho H_k = S (M_k - I).
+//  4. The same inverse with M = I (the decoders' equality-only QP layer)
+//     into the operator slot of N = 0.
 #include "sf_internal.cuh"
 
 namespace sf {
@@ -151,6 +153,17 @@ __global__ void kkt_kernel(int T, double rho, int max_robots, double* s64, float
     A1[5 * NV + k] = Pdd[(T - 1) * NV + k];
   }
   double M[NV * NV], S0[NV * NV], R0[NV * 6], W0[NV * NV], S1[NV * NV], R1[NV * 6], W1[NV * NV];
+  if (N == 1) {
+    // slot 0: the decoders' QP layer, [[I, A1^T], [A1, 0]]^-1 -> Pi (S1 field), R (R1 field)
+    for (int r = 0; r < NV; ++r)
+      for (int c = 0; c < NV; ++c) M[r * NV + c] = (r == c ? 1.0 : 0.0);
+    if (!kkt_operators(M, A1, S0, R0, W0)) { atomicOr(fail, 1); return; }
+    float* o0 = ops32;
+    for (int r = 0; r < NV; ++r) {
+      for (int c = 0; c < NP; ++c) o0[OPS_S1 + r * NP + c] = c < NV ? (float)S0[r * NV + c] : 0.0f;
+      for (int q = 0; q < 8; ++q) o0[OPS_R1 + r * 8 + q] = q < 6 ? (float)R0[r * 6 + q] : 0.0f;
+    }
+  }
   for (int r = 0; r < NV; ++r)
     for (int c = 0; c < NV; ++c) M[r * NV + c] = (r == c ? 1.0 : 0.0) + rho * G[r * NV + c];
   bool ok = kkt_operators(M, A1, S0, R0, W0);

@@ -244,6 +244,34 @@ class SafetyFilter:
         nat.check(self._lib, self._h, code)
         return gx0, gl0, gxb
 
+    def eq_project(self, xi_prime, start, goal, n_robots=None, n_samples=None, start_va=None, goal_va=None,
+                   stream=None, out=None):
+        """``sf_eq_project``: the decoders' QP layer, the projection of xi'
+        onto the boundary conditions of every robot (layout of xi_bar)."""
+        b, keep, ncoef, nsamp = self._batch(xi_prime, start, goal, n_robots, n_samples, start_va, goal_va)
+        if out is None:
+            out = torch.empty_like(xi_prime)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        code = self._lib.sf_eq_project(self._h, C.c_void_p(stream.cuda_stream), C.byref(b), _ptr(out))
+        del keep
+        nat.check(self._lib, self._h, code)
+        return out
+
+    def eq_project_backward(self, grad_out, start, goal, n_robots=None, n_samples=None, start_va=None,
+                            goal_va=None, want_grad_b=False, stream=None):
+        """``sf_eq_project_backward``: (dL/dxi', dL/db per coefficient row or None)."""
+        b, keep, ncoef, nsamp = self._batch(grad_out, start, goal, n_robots, n_samples, start_va, goal_va)
+        gin = torch.empty_like(grad_out)
+        gb = torch.empty((ncoef // self.nvar, 6), dtype=torch.float32, device=self.device) if want_grad_b else None
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        code = self._lib.sf_eq_project_backward(self._h, C.c_void_p(stream.cuda_stream), C.byref(b),
+                                                _ptr(grad_out), _ptr(gin), _ptr(gb))
+        del keep
+        nat.check(self._lib, self._h, code)
+        return gin, gb
+
     def autotune(self, xi_bar, start, goal, K_probe=10, n_candidates=8, n_robots=None, n_samples=None,
                  start_va=None, goal_va=None, stream=None):
         """``sf_autotune``: times the cost model's best launch shapes for this
