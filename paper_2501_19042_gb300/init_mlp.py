@@ -50,6 +50,53 @@ class InitMLP(nn.Module):
         return xi0.contiguous(), lam0.contiguous()
 
 
+class InitPointNet(nn.Module):
+    """The paper's initialisation network (Sec. IV, "Initialization Network
+    Details"): a PointNet-like CNN over the agents, whose 18 input channels
+    are the start and goal position, velocity and acceleration of an agent in
+    3D, max-pooled over the agents into a feature vector c; c concatenated
+    with the sample xi_bar goes through a 4-layer MLP (linear, batch
+    normalisation, LeakyReLU). Same residual output as ``InitMLP`` (zero last
+    layer: untrained, it is the sample initialisation). Velocities and
+    accelerations at the boundary are zero in these workloads."""
+
+    def __init__(self, n_robots: int, dim: int = 3, nvar: int = 11, width: int = 512, feat: int = 256,
+                 scale: float = 4.0):
+        super().__init__()
+        self.N, self.dim, self.nvar, self.scale = n_robots, dim, nvar, scale
+        self.n = dim * n_robots * nvar
+        ch = 6 * dim
+        self.point = nn.Sequential(nn.Conv1d(ch, 64, 1), nn.BatchNorm1d(64), nn.ReLU(),
+                                   nn.Conv1d(64, 128, 1), nn.BatchNorm1d(128), nn.ReLU(),
+                                   nn.Conv1d(128, feat, 1))
+        self.mlp = nn.Sequential(nn.Linear(feat + self.n, width), nn.BatchNorm1d(width), nn.LeakyReLU(0.1),
+                                 nn.Linear(width, width), nn.BatchNorm1d(width), nn.LeakyReLU(0.1),
+                                 nn.Linear(width, width), nn.BatchNorm1d(width), nn.LeakyReLU(0.1),
+                                 nn.Linear(width, 2 * self.n))
+        nn.init.zeros_(self.mlp[-1].weight)
+        nn.init.zeros_(self.mlp[-1].bias)
+
+    def forward(self, start_s, goal_s, xi_bar):
+        """start_s, goal_s: [S, N, dim]; xi_bar: [S, dim, N, nvar]."""
+        S = xi_bar.shape[0]
+        z = torch.zeros_like(start_s)
+        states = torch.cat([start_s, z, z, goal_s, z, z], 2) / self.scale      # [S, N, 6 dim]
+        c = self.point(states.transpose(1, 2)).amax(2)                         # [S, feat]
+        y = self.mlp(torch.cat([c, xi_bar.reshape(S, -1) / self.scale], 1)) * self.scale
+        xi0 = xi_bar + y[:, : self.n].reshape(xi_bar.shape)
+        lam0 = y[:, self.n:].reshape(xi_bar.shape)
+        return xi0.contiguous(), lam0.contiguous()
+
+
+def make_init_net(arch: str, n_robots: int, dim: int = 3):
+    """``mlp``: the 3-layer MLP; ``pointnet``: the paper's network."""
+    if arch == "mlp":
+        return InitMLP(n_robots, dim)
+    if arch == "pointnet":
+        return InitPointNet(n_robots, dim)
+    raise ValueError(f"unknown init network {arch!r}")
+
+
 @dataclass
 class SceneBatch:
     xi_bar: torch.Tensor     # [S_total, dim, N, nvar]
@@ -121,7 +168,10 @@ def evaluate(sf, mlp, spec: si.SceneSpec, K: int, seed: int = 5, n_scenes: int =
     r_sample = sf.project(b.xi_bar, b.start, b.goal, K, **kw).residual
     r_zero = sf.project(b.xi_bar, b.start, b.goal, K, xi0=torch.zeros_like(b.xi_bar),
                         lam0=torch.zeros_like(b.xi_bar), **kw).residual
+    was = mlp.training
+    mlp.eval()
     xi0, lam0 = mlp(b.start_s, b.goal_s, b.xi_bar)
+    mlp.train(was)
     r_learn = sf.project(b.xi_bar, b.start, b.goal, K, xi0=xi0, lam0=lam0, **kw).residual
     r_fb = torch.minimum(r_learn, r_sample)
     q = lambda r: {"median": float(r.median()), "p90": float(r.quantile(0.9)), "mean": float(r.mean())}
@@ -131,12 +181,39 @@ def evaluate(sf, mlp, spec: si.SceneSpec, K: int, seed: int = 5, n_scenes: int =
 
 
 @torch.no_grad()
+def residual_curves(sf, nets: dict, spec: si.SceneSpec, K: int, seed: int = 5, n_scenes: int = 64,
+                    at=(1, 2, 5, 10, 20, 50, 100, 200)):
+    """Median projection residual ||F xi^k - e^{k+1}|| across held-out samples
+    at iterations `at` (the per-iteration history of sf_project) for the zero
+    and sample initialisations and each trained network in `nets` (name ->
+    module, evaluated in eval mode), as in the paper's residual figure."""
+    b = make_batch(spec, seed * 1_000_003, n_scenes, sf.device)
+    kw = dict(n_robots=b.n_robots, n_samples=b.n_samples, hist=True)
+    inits = {"zero": (torch.zeros_like(b.xi_bar), torch.zeros_like(b.xi_bar)), "sample": (None, None)}
+    for name, net in nets.items():
+        was = net.training
+        net.eval()
+        inits[name] = net(b.start_s, b.goal_s, b.xi_bar)
+        net.train(was)
+    out = {}
+    for name, (x0, l0) in inits.items():
+        r = sf.project(b.xi_bar, b.start, b.goal, K, xi0=x0, lam0=l0, **kw)
+        med = r.hist.median(dim=1).values.cpu()
+        out[name] = {str(k): float(med[k - 1]) for k in at if k <= K}
+        out[name]["final_rp_median"] = float(r.residual.median())
+    return out
+
+
+@torch.no_grad()
 def project_with_fallback(sf, mlp, xi_bar, start, goal, start_s, goal_s, K, n_robots=None, n_samples=None):
     """Runs the SF from the learned and from the sample initialisation and
     keeps, per sample, the result with the smaller final primal residual."""
     kw = dict(n_robots=n_robots, n_samples=n_samples)
     a = sf.project(xi_bar, start, goal, K, **kw)
+    was = mlp.training
+    mlp.eval()
     xi0, lam0 = mlp(start_s, goal_s, xi_bar)
+    mlp.train(was)
     b = sf.project(xi_bar, start, goal, K, xi0=xi0, lam0=lam0, **kw)
     pick = (b.residual < a.residual)
     shape = (-1,) + (1,) * (xi_bar.dim() - 1)
@@ -160,22 +237,32 @@ def main():
     ap.add_argument("--fp-weight", type=float, default=1.0)
     ap.add_argument("--rho", type=float, default=0.1)
     ap.add_argument("--eval-scenes", type=int, default=64)
+    ap.add_argument("--arch", default="mlp", choices=["mlp", "pointnet", "both"])
+    ap.add_argument("--curves-K", type=int, default=0,
+                    help="after training, median residual vs iteration over K iterations for every init")
     args = ap.parse_args()
     spec = si.config_diff(n_samples=args.samples_per_scene, K=args.K)
     sf = SafetyFilter(dim=3, T=spec.T, rho=args.rho, coll_a=spec.coll, v_max=spec.v_max, a_max=spec.a_max,
                       max_robots=spec.n_robots, checkpoint_every=10)
-    torch.manual_seed(0)
-    mlp = InitMLP(spec.n_robots).to(sf.device)
-    before = evaluate(sf, mlp, spec, args.K, n_scenes=args.eval_scenes)
-    t0 = time.perf_counter()
-    hist = train(sf, mlp, spec, K=args.K, n_train_scenes=args.scenes, scenes_per_step=args.scenes_per_step,
-                 epochs=args.epochs, lr=args.lr, fp_weight=args.fp_weight)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    after = evaluate(sf, mlp, spec, args.K, n_scenes=args.eval_scenes)
-    print(json.dumps({"train_scenes": args.scenes, "epochs": args.epochs, "steps": len(hist),
-                      "train_seconds": dt, "loss_first": hist[0], "loss_last": hist[-1],
-                      "heldout_before": before, "heldout_after": after}))
+    result, nets = {}, {}
+    for arch in (["mlp", "pointnet"] if args.arch == "both" else [args.arch]):
+        torch.manual_seed(0)
+        net = make_init_net(arch, spec.n_robots).to(sf.device)
+        before = evaluate(sf, net, spec, args.K, n_scenes=args.eval_scenes)
+        t0 = time.perf_counter()
+        hist = train(sf, net, spec, K=args.K, n_train_scenes=args.scenes, scenes_per_step=args.scenes_per_step,
+                     epochs=args.epochs, lr=args.lr, fp_weight=args.fp_weight)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        after = evaluate(sf, net, spec, args.K, n_scenes=args.eval_scenes)
+        result[arch] = {"train_scenes": args.scenes, "epochs": args.epochs, "steps": len(hist),
+                        "train_seconds": dt, "loss_first": hist[0], "loss_last": hist[-1],
+                        "heldout_before": before, "heldout_after": after}
+        nets[arch] = net
+    if args.curves_K > 0:
+        cspec = si.config_diff(n_samples=args.samples_per_scene, K=args.curves_K)
+        result["residual_curves"] = residual_curves(sf, nets, cspec, args.curves_K, n_scenes=args.eval_scenes)
+    print(json.dumps(result))
 
 
 if __name__ == "__main__":

@@ -47,3 +47,28 @@ def test_training_reduces_the_loss_and_fallback_never_worse(setup):
                                                  n_robots=b.n_robots, n_samples=b.n_samples)
     plain = sf.project(b.xi_bar, b.start, b.goal, 20, n_robots=b.n_robots, n_samples=b.n_samples)
     assert torch.all(res <= plain.residual)
+
+
+def test_paper_init_network_and_residual_curves(setup):
+    """The paper's PointNet-like initialisation network: untrained (eval mode)
+    it is the sample initialisation; a few training steps through the
+    differentiable SF lower the loss; the residual curves of zero, sample and
+    learned initialisation come from the per-iteration history and the
+    zero / sample curves equal direct sf_project histories."""
+    P, M, spec, sf = setup
+    torch.manual_seed(0)
+    net = M.make_init_net("pointnet", 16).cuda()
+    b = M.make_batch(spec, 321, 4, sf.device)
+    net.eval()
+    xi0, lam0 = net(b.start_s, b.goal_s, b.xi_bar)
+    assert torch.equal(xi0, b.xi_bar) and torch.count_nonzero(lam0) == 0
+    net.train()
+    hist = M.train(sf, net, spec, K=20, n_train_scenes=30 * 16, scenes_per_step=16, lr=1e-3, max_steps=30)
+    assert np.mean(hist[-5:]) < np.mean(hist[:5])
+    cur = M.residual_curves(sf, {"pointnet": net}, spec, 20, n_scenes=4, at=(1, 5, 20))
+    assert set(cur) == {"zero", "sample", "pointnet"}
+    bb = M.make_batch(spec, 5 * 1_000_003, 4, sf.device)
+    r = sf.project(bb.xi_bar, bb.start, bb.goal, 20, n_robots=bb.n_robots, n_samples=bb.n_samples, hist=True)
+    assert cur["sample"]["20"] == float(r.hist.median(dim=1).values[19])
+    for name in cur:
+        assert 0 < cur[name]["20"] < cur[name]["1"]
