@@ -249,3 +249,26 @@ def test_ragged_64_scenes_full_size_sampled(sfmod, oracle_lib):
         assert rel_l2(got, ref["xi"]).max() <= TOL_XI_REL, (q, N)
         assert abs(res[offs_s[q] + smp] - ref["rp_final"][0]) <= TOL_RESID_ABS
     g.close()
+
+
+@pytest.mark.parametrize("form,prec", [("fused", "fp32"), ("plain", "fp32"), ("fused", "bf16")])
+def test_nonfinite_input_is_reported_and_contained(sfmod, form, prec):
+    """A NaN in one sample's coefficients: sf_sync_status reports
+    SF_ERR_NONFINITE (and clears the word), every other sample's output is
+    bit-identical to a run without the bad sample's NaN, and the next clean
+    call reports no error."""
+    P = sfmod
+    sc = si.scene(si.config_n16_3d(n_samples=20), 1)
+    f = P.SafetyFilter(dim=3, T=100, rho=RHO_3D, coll_a=sc.spec.coll, max_robots=16, precision=prec)
+    clean = f.project(_dev(sc.xi_bar), _dev(sc.start), _dev(sc.goal), 15, form=form)
+    f.sync_status()
+    bad = sc.xi_bar.copy()
+    bad[7, 1, 3, 5] = np.nan
+    out = f.project(_dev(bad), _dev(sc.start), _dev(sc.goal), 15, form=form)
+    with pytest.raises(RuntimeError, match="NONFINITE"):
+        f.sync_status()
+    keep = [s for s in range(20) if s != 7]
+    assert torch.equal(out.xi[keep], clean.xi[keep]) and torch.equal(out.residual[keep], clean.residual[keep])
+    assert not torch.isfinite(out.residual[7])
+    f.project(_dev(sc.xi_bar), _dev(sc.start), _dev(sc.goal), 15, form=form)
+    f.sync_status()
