@@ -186,6 +186,23 @@ unsigned long long sf_launch_count(const sf_handle *h);
  * 16-bit mode) makes them fail with SF_ERR_UNSUPPORTED. */
 sf_status sf_set_launch_shape(sf_handle *h, int samples_per_cta, int warps, int time_chunk);
 
+/* Options of a handle (sf_set_option). */
+typedef enum {
+  /* 1 (default): between full pair tests, the float32 fused forward tests
+   * only the pair rows that were within scaled distance 1.5 at the last full
+   * test of the sample; a full test is rerun as soon as the sample's
+   * coefficients may have moved its positions by 0.25 (scaled) or more, in a
+   * bound that holds for every t (Bernstein weights are non-negative and sum
+   * to 1). The result is the same as testing every pair. 0: every pair every
+   * iteration. Off while use_workspace is set; no effect in the 16-bit modes,
+   * the plain form and the backward's recompute. */
+  SF_OPT_PAIR_PRUNING = 1
+} sf_option;
+
+/* Sets option `option` of the handle to `value` (for later calls).
+ * SF_ERR_INVALID_ARG for an unknown option or value. */
+sf_status sf_set_option(sf_handle *h, int option, int value);
+
 /* Shape of the last fused launch of the handle: out[0..3] = G, warps, tc and
  * the number of time ranges of the contraction phase. */
 sf_status sf_get_launch_shape(const sf_handle *h, int *out4);

@@ -25,6 +25,7 @@ struct sf_handle {
   int last_plan[4] = {0, 0, 0, 0};                 // G, warps, tc, nq of the last fused launch
   std::map<std::string, sf::FusedPlan> tuned;      // autotuned shapes per launch-group key
   bool use_tuned = true;
+  int prune = 1;                                   // SF_OPT_PAIR_PRUNING
   cudaStream_t aux[2] = {nullptr, nullptr};        // extra streams for concurrent launch groups
   cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
   float eq_pi[sf::NV * sf::NV] = {};               // QP layer operators (host copy of slot 0)
@@ -228,6 +229,7 @@ sf_status build_groups(sf_handle* h, const sf_batch* b, int K, long long S, cons
       a.ck_every = std::max(1, h->pb.checkpoint_every);
       a.total_coefs = tot;
       a.fp_res2 = rq.fp_res2;
+      a.prune = (h->prune && !h->pb.use_workspace) ? 1 : 0;
       if (rq.ckpt && !rq.backward) {
         const long long ck = a.ck_every, nck = (K + ck - 1) / ck;
         a.amask = reinterpret_cast<unsigned*>(rq.ckpt + states_floats_aligned(nck + ck + 1, tot));
@@ -959,6 +961,16 @@ sf_status sf_project_plain_noalloc(sf_handle* h, void* stream, const sf_batch* b
   if (s != SF_OK) return s;
   return sf_project(h, stream, b, K, SF_FORM_PLAIN, xi0, lam0, xi_out, lam_out, resid_out, resid_hist, scratch,
                     (size_t)SF_NOALLOC_SCRATCH_BYTES, nullptr);
+}
+
+sf_status sf_set_option(sf_handle* h, int option, int value) {
+  if (!h) return SF_ERR_INVALID_ARG;
+  if (option == SF_OPT_PAIR_PRUNING) {
+    if (value != 0 && value != 1) return fail(h, SF_ERR_INVALID_ARG, "SF_OPT_PAIR_PRUNING takes 0 or 1");
+    h->prune = value;
+    return SF_OK;
+  }
+  return fail(h, SF_ERR_INVALID_ARG, "unknown option");
 }
 
 sf_status sf_sync_status(sf_handle* h, void* stream) {

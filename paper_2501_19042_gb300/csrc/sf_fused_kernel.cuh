@@ -33,6 +33,18 @@ namespace fused_impl {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// Pair pruning (float32 forward). A full pair test of a sample records as
+// candidates the pair rows with scaled distance < 1 + kPruneMargin; while the
+// sample's coefficients stay within kPruneMargin / 2 (minus a rounding slack)
+// of the coefficients of that test, in the bound below, only candidates are
+// tested. Bound: with Bernstein weights P[t][k] >= 0 summing to 1,
+// |M^-1 (p_i(t) - p_i^ref(t))| <= max_k |M^-1 (c_ik - c_ik^ref)|
+// <= sqrt(dim) max_{k,x} |c_ikx - c_ikx^ref| / a_x, so a pair that was not a
+// candidate is still at scaled distance > 1 and inactive.
+constexpr float kPruneMargin = 0.5f;
+constexpr float kPruneCandS2 = (1.0f + kPruneMargin) * (1.0f + kPruneMargin);
+constexpr float kPruneDriftLimit = 0.5f * kPruneMargin - 1e-3f;
+
 // Shared-memory layout (floats). Head, float32 form: basis [T][36],
 // operators, beta. Head, tensor-core form: the basis as 16-bit operand
 // tables BN [T][3][4][4] words (rows of P, Pd, Pdd by time step: per lane
@@ -48,12 +60,16 @@ constexpr unsigned FULL = 0xffffffffu;
 // residual per t); RSB [NQ][NMAX] (ball residual partials); tensor-core form
 // only: CF [16 MT][4][4] words, the coefficient rows r = x * NMAX + i as MMA
 // A fragments (per lane quad t4: k pairs (2 t4, 2 t4 + 8) rounded to 16 bits,
-// then their rounding remainders), refreshed by every xi step.
+// then their rounding remainders), refreshed by every xi step; float32 form
+// with pair pruning only: CR [NMAX][DIM][12] (coefficients at the last full
+// pair test), CM [T][CMW] (candidate pair rows of that test), RF (drift of
+// the coefficients since then, as the bit pattern of a non-negative float).
 struct Lay {
   int RS, EP, TC, NQ, T, nmax, dim;
-  int C, LAM, XIB, PG, MC, MR, EB, RS2, RSB, FPP, FPR, XB, LB, GXB, U, CW, CF, SB;
+  int C, LAM, XIB, PG, MC, MR, EB, RS2, RSB, FPP, FPR, XB, LB, GXB, U, CW, CF, CR, CM, RF, CMW, SB;
   int head, TH, bno, bto, opso, betao;
-  __host__ __device__ Lay(int dim_, int nmax_, int T_, int TC_, int NQ_, bool bwd = false, bool tcm = false) {
+  __host__ __device__ Lay(int dim_, int nmax_, int T_, int TC_, int NQ_, bool bwd = false, bool tcm = false,
+                          bool cand = false) {
     dim = dim_; nmax = nmax_; T = T_; TC = TC_; NQ = NQ_;
     RS = dim * NP;
     EP = nmax * dim + (tcm ? 4 : 1);
@@ -76,7 +92,13 @@ struct Lay {
     U = GXB + (bwd ? nmax * RS : 0);
     CW = U + (bwd ? nmax * RS : 0);
     CF = CW + (bwd ? nmax * RS : 0);
-    SB = CF + (tcm ? ((dim * nmax + 15) / 16) * 256 : 0);
+    // pair pruning (float32 forward): reference coefficients, candidate
+    // pair masks per (t) of mask_pair_words rounded to 4 words, drift word
+    CMW = cand ? (mask_pair_words(nmax) + 3) / 4 * 4 : 0;
+    CR = CF + (tcm ? ((dim * nmax + 15) / 16) * 256 : 0);
+    CM = CR + (cand ? nmax * RS : 0);
+    RF = CM + T * CMW;
+    SB = RF + (cand ? 4 : 0);
     TH = (T + 1) / 2;
     bno = 0;
     if (tcm) {
@@ -258,12 +280,18 @@ __device__ __forceinline__ void ws_row(const float (&ps)[DIM], float (&Ei)[DIM],
 // element NMAX*DIM is set to 1 when some pair of the row is active. With
 // MASKS the lane's activity-mask row (mk + (s T + t) mask_words) is cleared
 // and the bit of every active pair row is set.
-template <int DIM, int NMAX, bool TCM = false, bool MASKS = false>
+// With CAND (float32 form, prune on) a sample whose drift word allows it
+// runs the candidate path: only the recorded candidate rows are tested, the
+// robots' positions computed on demand and E accumulated in the row; a
+// sample due for a full test records its candidates (and, in the first
+// chunk, copies C to the reference coefficients).
+template <int DIM, int NMAX, bool TCM = false, bool MASKS = false, bool CAND = false>
 __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G, int N, int t0, int TCc,
                            const ProblemConsts& pc, bool want_res, int warp, int nwarps, int lane,
-                           unsigned* mk = nullptr) {
+                           unsigned* mk = nullptr, bool prune = false) {
   constexpr int MW = mask_words(NMAX);
   constexpr int RS = DIM * NP;
+  constexpr int PW = mask_pair_words(NMAX);
   const int nA = G * TCc;
   for (int base = warp * 32; base < nA; base += nwarps * 32) {
     const int u = base + lane;
@@ -294,7 +322,75 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
         atomicOr(mrow + (b >> 5), 1u << (b & 31));
       }
     };
-    if (NMAX <= 16) {
+    // pair pruning: full test (and record candidates) or candidates only
+    bool refresh = true;
+    unsigned* cmrow = nullptr;
+    if (CAND) {
+      const float drift = __int_as_float(*reinterpret_cast<const int*>(blk + L.RF));
+      refresh = !prune || !(sqrtf((float)DIM) * drift < kPruneDriftLimit);   // NaN: full test
+      cmrow = reinterpret_cast<unsigned*>(blk + L.CM) + (size_t)t * L.CMW;
+    }
+    const bool rec = CAND && refresh && valid;
+    auto cand = [&](int i, int j, float s2) {
+      if (CAND && rec && s2 < kPruneCandS2) {
+        const int b = pair_bit(NMAX, i, j);
+        cmrow[b >> 5] |= 1u << (b & 31);
+      }
+    };
+    if (rec) {
+      for (int q = 0; q < L.CMW / 4; ++q) reinterpret_cast<uint4*>(cmrow)[q] = make_uint4(0u, 0u, 0u, 0u);
+      if (t0 == 0)
+        for (int v = tl; v < NMAX * RS; v += TCc) blk[L.CR + v] = Cs[v];
+    }
+    bool e_in_row = false;
+    if (CAND && !__any_sync(FULL, refresh)) {
+      // candidate path: no warp-wide votes below, lanes run their own lists
+      e_in_row = true;
+      if (valid) {
+        for (int q = 0; q < N * DIM; ++q) ebw[q] = 0.0f;
+        unsigned w[(PW + 3) / 4 * 4];
+        const uint4* c4 = reinterpret_cast<const uint4*>(cmrow);
+#pragma unroll
+        for (int q = 0; q < (PW + 3) / 4; ++q) {
+          const uint4 v = c4[q];
+          w[4 * q] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w;
+        }
+#pragma unroll
+        for (int q = 0; q < PW; ++q) {
+          unsigned m = w[q];
+          while (m) {
+            int idx = q * 32 + __ffs(m) - 1;
+            m &= m - 1;
+            int i = 0;
+            while (idx >= NMAX - 1 - i) {   // row-major upper triangle
+              idx -= NMAX - 1 - i;
+              ++i;
+            }
+            const int j = i + 1 + idx;
+            float pi[DIM], pj[DIM];
+            state<DIM>(Pr, Cs + i * RS, pi);
+            state<DIM>(Pr, Cs + j * RS, pj);
+#pragma unroll
+            for (int x = 0; x < DIM; ++x) {
+              pi[x] *= (x == 2 ? pc.inv_b : pc.inv_a);
+              pj[x] *= (x == 2 ? pc.inv_b : pc.inv_a);
+            }
+            if (scaled_d2<DIM>(pi, pj) < 1.0f) {
+              float Ei[DIM], Ej[DIM];
+#pragma unroll
+              for (int x = 0; x < DIM; ++x) Ei[x] = Ej[x] = 0.0f;
+              mark(i, j, true);
+              pair_apply_scaled<DIM>(pi, pj, Ei, Ej, pc, res2);
+#pragma unroll
+              for (int x = 0; x < DIM; ++x) {
+                ebw[i * DIM + x] += Ei[x];
+                ebw[j * DIM + x] += Ej[x];
+              }
+            }
+          }
+        }
+      }
+    } else if (NMAX <= 16) {
       // scaled positions of all robots in registers; lanes past the chunk get
       // far-apart dummies so that none of their rows tests active
       float p[NMAX][DIM];
@@ -335,7 +431,11 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
           bool row = false;
 #pragma unroll
           for (int j = 0; j < NMAX; ++j)
-            if (j > i && j < N) row |= scaled_d2<DIM>(p[i], p[j]) < 1.0f;
+            if (j > i && j < N) {
+              const float s2 = scaled_d2<DIM>(p[i], p[j]);
+              row |= s2 < 1.0f;
+              cand(i, j, s2);
+            }
           if (__any_sync(FULL, row)) {
 #pragma unroll
             for (int j = 0; j < NMAX; ++j)
@@ -401,7 +501,11 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
           for (int a = 0; a < 8; ++a)
 #pragma unroll
             for (int b = 0; b < 8; ++b)
-              if (b > a && I0 + b < N) blkrow |= scaled_d2<DIM>(pI[a], pI[b]) < 1.0f;
+              if (b > a && I0 + b < N) {
+                const float s2 = scaled_d2<DIM>(pI[a], pI[b]);
+                blkrow |= s2 < 1.0f;
+                cand(I0 + a, I0 + b, s2);
+              }
           if (__any_sync(FULL, blkrow)) {
 #pragma unroll
             for (int a = 0; a < 8; ++a)
@@ -424,7 +528,11 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
               if (!valid) pj[0] = 4096.0f * (float)j;
               bool grp = false;
 #pragma unroll
-              for (int a = 0; a < 8; ++a) grp |= scaled_d2<DIM>(pI[a], pj) < 1.0f;
+              for (int a = 0; a < 8; ++a) {
+                const float s2 = scaled_d2<DIM>(pI[a], pj);
+                grp |= s2 < 1.0f;
+                cand(I0 + a, j, s2);
+              }
               if (__any_sync(FULL, grp)) {
 #pragma unroll
                 for (int a = 0; a < 8; ++a) {
@@ -464,7 +572,9 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
     }
     if (valid) {
       float* eb = blk + L.EB + tl * L.EP;
-      if (TCM) {
+      if (e_in_row) {
+        // candidate path: E is already in the row
+      } else if (TCM) {
         // whole row in 16-byte stores (E of robots >= N is zero); the row
         // stride is a multiple of 4 floats, scalar stores would conflict
         float Ef[NMAX * DIM];
@@ -1020,8 +1130,9 @@ struct Cta {
   float *BASIS, *OPS, *BETA, *SAMP;
   uint32_t *BN, *BT;
   int tid, nthr, warp, lane, nwarps;
-  __device__ Cta(const SceneDesc* sc, int n_scenes, int T, int tc, int nq, bool bwd, float* sm, bool tcm = false)
-      : L(DIM, NMAX, T, tc, nq, bwd, tcm) {
+  __device__ Cta(const SceneDesc* sc, int n_scenes, int T, int tc, int nq, bool bwd, float* sm, bool tcm = false,
+                 bool cand = false)
+      : L(DIM, NMAX, T, tc, nq, bwd, tcm, cand) {
     int sidx = 0;
     for (int q = 1; q < n_scenes; ++q) {
       if (sc[q].cta_begin <= (int)blockIdx.x) sidx = q;
@@ -1176,9 +1287,10 @@ __device__ void store_state(const Cta<DIM, NMAX>& c, float* xi_dst, float* lam_d
 // One iteration of f_FP on every sample of the CTA (time chunks, then the
 // lambda step and the xi step). keep_prev stores xi^k in the EB region for
 // the final residual. fp (when set) adds ||z^{k+1} - z^k||^2 per sample to FPR.
-template <int DIM, int NMAX, int PREC = 0, bool MASKS = false>
+template <int DIM, int NMAX, int PREC = 0, bool MASKS = false, bool CAND = false>
 __device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, const float* xi_bar, int it,
-                              bool keep_prev, float* hist, int total_samples, bool fp, unsigned* mslot = nullptr) {
+                              bool keep_prev, float* hist, int total_samples, bool fp, unsigned* mslot = nullptr,
+                              bool prune = false) {
   constexpr int RS = DIM * NP;
   const Lay& L = c.L;
   const int T = pc.T, N = c.N, G = c.G, TC = L.TC;
@@ -1196,13 +1308,14 @@ __device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, 
                                          c.nwarps, c.lane);
     } else if (MASKS && mslot != nullptr) {
       unsigned* mk = mslot + c.mask0;
-      pair_phase<DIM, NMAX, false, true>(c.SAMP, L, c.BASIS, G, N, t0, TCc, pc, want_res, c.warp, c.nwarps,
-                                         c.lane, mk);
+      pair_phase<DIM, NMAX, false, true, CAND>(c.SAMP, L, c.BASIS, G, N, t0, TCc, pc, want_res, c.warp, c.nwarps,
+                                               c.lane, mk, prune);
       __syncthreads();
       contract_phase<DIM, NMAX, true>(c.SAMP, L, c.BASIS, G, N, t0, TCc, t0 == 0, pc, want_res, c.tid, c.nthr,
                                       mk);
     } else {
-      pair_phase<DIM, NMAX>(c.SAMP, L, c.BASIS, G, N, t0, TCc, pc, want_res, c.warp, c.nwarps, c.lane);
+      pair_phase<DIM, NMAX, false, false, CAND>(c.SAMP, L, c.BASIS, G, N, t0, TCc, pc, want_res, c.warp,
+                                                c.nwarps, c.lane, nullptr, prune);
       __syncthreads();
       contract_phase<DIM>(c.SAMP, L, c.BASIS, G, N, t0, TCc, t0 == 0, pc, want_res, c.tid, c.nthr);
     }
@@ -1227,6 +1340,7 @@ __device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, 
     }
     blk[L.MR + x * NP + k] = sr * invN;
     blk[L.MC + x * NP + k] = sc * invN;
+    if (CAND && x == 0 && k == 0) *reinterpret_cast<int*>(blk + L.RF) = 0;   // drift since the reference
     if (fp) blk[L.FPP + x * NV + k] = dl2;
     if (want_res && x == 0 && k == 0) {
       float r2 = 0.0f;
@@ -1277,6 +1391,19 @@ __device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, 
     }
     out[NV] = 0.0f;
     if constexpr (PREC != 0) cf_write_row<PREC>(blk + L.CF, x * NMAX + i, out);
+    if constexpr (CAND) {
+      // drift of this coefficient row from the reference, in scaled units
+      const float inv = x == 2 ? pc.inv_b : pc.inv_a;
+      float d = 0.0f;
+      bool bad = false;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        const float e = fabsf(out[k] - blk[L.CR + o + k]) * inv;
+        d = fmaxf(d, e);
+        bad |= !(e == e);
+      }
+      atomicMax(reinterpret_cast<int*>(blk + L.RF), __float_as_int(bad ? INFINITY : d));
+    }
     float4* o4 = reinterpret_cast<float4*>(blk + L.C + o);
     float4* p4 = reinterpret_cast<float4*>(blk + L.EB + o);
 #pragma unroll
@@ -1316,7 +1443,8 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
   float* sm = reinterpret_cast<float*>(smem4);
   const ProblemConsts& pc = A.pc;
   const int T = pc.T;
-  const Cta<DIM, NMAX> c(A.sc, A.n_scenes, T, A.tc, A.nq, false, sm, PREC != 0);
+  constexpr bool CAND = PREC == 0;   // pair pruning in the float32 form
+  const Cta<DIM, NMAX> c(A.sc, A.n_scenes, T, A.tc, A.nq, false, sm, PREC != 0, CAND);
   if (c.G <= 0) return;
   const Lay& L = c.L;
   const int N = c.N, G = c.G;
@@ -1324,7 +1452,10 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
 
   prologue<DIM, NMAX, PREC>(c, T, A.basis, A.ops, A.start, A.goal, A.start_va, A.goal_va);
   load_state<DIM, NMAX>(c, A.xi0, A.lam0, A.xi_bar, A.xi_bar);
-  for (int s = c.tid; s < G; s += c.nthr) c.blk(s)[L.FPR] = 0.0f;
+  for (int s = c.tid; s < G; s += c.nthr) {
+    c.blk(s)[L.FPR] = 0.0f;
+    if (CAND) *reinterpret_cast<int*>(c.blk(s) + L.RF) = __float_as_int(INFINITY);   // first test is full
+  }
   __syncthreads();
   if constexpr (PREC != 0) {
     cf_prepare<DIM, NMAX, PREC>(c.SAMP, L, G, N, c.tid, c.nthr);
@@ -1341,7 +1472,8 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
     if (A.ckpt && it % A.ck_every == 0) write_checkpoint<DIM, NMAX>(c, A.ckpt, it / A.ck_every, A.total_coefs);
     if (tail && it >= last_ck) write_checkpoint<DIM, NMAX>(c, tail, it - last_ck, A.total_coefs);
     unsigned* ms = (MASKS && A.amask && it >= last_ck) ? A.amask + (size_t)(it - last_ck) * A.amask_slot : nullptr;
-    fwd_iteration<DIM, NMAX, PREC, MASKS>(c, pc, A.xi_bar, it, it == pc.K - 1, A.hist, A.total_samples, fp, ms);
+    fwd_iteration<DIM, NMAX, PREC, MASKS, CAND>(c, pc, A.xi_bar, it, it == pc.K - 1, A.hist, A.total_samples, fp,
+                                                ms, A.prune != 0);
   }
   if (tail) write_checkpoint<DIM, NMAX>(c, tail, pc.K - last_ck, A.total_coefs);
 

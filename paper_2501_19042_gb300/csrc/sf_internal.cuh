@@ -105,6 +105,7 @@ struct FusedArgs {
   float* fp_res2;          // [total samples] sum_k ||z^{k+1} - z^k||^2, or null
   unsigned* amask;         // activity masks of the last checkpoint segment [ck_every][slot], or null
   long long amask_slot;    // words per mask slot (one iteration, all samples)
+  int prune;               // float32 form: exact pair pruning on (1) or every pair tested (0)
   SceneDesc sc[MAX_SCENES_PER_LAUNCH];
 };
 

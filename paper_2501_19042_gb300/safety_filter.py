@@ -193,6 +193,11 @@ class SafetyFilter:
     def set_launch_shape(self, samples_per_cta: int = 0, warps: int = 0, time_chunk: int = 0):
         nat.check(self._lib, self._h, self._lib.sf_set_launch_shape(self._h, samples_per_cta, warps, time_chunk))
 
+    def set_pair_pruning(self, on: bool):
+        """``sf_set_option(SF_OPT_PAIR_PRUNING)``: exact pruning of far pair
+        rows between full tests (default on)."""
+        nat.check(self._lib, self._h, self._lib.sf_set_option(self._h, 1, int(bool(on))))
+
     def launch_shape(self):
         out = (C.c_int * 4)()
         nat.check(self._lib, self._h, self._lib.sf_get_launch_shape(self._h, out))

@@ -272,3 +272,41 @@ def test_nonfinite_input_is_reported_and_contained(sfmod, form, prec):
     assert not torch.isfinite(out.residual[7])
     f.project(_dev(sc.xi_bar), _dev(sc.start), _dev(sc.goal), 15, form=form)
     f.sync_status()
+
+
+@pytest.mark.parametrize("N,S,K,T,seed", [(16, 64, 200, 100, 1), (27, 8, 60, 64, 3), (5, 12, 80, 40, 9),
+                                          (9, 20, 150, 97, 4)])
+def test_pair_pruning_is_exact(sfmod, N, S, K, T, seed):
+    """Testing only the candidate pair rows between full tests gives the same
+    xi, lambda, final residual and per-iteration history as testing every
+    pair every iteration (the drift bound excludes every other row)."""
+    P = sfmod
+    sc = si.scene(si.config_n16_3d(n_robots=N, n_samples=S, T=T), seed)
+    outs = []
+    for prune in (True, False):
+        f = P.SafetyFilter(dim=3, T=T, rho=RHO_3D, coll_a=sc.spec.coll, max_robots=N)
+        f.set_pair_pruning(prune)
+        outs.append(f.project(_dev(sc.xi_bar), _dev(sc.start), _dev(sc.goal), K, hist=True))
+        torch.cuda.synchronize()
+    a, b = outs
+    assert torch.equal(a.xi, b.xi) and torch.equal(a.lam, b.lam)
+    assert torch.equal(a.residual, b.residual) and torch.equal(a.hist, b.hist)
+
+
+def test_pair_pruning_training_forward_and_gradients(sfmod):
+    """The training forward (checkpoints and activity masks) and the adjoint
+    give identical results with and without pair pruning."""
+    from paper_2501_19042_gb300.autograd import sf_unroll
+    P = sfmod
+    sc = si.scene(si.config_diff(n_samples=24), 5)
+    g = torch.randn(sc.xi_bar.shape, generator=torch.Generator().manual_seed(1)).cuda()
+    res = []
+    for prune in (True, False):
+        f = P.SafetyFilter(dim=3, T=100, rho=RHO_3D, coll_a=sc.spec.coll, max_robots=16, checkpoint_every=10)
+        f.set_pair_pruning(prune)
+        xb = _dev(sc.xi_bar).requires_grad_(True)
+        xi, lam, fp, r = sf_unroll(f, xb, _dev(sc.start), _dev(sc.goal), 50)
+        ((g * xi).sum() + fp.sum()).backward()
+        res.append((xi.detach(), fp.detach(), xb.grad.detach()))
+    for u, v in zip(*res):
+        assert torch.equal(u, v)
