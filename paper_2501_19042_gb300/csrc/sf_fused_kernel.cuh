@@ -654,29 +654,35 @@ __device__ void contract_phase(float* SAMP, const Lay& L, const float* BASIS, in
       unsigned* mball = nullptr;
       if (MASKS)
         mball = mk + ((size_t)s * L.T + t0 + tl) * mask_words(NMAX) + mask_pair_words(NMAX);
+      // ball rows: the projection (rsqrt, residual, its square) only runs when
+      // some lane of the warp is outside its ball; inside, q = 0 exactly
       if (pc.use_v) {
-        float v[DIM];
+        float v[DIM], n2 = 0.0f;
 #pragma unroll
-        for (int x = 0; x < DIM; ++x) v[x] = dot_reg(Pd, c[x]);
-        ball_residual<DIM>(v, pc.v_max, qv, rl);
-        if (MASKS) {
-          float n2 = 0.0f;
-#pragma unroll
-          for (int x = 0; x < DIM; ++x) n2 = fmaf(v[x], v[x], n2);
-          if (live && n2 > pc.v_max * pc.v_max) atomicOr(mball + (i >> 5), 1u << (i & 31));
+        for (int x = 0; x < DIM; ++x) {
+          v[x] = dot_reg(Pd, c[x]);
+          n2 = fmaf(v[x], v[x], n2);
+        }
+        const bool out = n2 > pc.v_max * pc.v_max;
+        if (__any_sync(FULL, out)) {
+          ball_residual<DIM>(v, pc.v_max, qv, rl);
+          if (MASKS && live && out) atomicOr(mball + (i >> 5), 1u << (i & 31));
         }
       }
       if (pc.use_a) {
-        float a[DIM];
+        float a[DIM], n2 = 0.0f;
 #pragma unroll
-        for (int x = 0; x < DIM; ++x) a[x] = dot_reg(Pdd, c[x]);
-        ball_residual<DIM>(a, pc.a_max, qa, rl);
-        if (MASKS) {
-          float n2 = 0.0f;
-#pragma unroll
-          for (int x = 0; x < DIM; ++x) n2 = fmaf(a[x], a[x], n2);
-          const int b = NMAX + i;
-          if (live && n2 > pc.a_max * pc.a_max) atomicOr(mball + (b >> 5), 1u << (b & 31));
+        for (int x = 0; x < DIM; ++x) {
+          a[x] = dot_reg(Pdd, c[x]);
+          n2 = fmaf(a[x], a[x], n2);
+        }
+        const bool out = n2 > pc.a_max * pc.a_max;
+        if (__any_sync(FULL, out)) {
+          ball_residual<DIM>(a, pc.a_max, qa, rl);
+          if (MASKS && live && out) {
+            const int b = NMAX + i;
+            atomicOr(mball + (b >> 5), 1u << (b & 31));
+          }
         }
       }
       if (live) rb += rl;
