@@ -280,11 +280,12 @@ __device__ __forceinline__ void ws_row(const float (&ps)[DIM], float (&Ei)[DIM],
 // element NMAX*DIM is set to 1 when some pair of the row is active. With
 // MASKS the lane's activity-mask row (mk + (s T + t) mask_words) is cleared
 // and the bit of every active pair row is set.
-// With CAND (float32 form, prune on) a sample whose drift word allows it
-// runs the candidate path: only the recorded candidate rows are tested, the
-// robots' positions computed on demand and E accumulated in the row; a
-// sample due for a full test records its candidates (and, in the first
-// chunk, copies C to the reference coefficients).
+// With CAND (float32 form, prune on) the CTA runs the candidate path while
+// the drift words of all its samples allow it: only the recorded candidate
+// rows are tested, the robots' positions computed on demand and E
+// accumulated in the row; otherwise every sample gets a full test, records
+// its candidates and (in the first chunk) copies C to the reference
+// coefficients.
 template <int DIM, int NMAX, bool TCM = false, bool MASKS = false, bool CAND = false>
 __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G, int N, int t0, int TCc,
                            const ProblemConsts& pc, bool want_res, int warp, int nwarps, int lane,
@@ -322,12 +323,18 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
         atomicOr(mrow + (b >> 5), 1u << (b & 31));
       }
     };
-    // pair pruning: full test (and record candidates) or candidates only
+    // pair pruning: full test (and record candidates) or candidates only.
+    // The decision is taken for the whole CTA (a full test of every sample as
+    // soon as one sample needs it), so that the warps of a phase do the same
+    // kind of work and none waits at the barrier for a full test of another.
     bool refresh = true;
     unsigned* cmrow = nullptr;
     if (CAND) {
-      const float drift = __int_as_float(*reinterpret_cast<const int*>(blk + L.RF));
-      refresh = !prune || !(sqrtf((float)DIM) * drift < kPruneDriftLimit);   // NaN: full test
+      refresh = !prune;
+      for (int q = 0; q < G && !refresh; ++q) {
+        const float drift = __int_as_float(*reinterpret_cast<const int*>(SAMP + (size_t)q * L.SB + L.RF));
+        refresh = !(sqrtf((float)DIM) * drift < kPruneDriftLimit);   // NaN: full test
+      }
       cmrow = reinterpret_cast<unsigned*>(blk + L.CM) + (size_t)t * L.CMW;
     }
     const bool rec = CAND && refresh && valid;
@@ -424,7 +431,11 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
         }
       }
       // a row of pairs (i, j > i) is tested without branches; only a row that
-      // is active on some lane of the warp is walked pair by pair
+      // is active on some lane of the warp is walked pair by pair. Candidate
+      // rows (pruning) are collected branch-free in registers.
+      unsigned cmr[PW];
+#pragma unroll
+      for (int q = 0; q < PW; ++q) cmr[q] = 0u;
 #pragma unroll
       for (int i = 0; i < NMAX; ++i) {
         if (i + 1 < N) {
@@ -434,7 +445,10 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
             if (j > i && j < N) {
               const float s2 = scaled_d2<DIM>(p[i], p[j]);
               row |= s2 < 1.0f;
-              cand(i, j, s2);
+              if (CAND) {
+                const int b = pair_bit(NMAX, i, j);
+                cmr[b >> 5] |= (s2 < kPruneCandS2) ? (1u << (b & 31)) : 0u;
+              }
             }
           if (__any_sync(FULL, row)) {
 #pragma unroll
@@ -448,6 +462,10 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
               }
           }
         }
+      }
+      if (CAND && rec) {
+#pragma unroll
+        for (int q = 0; q < PW; ++q) cmrow[q] = cmr[q];
       }
       // workspace rows of every robot (Eq. workspace_con): q = e - p pulls a
       // position outside the spheroid back to its surface
