@@ -193,9 +193,12 @@ typedef enum {
    * test of the sample; a full test is rerun as soon as the sample's
    * coefficients may have moved its positions by 0.25 (scaled) or more, in a
    * bound that holds for every t (Bernstein weights are non-negative and sum
-   * to 1). The result is the same as testing every pair. 0: every pair every
-   * iteration. Off while use_workspace is set; no effect in the 16-bit modes,
-   * the plain form and the backward's recompute. */
+   * to 1); with the workspace block, the workspace rows of robots that were
+   * within 0.1 (workspace-scaled) of its boundary are retested likewise. The
+   * result is the same as testing every row. 0: every row every iteration.
+   * In the 16-bit modes the retests use float32 positions and the MMA
+   * positions are computed only for full tests. No effect in the plain form
+   * and the backward's recompute. */
   SF_OPT_PAIR_PRUNING = 1
 } sf_option;
 

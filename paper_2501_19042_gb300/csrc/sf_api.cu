@@ -229,7 +229,7 @@ sf_status build_groups(sf_handle* h, const sf_batch* b, int K, long long S, cons
       a.ck_every = std::max(1, h->pb.checkpoint_every);
       a.total_coefs = tot;
       a.fp_res2 = rq.fp_res2;
-      a.prune = (h->prune && !h->pb.use_workspace) ? 1 : 0;
+      a.prune = h->prune ? 1 : 0;
       if (rq.ckpt && !rq.backward) {
         const long long ck = a.ck_every, nck = (K + ck - 1) / ck;
         a.amask = reinterpret_cast<unsigned*>(rq.ckpt + states_floats_aligned(nck + ck + 1, tot));

@@ -68,7 +68,7 @@ cudaError_t prepare_kernels(int dim, int smem, int prec) {
 int fused_max_warps(int nmax, bool bwd) { return (bwd && nmax > 16) ? 8 : 12; }
 
 size_t fused_smem_bytes(int dim, int nmax, int T, int gmax, int tc, int nq, bool bwd, int prec) {
-  const fused_impl::Lay L(dim, nmax, T, tc, nq, bwd, prec != 0, prec == 0 && !bwd);
+  const fused_impl::Lay L(dim, nmax, T, tc, nq, bwd, prec != 0, !bwd);
   return sizeof(float) * ((size_t)L.head + (size_t)gmax * L.SB);
 }
 

@@ -44,6 +44,12 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr float kPruneMargin = 0.5f;
 constexpr float kPruneCandS2 = (1.0f + kPruneMargin) * (1.0f + kPruneMargin);
 constexpr float kPruneDriftLimit = 0.5f * kPruneMargin - 1e-3f;
+// Workspace rows: a full test records the robots with workspace-scaled
+// offset > 1 - kWsMargin; the others stay inside while the workspace-scaled
+// drift sqrt(dim) max_x (a_x / w_x) max |c - c_ref| / a_x stays below it.
+constexpr float kWsMargin = 0.1f;
+constexpr float kWsCandS2 = (1.0f - kWsMargin) * (1.0f - kWsMargin);
+constexpr float kWsDriftLimit = kWsMargin - 1e-3f;
 
 // Shared-memory layout (floats). Head, float32 form: basis [T][36],
 // operators, beta. Head, tensor-core form: the basis as 16-bit operand
@@ -62,11 +68,12 @@ constexpr float kPruneDriftLimit = 0.5f * kPruneMargin - 1e-3f;
 // A fragments (per lane quad t4: k pairs (2 t4, 2 t4 + 8) rounded to 16 bits,
 // then their rounding remainders), refreshed by every xi step; float32 form
 // with pair pruning only: CR [NMAX][DIM][12] (coefficients at the last full
-// pair test), CM [T][CMW] (candidate pair rows of that test), RF (drift of
-// the coefficients since then, as the bit pattern of a non-negative float).
+// pair test), CM [T][CMW] (candidate pair rows of that test), WC [T]
+// (candidate workspace rows: robots near or outside the workspace), RF (drift
+// of the coefficients since then, as the bit pattern of a non-negative float).
 struct Lay {
   int RS, EP, TC, NQ, T, nmax, dim;
-  int C, LAM, XIB, PG, MC, MR, EB, RS2, RSB, FPP, FPR, XB, LB, GXB, U, CW, CF, CR, CM, RF, CMW, SB;
+  int C, LAM, XIB, PG, MC, MR, EB, RS2, RSB, FPP, FPR, XB, LB, GXB, U, CW, CF, CR, CM, WC, RF, CMW, SB;
   int head, TH, bno, bto, opso, betao;
   __host__ __device__ Lay(int dim_, int nmax_, int T_, int TC_, int NQ_, bool bwd = false, bool tcm = false,
                           bool cand = false) {
@@ -93,11 +100,13 @@ struct Lay {
     CW = U + (bwd ? nmax * RS : 0);
     CF = CW + (bwd ? nmax * RS : 0);
     // pair pruning (float32 forward): reference coefficients, candidate
-    // pair masks per (t) of mask_pair_words rounded to 4 words, drift word
+    // pair masks per (t) of mask_pair_words rounded to 4 words, workspace
+    // candidate robots per (t), drift word
     CMW = cand ? (mask_pair_words(nmax) + 3) / 4 * 4 : 0;
     CR = CF + (tcm ? ((dim * nmax + 15) / 16) * 256 : 0);
     CM = CR + (cand ? nmax * RS : 0);
-    RF = CM + T * CMW;
+    WC = CM + T * CMW;
+    RF = WC + (cand ? ((T + 3) / 4) * 4 : 0);
     SB = RF + (cand ? 4 : 0);
     TH = (T + 1) / 2;
     bno = 0;
@@ -303,7 +312,7 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
     float* blk = SAMP + (size_t)s * L.SB;
     const float* Cs = blk + L.C;
     float Pr[NV];
-    if (!TCM) row_from(BASIS + (size_t)t * BASIS_ROW, Pr);
+    if (!TCM || CAND) row_from(BASIS + (size_t)t * BASIS_ROW, Pr);   // TCM: the global float32 basis
     float E[NMAX][DIM];
 #pragma unroll
     for (int i = 0; i < NMAX; ++i)
@@ -331,9 +340,13 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
     unsigned* cmrow = nullptr;
     if (CAND) {
       refresh = !prune;
+      float wkmax = 0.0f;
+#pragma unroll
+      for (int x = 0; x < DIM; ++x) wkmax = fmaxf(wkmax, pc.wk[x]);
       for (int q = 0; q < G && !refresh; ++q) {
-        const float drift = __int_as_float(*reinterpret_cast<const int*>(SAMP + (size_t)q * L.SB + L.RF));
-        refresh = !(sqrtf((float)DIM) * drift < kPruneDriftLimit);   // NaN: full test
+        const float drift = sqrtf((float)DIM) *
+                            __int_as_float(*reinterpret_cast<const int*>(SAMP + (size_t)q * L.SB + L.RF));
+        refresh = !(drift < kPruneDriftLimit) || (pc.use_w && !(drift * wkmax < kWsDriftLimit));  // NaN: full
       }
       cmrow = reinterpret_cast<unsigned*>(blk + L.CM) + (size_t)t * L.CMW;
     }
@@ -394,6 +407,23 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
                 ebw[j * DIM + x] += Ej[x];
               }
             }
+          }
+        }
+        if (pc.use_w) {   // workspace rows of the robots recorded near the boundary
+          unsigned m = reinterpret_cast<const unsigned*>(blk + L.WC)[t];
+          while (m) {
+            const int i = __ffs(m) - 1;
+            m &= m - 1;
+            float pi[DIM], Ei[DIM];
+            state<DIM>(Pr, Cs + i * RS, pi);
+#pragma unroll
+            for (int x = 0; x < DIM; ++x) {
+              pi[x] *= (x == 2 ? pc.inv_b : pc.inv_a);
+              Ei[x] = 0.0f;
+            }
+            ws_row<DIM, NMAX, MASKS>(pi, Ei, true, i, pc, res2, mrow);
+#pragma unroll
+            for (int x = 0; x < DIM; ++x) ebw[i * DIM + x] += Ei[x];
           }
         }
       }
@@ -471,6 +501,7 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
       // position outside the spheroid back to its surface
       if (pc.use_w) {
         bool outw = false;
+        unsigned wsc = 0u;
 #pragma unroll
         for (int i = 0; i < NMAX; ++i)
           if (i < N) {
@@ -481,7 +512,9 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
               s2 = fmaf(w, w, s2);
             }
             outw |= valid && s2 > 1.0f;
+            if (CAND) wsc |= (s2 > kWsCandS2) ? (1u << i) : 0u;
           }
+        if (CAND && rec) reinterpret_cast<unsigned*>(blk + L.WC)[t] = wsc;
         if (__any_sync(FULL, outw)) {
 #pragma unroll
           for (int i = 0; i < NMAX; ++i)
@@ -567,6 +600,7 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
       }
       if (pc.use_w) {
         bool outw = false;
+        unsigned wsc = 0u;
         for (int i = 0; i < N; ++i) {
           float s2 = 0.0f;
 #pragma unroll
@@ -575,7 +609,9 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
             s2 = fmaf(w, w, s2);
           }
           outw |= valid && s2 > 1.0f;
+          if (CAND && s2 > kWsCandS2) wsc |= 1u << i;
         }
+        if (CAND && rec) reinterpret_cast<unsigned*>(blk + L.WC)[t] = wsc;
         if (__any_sync(FULL, outw)) {
 #pragma unroll
           for (int i = 0; i < NMAX; ++i)
@@ -592,6 +628,7 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
       float* eb = blk + L.EB + tl * L.EP;
       if (e_in_row) {
         // candidate path: E is already in the row
+        if (TCM) eb[NMAX * DIM] = res2 > 0.0f ? 1.0f : 0.0f;
       } else if (TCM) {
         // whole row in 16-byte stores (E of robots >= N is zero); the row
         // stride is a multiple of 4 floats, scalar stores would conflict
@@ -1308,13 +1345,30 @@ __device__ void store_state(const Cta<DIM, NMAX>& c, float* xi_dst, float* lam_d
   }
 }
 
+// The CTA-wide pruning decision of the pair phase: a full pair test when
+// pruning is off or some sample's drift (or workspace drift) bound is
+// reached.
+template <int DIM, int NMAX>
+__device__ __forceinline__ bool cta_refresh(const Cta<DIM, NMAX>& c, const Lay& L, const ProblemConsts& pc,
+                                            bool prune) {
+  if (!prune) return true;
+  float wkmax = 0.0f;
+#pragma unroll
+  for (int x = 0; x < DIM; ++x) wkmax = fmaxf(wkmax, pc.wk[x]);
+  for (int q = 0; q < c.G; ++q) {
+    const float drift = sqrtf((float)DIM) * __int_as_float(*reinterpret_cast<const int*>(c.blk(q) + L.RF));
+    if (!(drift < kPruneDriftLimit) || (pc.use_w && !(drift * wkmax < kWsDriftLimit))) return true;
+  }
+  return false;
+}
+
 // One iteration of f_FP on every sample of the CTA (time chunks, then the
 // lambda step and the xi step). keep_prev stores xi^k in the EB region for
 // the final residual. fp (when set) adds ||z^{k+1} - z^k||^2 per sample to FPR.
 template <int DIM, int NMAX, int PREC = 0, bool MASKS = false, bool CAND = false>
 __device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, const float* xi_bar, int it,
                               bool keep_prev, float* hist, int total_samples, bool fp, unsigned* mslot = nullptr,
-                              bool prune = false) {
+                              bool prune = false, const float* gbasis = nullptr) {
   constexpr int RS = DIM * NP;
   const Lay& L = c.L;
   const int T = pc.T, N = c.N, G = c.G, TC = L.TC;
@@ -1324,9 +1378,13 @@ __device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, 
   for (int t0 = 0; t0 < T; t0 += TC) {
     const int TCc = min(TC, T - t0);
     if constexpr (PREC != 0) {
-      tc_positions_phase<DIM, NMAX, PREC>(c.SAMP, L, c.BN, G, N, t0, TCc, pc, c.warp, c.nwarps, c.lane);
-      __syncthreads();
-      pair_phase<DIM, NMAX, true>(c.SAMP, L, nullptr, G, N, t0, TCc, pc, want_res, c.warp, c.nwarps, c.lane);
+      // the positions from the MMAs are needed only by a full pair test
+      if (!CAND || cta_refresh<DIM>(c, L, pc, prune)) {
+        tc_positions_phase<DIM, NMAX, PREC>(c.SAMP, L, c.BN, G, N, t0, TCc, pc, c.warp, c.nwarps, c.lane);
+        __syncthreads();
+      }
+      pair_phase<DIM, NMAX, true, false, CAND>(c.SAMP, L, gbasis, G, N, t0, TCc, pc, want_res, c.warp, c.nwarps,
+                                               c.lane, nullptr, prune);
       __syncthreads();
       tc_contract_phase<DIM, NMAX, PREC>(c.SAMP, L, c.BN, c.BT, G, N, t0, TCc, t0 == 0, pc, want_res, c.warp,
                                          c.nwarps, c.lane);
@@ -1467,7 +1525,7 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
   float* sm = reinterpret_cast<float*>(smem4);
   const ProblemConsts& pc = A.pc;
   const int T = pc.T;
-  constexpr bool CAND = PREC == 0;   // pair pruning in the float32 form
+  constexpr bool CAND = true;   // pair pruning (the 16-bit forms too)
   const Cta<DIM, NMAX> c(A.sc, A.n_scenes, T, A.tc, A.nq, false, sm, PREC != 0, CAND);
   if (c.G <= 0) return;
   const Lay& L = c.L;
@@ -1497,7 +1555,7 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
     if (tail && it >= last_ck) write_checkpoint<DIM, NMAX>(c, tail, it - last_ck, A.total_coefs);
     unsigned* ms = (MASKS && A.amask && it >= last_ck) ? A.amask + (size_t)(it - last_ck) * A.amask_slot : nullptr;
     fwd_iteration<DIM, NMAX, PREC, MASKS, CAND>(c, pc, A.xi_bar, it, it == pc.K - 1, A.hist, A.total_samples, fp,
-                                                ms, A.prune != 0);
+                                                ms, A.prune != 0, reinterpret_cast<const float*>(A.basis));
   }
   if (tail) write_checkpoint<DIM, NMAX>(c, tail, pc.K - last_ck, A.total_coefs);
 

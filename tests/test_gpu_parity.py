@@ -278,8 +278,9 @@ def test_nonfinite_input_is_reported_and_contained(sfmod, form, prec):
                                           (9, 20, 150, 97, 4)])
 def test_pair_pruning_is_exact(sfmod, N, S, K, T, seed):
     """Testing only the candidate pair rows between full tests gives the same
-    xi, lambda, final residual and per-iteration history as testing every
-    pair every iteration (the drift bound excludes every other row)."""
+    xi, lambda and final residual as testing every pair every iteration (the
+    drift bound excludes every other row), and the same per-iteration history
+    up to the order of its sum."""
     P = sfmod
     sc = si.scene(si.config_n16_3d(n_robots=N, n_samples=S, T=T), seed)
     outs = []
@@ -290,7 +291,10 @@ def test_pair_pruning_is_exact(sfmod, N, S, K, T, seed):
         torch.cuda.synchronize()
     a, b = outs
     assert torch.equal(a.xi, b.xi) and torch.equal(a.lam, b.lam)
-    assert torch.equal(a.residual, b.residual) and torch.equal(a.hist, b.hist)
+    assert torch.equal(a.residual, b.residual)
+    # the history sums squared residuals; above 16 robots the full test sums
+    # them in block order, the candidate path in row order
+    torch.testing.assert_close(a.hist, b.hist, rtol=1e-5, atol=1e-7)
 
 
 def test_pair_pruning_training_forward_and_gradients(sfmod):

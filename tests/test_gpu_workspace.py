@@ -127,3 +127,24 @@ def test_workspace_adjoint_matches_autograd(sfmod, oracle_lib):
     a = xbd.grad.double().cpu().reshape(6, -1)
     b = g_ref.reshape(6, -1)
     assert ((a - b).norm(dim=1) / b.norm(dim=1)).max().item() <= 2e-3
+
+
+@pytest.mark.parametrize("n_robots,seed,ws", [(16, 61, WS3), (27, 63, ((0.0, 0.0, 0.0), 5.0, 3.0))])
+def test_workspace_pruning_is_exact(sfmod, n_robots, seed, ws):
+    """Pair and workspace-row pruning give the same xi, lambda, residual and
+    history as testing every row every iteration."""
+    sc = _scene3(n_robots=n_robots, n_samples=12, T=80, seed=seed, ws=ws)
+    outs = []
+    for prune in (True, False):
+        spec = sc.spec
+        f = sfmod.SafetyFilter(dim=3, T=spec.T, rho=RHO_3D, coll_a=spec.coll, v_max=spec.v_max, a_max=spec.a_max,
+                               max_robots=spec.n_robots, t_final=spec.t_final, workspace=ws)
+        f.set_pair_pruning(prune)
+        outs.append(f.project(_dev(sc.xi_bar), _dev(sc.start), _dev(sc.goal), 150, hist=True))
+        torch.cuda.synchronize()
+    a, b = outs
+    assert torch.equal(a.xi, b.xi) and torch.equal(a.lam, b.lam)
+    assert torch.equal(a.residual, b.residual)
+    # the history sums squared residuals; above 16 robots the full test sums
+    # them in block order, the candidate path in row order
+    torch.testing.assert_close(a.hist, b.hist, rtol=1e-5, atol=1e-7)
