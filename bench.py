@@ -225,6 +225,8 @@ def run_gpu(args):
             "wall_s_timed": wall,
             "clocks": clocks,
         }
+        if args.form == "fused":
+            line["plain_form"] = plain_form_timing(f, xb, st, gl, K, flush, stream, ms, S)
         if not args.no_diff:
             line["differentiation"] = diff_timing(P, dev)
         if not args.no_batching:
@@ -242,6 +244,30 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def plain_form_timing(f, xb, st, gl, K, flush, stream, fused_ms, S, steps: int = 3):
+    """The plain form (states / project / transpose / solve / residual
+    kernels, time-domain arrays in HBM) on the bench workload and handle, with
+    the same warm-up, L2 flush and event timing as the headline number."""
+    import torch
+    out = f.project(xb, st, gl, K, form="plain")
+    for _ in range(2):
+        f.project(xb, st, gl, K, form="plain", out=out)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        f.project(xb, st, gl, K, form="plain", out=out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    f.sync_status()
+    ms = float(np.mean(ts))
+    return {"ms_per_step": ms, "samples_per_s": S / (ms * 1e-3), "chosen_over_plain": ms / fused_ms,
+            "median_final_residual": float(out.residual.median()), "steps": steps}
 
 
 def diff_timing(P, dev):

@@ -4,9 +4,9 @@ The samples of a batch are independent (every sample is its own fixed-point
 problem, Appendix), and so are scenes: a batch is split into contiguous
 ranges of its concatenated samples, one range per rank, with no collective on
 the data path. A scene cut by a range boundary appears on both ranks with
-its own robots' start / goal rows and the samples each rank owns. Only the
-timing (the slowest rank) and, when one consumer needs every result, an
-all-gather of the outputs cross ranks.
+its own robots' start / goal rows and the samples each rank owns. What
+crosses ranks is only the timing (the slowest rank) and, when one consumer
+needs every result, an all-gather of the outputs.
 """
 from __future__ import annotations
 

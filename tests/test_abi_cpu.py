@@ -57,6 +57,20 @@ def test_create_validates_before_device(lib):
     assert lib.sf_project(None, None, None, 1, 0, None, None, None, None, None, None, None, 0, None) == 1
     assert lib.sf_workspace_bytes(None, None, 0, 1) == 0
     assert lib.sf_launch_count(None) == 0
+    assert lib.sf_set_option(None, 1, 1) == 1
+    assert lib.sf_eq_project(None, None, None, None) == 1
+    assert lib.sf_eq_project_backward(None, None, None, None, None, None) == 1
+    # workspace block: semi-axes must be positive and the centre finite
+    bad = nat.SfProblem.from_buffer_copy(pb)
+    bad.use_workspace, bad.ws_a, bad.ws_b = 1, 0.0, 1.0
+    assert lib.sf_create(C.byref(bad), 0, C.byref(h)) == 1
+    bad = nat.SfProblem.from_buffer_copy(pb)
+    bad.use_workspace, bad.ws_a, bad.ws_b = 1, 2.0, 1.0
+    bad.ws_center[1] = float("nan")
+    assert lib.sf_create(C.byref(bad), 0, C.byref(h)) == 1
+    bad = nat.SfProblem.from_buffer_copy(pb)
+    bad.use_workspace = 2
+    assert lib.sf_create(C.byref(bad), 0, C.byref(h)) == 1
     lib.sf_destroy(None)
 
 
