@@ -331,13 +331,36 @@ __device__ void adjoint_step(const Cta<DIM, NMAX>& c, const BwdArgs& A, const fl
     blk[L.C + rem] = val;
   }
   __syncthreads();
-  // (1) robot mean of xb
-  for (int v = c.tid; v < G * DIM * NV; v += c.nthr) {
-    const int s = v / (DIM * NV), x = (v / NV) % DIM, k = v % NV;
-    float* blk = c.blk(s);
-    float sm = 0.0f;
-    for (int i = 0; i < N; ++i) sm += blk[L.XB + i * RS + x * NP + k];
-    blk[L.MC + x * NP + k] = sm * invN;
+  // (1) robot mean of xb, and the mean terms of the transposed xi step:
+  // MC = DS^T mean(xb), MR = DW^T mean(xb). Lanes (s, x, k) with k padded to
+  // 16, so that the 11 k of one (s, x) share a half-warp and exchange their
+  // means by shuffles.
+  {
+    const int nB1 = G * DIM * 16;
+    const int lane = c.lane;
+    for (int base = c.tid - lane; base < nB1; base += c.nthr) {
+      const int v = base + lane;
+      const int vq = v < nB1 ? v : 0;
+      const int s = vq / (DIM * 16), x = (vq >> 4) % DIM, k = vq & 15;
+      const bool act = v < nB1 && k < NV;
+      float* blk = c.blk(s);
+      float sm = 0.0f;
+      if (act)
+        for (int i = 0; i < N; ++i) sm += blk[L.XB + i * RS + x * NP + k];
+      const float mx = sm * invN;
+      const int kk = k < NV ? k : 0;
+      float md = 0.0f, mw = 0.0f;
+#pragma unroll
+      for (int m = 0; m < NV; ++m) {
+        const float xm = __shfl_sync(FULL, mx, (lane & 16) + m);
+        md = fmaf(c.OPS[OPS_DS + m * NP + kk], xm, md);
+        mw = fmaf(c.OPS[OPS_DW + m * NP + kk], xm, mw);
+      }
+      if (act) {
+        blk[L.MC + x * NP + k] = md;
+        blk[L.MR + x * NP + k] = mw;
+      }
+    }
   }
   __syncthreads();
   // (2) coefficient-space adjoint of the xi step and the lambda step
@@ -345,18 +368,16 @@ __device__ void adjoint_step(const Cta<DIM, NMAX>& c, const BwdArgs& A, const fl
     const int s = v / (N * DIM), i = (v / DIM) % N, x = v % DIM;
     float* blk = c.blk(s);
     const int o = i * RS + x * NP;
-    float xb[NV], mx[NV];
+    float xb[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) { xb[k] = blk[L.XB + o + k]; mx[k] = blk[L.MC + x * NP + k]; }
+    for (int k = 0; k < NV; ++k) xb[k] = blk[L.XB + o + k];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      float u1 = 0.0f, cw = 0.0f;
+      float u1 = blk[L.MC + x * NP + k], cw = blk[L.MR + x * NP + k];
 #pragma unroll
       for (int m = 0; m < NV; ++m) {
         u1 = fmaf(c.OPS[OPS_S1 + m * NP + k], xb[m], u1);
-        u1 = fmaf(c.OPS[OPS_DS + m * NP + k], mx[m], u1);
         cw = fmaf(c.OPS[OPS_W1 + m * NP + k], xb[m], cw);
-        cw = fmaf(c.OPS[OPS_DW + m * NP + k], mx[m], cw);
       }
       const float lt = blk[L.LB + o + k] + u1;
       blk[L.U + o + k] = rho * (u1 + lt);

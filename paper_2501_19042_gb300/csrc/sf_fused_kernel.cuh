@@ -59,10 +59,11 @@ constexpr float kWsDriftLimit = kWsMargin - 1e-3f;
 // time steps, TH = ceil(T / 2); rounded, then the rounding remainders),
 // operators, beta.
 // Per sample: C, LAM [NMAX][DIM][12]; PG [NQ][NMAX][DIM][12] (partials of
-// F^T q, later r); MC, MR [DIM][12] (robot means); EB [TC][EP] (E of the
-// chunk, EP = NMAX*DIM + 1, or NMAX*DIM + 4 in the tensor-core form where a
-// row first holds the scaled positions and its element NMAX*DIM flags an
-// active pair; also holds xi^{K-1} after the last iteration); RS2 [T] (pair
+// F^T q, later r); MC, MR [DIM][12] (forward: MR holds the xi step's mean
+// term DW mean(c) + DS mean(r); adjoint: DS^T mean(xb) and DW^T mean(xb));
+// EB [TC][EP] (E of the chunk, EP = NMAX*DIM + 1, or NMAX*DIM + 4 in the
+// tensor-core form where a row first holds the scaled positions and its
+// element NMAX*DIM flags an active pair; also holds xi^{K-1} after the last iteration); RS2 [T] (pair
 // residual per t); RSB [NQ][NMAX] (ball residual partials); tensor-core form
 // only: CF [16 MT][4][4] words, the coefficient rows r = x * NMAX + i as MMA
 // A fragments (per lane quad t4: k pairs (2 t4, 2 t4 + 8) rounded to 16 bits,
@@ -1403,71 +1404,117 @@ __device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, 
     }
     __syncthreads();
   }
-  // ---- solve phase 1: lambda step, r, robot means (and the history entry)
-  for (int v = c.tid; v < G * DIM * NV; v += c.nthr) {
-    const int s = v / (DIM * NV), x = (v / NV) % DIM, k = v % NV;
-    float* blk = c.blk(s);
-    float sr = 0.0f, sc = 0.0f, dl2 = 0.0f;
-    for (int i = 0; i < N; ++i) {
-      const int o = i * RS + x * NP + k;
-      float g = blk[L.PG + o];
-      for (int q = 1; q < L.NQ; ++q) g += blk[L.PG + q * NMAX * RS + o];
-      const float lam = fmaf(rho, g, blk[L.LAM + o]);
-      dl2 = fmaf(lam - blk[L.LAM + o], lam - blk[L.LAM + o], dl2);
-      blk[L.LAM + o] = lam;
-      const float r = fmaf(rho, g, lam) + blk[L.XIB + o];
-      blk[L.PG + o] = r;
-      sr += r;
-      sc += blk[L.C + o];
-    }
-    blk[L.MR + x * NP + k] = sr * invN;
-    blk[L.MC + x * NP + k] = sc * invN;
-    if (CAND && x == 0 && k == 0) *reinterpret_cast<int*>(blk + L.RF) = 0;   // drift since the reference
-    if (fp) blk[L.FPP + x * NV + k] = dl2;
-    if (want_res && x == 0 && k == 0) {
-      float r2 = 0.0f;
-      for (int t = 0; t < T; ++t) r2 += blk[L.RS2 + t];
-      for (int q = 0; q < L.NQ; ++q)
-        for (int i = 0; i < N; ++i) r2 += blk[L.RSB + q * NMAX + i];
-      hist[(size_t)it * total_samples + c.gsample0 + s] = sqrtf(r2);
+  // ---- solve phase 1: lambda step, r, robot means, and the mean term of
+  // the xi step (and the history entry). Lanes (s, x, k) with k padded to 16,
+  // so that the 11 k of one (s, x) share a half-warp: after the robot loop
+  // each lane forms its k of DW mean(c) + DS mean(r) from its neighbours'
+  // means by shuffles, and stores it in MR (phase 2 reads only that).
+  {
+    const int nB1 = G * DIM * 16;
+    const int lane = c.lane;
+    for (int base = c.tid - lane; base < nB1; base += c.nthr) {
+      const int v = base + lane;
+      const int vq = v < nB1 ? v : 0;
+      const int s = vq / (DIM * 16), x = (vq >> 4) % DIM, k = vq & 15;
+      const bool act = v < nB1 && k < NV;
+      float* blk = c.blk(s);
+      float sr = 0.0f, sc = 0.0f, dl2 = 0.0f;
+      if (act) {
+        const int o0 = x * NP + k;
+        int i = 0;
+        // four robots' loads first (no store in between), then their updates
+        for (; i + 4 <= N; i += 4) {
+          float gq[4], lq[4], xq[4], cq[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int o = (i + u) * RS + o0;
+            float g = blk[L.PG + o];
+            for (int q = 1; q < L.NQ; ++q) g += blk[L.PG + q * NMAX * RS + o];
+            gq[u] = g;
+            lq[u] = blk[L.LAM + o];
+            xq[u] = blk[L.XIB + o];
+            cq[u] = blk[L.C + o];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int o = (i + u) * RS + o0;
+            const float lam = fmaf(rho, gq[u], lq[u]);
+            dl2 = fmaf(lam - lq[u], lam - lq[u], dl2);
+            blk[L.LAM + o] = lam;
+            const float r = fmaf(rho, gq[u], lam) + xq[u];
+            blk[L.PG + o] = r;
+            sr += r;
+            sc += cq[u];
+          }
+        }
+        for (; i < N; ++i) {
+          const int o = i * RS + o0;
+          float g = blk[L.PG + o];
+          for (int q = 1; q < L.NQ; ++q) g += blk[L.PG + q * NMAX * RS + o];
+          const float lold = blk[L.LAM + o];
+          const float lam = fmaf(rho, g, lold);
+          dl2 = fmaf(lam - lold, lam - lold, dl2);
+          blk[L.LAM + o] = lam;
+          const float r = fmaf(rho, g, lam) + blk[L.XIB + o];
+          blk[L.PG + o] = r;
+          sr += r;
+          sc += blk[L.C + o];
+        }
+      }
+      const float mr = sr * invN, mc = sc * invN;
+      float dw[NV], ds[NV];
+      row_from(c.OPS + OPS_DW + (k < NV ? k : 0) * NP, dw);
+      row_from(c.OPS + OPS_DS + (k < NV ? k : 0) * NP, ds);
+      float m0 = 0.0f, m1 = 0.0f;
+#pragma unroll
+      for (int m = 0; m < NV; ++m) {
+        m0 = fmaf(dw[m], __shfl_sync(FULL, mc, (lane & 16) + m), m0);
+        m1 = fmaf(ds[m], __shfl_sync(FULL, mr, (lane & 16) + m), m1);
+      }
+      if (act) blk[L.MR + x * NP + k] = m0 + m1;
+      if (CAND && act && x == 0 && k == 0) *reinterpret_cast<int*>(blk + L.RF) = 0;   // drift since the reference
+      if (fp && act) blk[L.FPP + x * NV + k] = dl2;
+      if (want_res && act && x == 0 && k == 0) {
+        float r2 = 0.0f;
+        for (int t = 0; t < T; ++t) r2 += blk[L.RS2 + t];
+        for (int q = 0; q < L.NQ; ++q)
+          for (int i = 0; i < N; ++i) r2 += blk[L.RSB + q * NMAX + i];
+        hist[(size_t)it * total_samples + c.gsample0 + s] = sqrtf(r2);
+      }
     }
   }
   __syncthreads();
-  // ---- solve phase 2: xi step
+  // ---- solve phase 2: xi step, xi_i = W1 c_i + S1 r_i + (DW mean(c) +
+  // DS mean(r)) + beta_i per (sample, robot, axis)
   for (int v = c.tid; v < G * N * DIM; v += c.nthr) {
     const int s = v / (N * DIM), i = (v / DIM) % N, x = v % DIM;
     float* blk = c.blk(s);
     const int o = i * RS + x * NP;
-    float cc[NP], r[NP], cm[NP], rm[NP];
+    float cc[NP], r[NP], mt[NP];
     const float4* c4 = reinterpret_cast<const float4*>(blk + L.C + o);
     const float4* r4 = reinterpret_cast<const float4*>(blk + L.PG + o);
-    const float4* cm4 = reinterpret_cast<const float4*>(blk + L.MC + x * NP);
-    const float4* rm4 = reinterpret_cast<const float4*>(blk + L.MR + x * NP);
+    const float4* mt4 = reinterpret_cast<const float4*>(blk + L.MR + x * NP);
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      const float4 a = c4[q], b = r4[q], e = cm4[q], f = rm4[q];
+      const float4 a = c4[q], b = r4[q], e = mt4[q];
       cc[4 * q] = a.x; cc[4 * q + 1] = a.y; cc[4 * q + 2] = a.z; cc[4 * q + 3] = a.w;
       r[4 * q] = b.x; r[4 * q + 1] = b.y; r[4 * q + 2] = b.z; r[4 * q + 3] = b.w;
-      cm[4 * q] = e.x; cm[4 * q + 1] = e.y; cm[4 * q + 2] = e.z; cm[4 * q + 3] = e.w;
-      rm[4 * q] = f.x; rm[4 * q + 1] = f.y; rm[4 * q + 2] = f.z; rm[4 * q + 3] = f.w;
+      mt[4 * q] = e.x; mt[4 * q + 1] = e.y; mt[4 * q + 2] = e.z; mt[4 * q + 3] = e.w;
     }
     float out[NP];
     float dx2 = 0.0f;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      float w1[NV], s1[NV], dw[NV], ds[NV];
+      float w1[NV], s1[NV];
       row_from(c.OPS + OPS_W1 + k * NP, w1);
       row_from(c.OPS + OPS_S1 + k * NP, s1);
-      row_from(c.OPS + OPS_DW + k * NP, dw);
-      row_from(c.OPS + OPS_DS + k * NP, ds);
-      float acc = c.BETA[o + k];
+      float a0 = c.BETA[o + k] + mt[k], a1 = 0.0f;
 #pragma unroll
       for (int m = 0; m < NV; ++m) {
-        acc = fmaf(w1[m], cc[m], acc);
-        acc = fmaf(s1[m], r[m], acc);
-        acc = fmaf(dw[m], cm[m], acc);
-        acc = fmaf(ds[m], rm[m], acc);
+        a0 = fmaf(w1[m], cc[m], a0);
+        a1 = fmaf(s1[m], r[m], a1);
       }
+      const float acc = a0 + a1;
       out[k] = acc;
       dx2 = fmaf(acc - cc[k], acc - cc[k], dx2);
     }
