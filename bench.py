@@ -225,7 +225,7 @@ def run_gpu(args):
             "wall_s_timed": wall,
             "clocks": clocks,
         }
-        if args.form == "fused":
+        if args.form == "fused" and not args.no_plain_form:
             line["plain_form"] = plain_form_timing(f, xb, st, gl, K, flush, stream, ms, S)
         if not args.no_diff:
             line["differentiation"] = diff_timing(P, dev)
@@ -590,6 +590,8 @@ def main():
     ap.add_argument("--no-workspace", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-qp", action="store_true")
+    ap.add_argument("--no-plain-form", action="store_true",
+                    help="skip the plain-form timing on the bench workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
