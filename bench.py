@@ -33,6 +33,10 @@ RHO = 0.1
 METRIC = "SF-projected samples/s (16 robots 3D, residual<=1e-3), chosen vs plain form"
 UNIT = "samples/s"
 FP32_LANES_PER_SM = 128
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one float32
+# fused_fwd_kernel launch on the bench workload, from one ncu capture of the
+# current kernel (profiles/fused_fwd_n16_3d_s1024_k200.md): the inputs once
+FWD_TRAFFIC_BYTES = 2_455_552
 DTYPES = {"fp32": "f32",
           "bf16": "bf16 tensor-core products (three-term), f32 accumulation and element-wise work",
           "fp16": "fp16 tensor-core products, f32 accumulation and element-wise work"}
@@ -215,7 +219,9 @@ def run_gpu(args):
                        "l2": "flushed between timed steps by a 256 MiB write outside the events"},
             "median_final_residual": med_res,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
-                         "frac": achieved / peak_tops, "traffic": None,
+                         "frac": achieved / peak_tops,
+                         "traffic": FWD_TRAFFIC_BYTES if (args.form == "fused" and args.precision == "fp32") else None,
+                         "traffic_unit": "DRAM bytes per launch (ncu)",
                          "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x {max_mhz:.0f} MHz "
                                         "(max SM clock of MEASURED_PEAKS.json)",
                          "kernel": "fused_fwd_kernel" if args.form == "fused" else "plain form (several kernels)"},
