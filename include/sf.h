@@ -189,9 +189,9 @@ sf_status sf_set_launch_shape(sf_handle *h, int samples_per_cta, int warps, int 
 /* Options of a handle (sf_set_option). */
 typedef enum {
   /* 1 (default): between full pair tests, the float32 fused forward tests
-   * only the pair rows that were within scaled distance 1.3 at the last full
+   * only the pair rows that were within scaled distance 1.5 at the last full
    * test of the sample; a full test is rerun as soon as the sample's
-   * coefficients may have moved its positions by 0.15 (scaled) or more, in a
+   * coefficients may have moved its positions by 0.25 (scaled) or more, in a
    * bound that holds for every t (Bernstein weights are non-negative and sum
    * to 1); with the workspace block, the workspace rows of robots that were
    * within 0.1 (workspace-scaled) of its boundary are retested likewise. The

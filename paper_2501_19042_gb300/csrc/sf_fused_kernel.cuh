@@ -41,7 +41,7 @@ constexpr unsigned FULL = 0xffffffffu;
 // |M^-1 (p_i(t) - p_i^ref(t))| <= max_k |M^-1 (c_ik - c_ik^ref)|
 // <= sqrt(dim) max_{k,x} |c_ikx - c_ikx^ref| / a_x, so a pair that was not a
 // candidate is still at scaled distance > 1 and inactive.
-constexpr float kPruneMargin = 0.3f;
+constexpr float kPruneMargin = 0.5f;
 constexpr float kPruneCandS2 = (1.0f + kPruneMargin) * (1.0f + kPruneMargin);
 constexpr float kPruneDriftLimit = 0.5f * kPruneMargin - 1e-3f;
 // Workspace rows: a full test records the robots with workspace-scaled
