@@ -137,15 +137,17 @@ FusedPlan plan_fused(int dim, int nmax, int T, const int* nr, const int* ns, int
           if (force_warps > 0 && w != force_warps) continue;
           const double rate = std::min(4.0, w / 2.0);
           const double p_rounds = std::ceil((double)G * nkb / w);
-          const double a_rounds = std::ceil((double)G * tc / (32.0 * w));
           for (int nq = 1; nq <= nkb; ++nq) {
             const size_t smem = fused_smem_bytes(dim, nmax, T, G, tc, nq, bwd, prec);
             if (smem > smem_cap) continue;
             const double c_rounds = std::ceil((double)G * nq / w);
             const double kbq = std::ceil((double)nkb / nq);
-            const double tP = std::max(p_rounds * w * cP_tc / rate, p_rounds * latP);
-            const double tC = std::max(c_rounds * w * (kbq * cC_tc + cU_tc) / rate, c_rounds * kbq * latC);
-            const double per_iter = real_nch * (tP + a_rounds * w * cA_tc / rate + tC) +
+            // issue work counts the units that exist (a last round that
+            // is not full issues less); the latency term counts rounds
+            const double tP = std::max((double)G * nkb * cP_tc / rate, p_rounds * latP);
+            const double tC = std::max((double)G * nq * (kbq * cC_tc + cU_tc) / rate, c_rounds * kbq * latC);
+            const double tA = std::ceil((double)G * tc / 32.0) * cA_tc / rate;
+            const double per_iter = real_nch * (tP + tA + tC) +
                                     (3.0 * real_nch + 2.0) * 400.0 + 24.0 * G * Nbig * dim * 4.0 / rate;
             add_top(FusedPlan{G, w, tc, nq, smem, waves * per_iter});
           }
