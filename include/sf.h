@@ -210,6 +210,18 @@ sf_status sf_set_option(sf_handle *h, int option, int value);
  * the number of time ranges of the contraction phase. */
 sf_status sf_get_launch_shape(const sf_handle *h, int *out4);
 
+/* The launch shape the library's cost model picks for one fused forward
+ * launch group, without a device and without a handle: n_scenes scenes of
+ * n_robots[q] robots and n_samples[q] samples (host arrays; every n_robots[q]
+ * in the same robot-count bucket 1-8, 9-16, 17-24 or 25-32), dim axes, T
+ * time steps, precision an sf_precision, on a GPU with num_sms SMs and
+ * smem_per_block_optin bytes of opt-in shared memory per block. Writes out4
+ * = G, warps, tc, nq (as sf_get_launch_shape) and, when out_smem is not NULL,
+ * the dynamic shared memory per CTA. SF_ERR_INVALID_ARG for bad arguments,
+ * SF_ERR_UNSUPPORTED when no shape fits in shared memory. */
+sf_status sf_plan_launch(int dim, int T, int n_scenes, const int *n_robots, const int *n_samples, int precision,
+                         int num_sms, size_t smem_per_block_optin, int *out4, size_t *out_smem);
+
 /* Measurement-based choice of the fused launch shape for this batch's scene
  * mix: for every launch group (scenes sharing a robot-count bucket) the
  * n_candidates cheapest shapes of the cost model are each run with K_probe

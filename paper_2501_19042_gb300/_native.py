@@ -25,7 +25,7 @@ EXPORTS = ("sf_create", "sf_destroy", "sf_last_error", "sf_workspace_bytes", "sf
            "sf_project_plain_noalloc", "sf_set_launch_shape", "sf_get_launch_shape",
            "sf_project_train", "sf_backward_workspace_bytes", "sf_project_backward",
            "sf_autotune", "sf_graph_capture", "sf_graph_launch", "sf_graph_destroy", "sf_sync_status",
-           "sf_eq_project", "sf_eq_project_backward", "sf_set_option")
+           "sf_eq_project", "sf_eq_project_backward", "sf_set_option", "sf_plan_launch")
 
 
 class SfProblem(C.Structure):
@@ -104,6 +104,10 @@ def load(path: str = LIB_PATH):
         lib.sf_project_backward.restype = C.c_int
         lib.sf_set_option.argtypes = [vp, C.c_int, C.c_int]
         lib.sf_set_option.restype = C.c_int
+        ip = C.POINTER(C.c_int)
+        lib.sf_plan_launch.argtypes = [C.c_int, C.c_int, C.c_int, ip, ip, C.c_int, C.c_int, sz, ip,
+                                       C.POINTER(sz)]
+        lib.sf_plan_launch.restype = C.c_int
         lib.sf_eq_project.argtypes = [vp, vp, C.POINTER(SfBatch), vp]
         lib.sf_eq_project.restype = C.c_int
         lib.sf_eq_project_backward.argtypes = [vp, vp, C.POINTER(SfBatch), vp, vp, vp]

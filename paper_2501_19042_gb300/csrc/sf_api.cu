@@ -963,6 +963,32 @@ sf_status sf_project_plain_noalloc(sf_handle* h, void* stream, const sf_batch* b
                     (size_t)SF_NOALLOC_SCRATCH_BYTES, nullptr);
 }
 
+sf_status sf_plan_launch(int dim, int T, int n_scenes, const int* n_robots, const int* n_samples, int precision,
+                         int num_sms, size_t smem_per_block_optin, int* out4, size_t* out_smem) {
+  if ((dim != 2 && dim != 3) || T < 2 || T > SF_MAX_T || n_scenes < 1 || n_scenes > MAX_SCENES_PER_LAUNCH ||
+      !n_robots || !n_samples || !out4 || num_sms < 1 || precision < SF_PREC_FP32 || precision > SF_PREC_FP16)
+    return SF_ERR_INVALID_ARG;
+  int bk = -1;
+  long long total = 0;
+  for (int q = 0; q < n_scenes; ++q) {
+    if (n_robots[q] < 1 || n_robots[q] > SF_MAX_ROBOTS || n_samples[q] < 0) return SF_ERR_INVALID_ARG;
+    const int b = bucket_index(n_robots[q]);
+    if (bk >= 0 && b != bk) return SF_ERR_INVALID_ARG;   // one robot-count bucket per launch group
+    bk = b;
+    total += n_samples[q];
+  }
+  if (total < 1) return SF_ERR_INVALID_ARG;
+  const FusedPlan p = plan_fused(dim, kBucketNmax[bk], T, n_robots, n_samples, n_scenes, num_sms,
+                                 smem_per_block_optin, 0, 0, 0, false, nullptr, 0, precision);
+  if (p.G == 0) return SF_ERR_UNSUPPORTED;
+  out4[0] = p.G;
+  out4[1] = p.warps;
+  out4[2] = p.tc;
+  out4[3] = p.nq;
+  if (out_smem) *out_smem = p.smem;
+  return SF_OK;
+}
+
 sf_status sf_set_option(sf_handle* h, int option, int value) {
   if (!h) return SF_ERR_INVALID_ARG;
   if (option == SF_OPT_PAIR_PRUNING) {

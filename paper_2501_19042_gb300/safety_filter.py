@@ -33,6 +33,25 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+
+def plan_launch(dim: int, T: int, n_robots, n_samples, precision: str = "fp32", num_sms: int = 152,
+                smem_per_block_optin: int = 232448) -> dict:
+    """``sf_plan_launch``: the fused launch shape the cost model picks for one
+    launch group (scenes in one robot-count bucket), without a device."""
+    lib = nat.load()
+    n = len(n_robots)
+    if n != len(n_samples):
+        raise ValueError("n_robots and n_samples differ in length")
+    nr = (C.c_int * max(n, 1))(*[int(x) for x in n_robots])
+    ns = (C.c_int * max(n, 1))(*[int(x) for x in n_samples])
+    out = (C.c_int * 4)()
+    smem = C.c_size_t(0)
+    code = lib.sf_plan_launch(int(dim), int(T), n, nr, ns, nat.PREC[precision], int(num_sms),
+                              C.c_size_t(smem_per_block_optin), out, C.byref(smem))
+    if code != nat.SF_OK:
+        raise nat.SfError(code, "sf_plan_launch failed")
+    return {"G": out[0], "warps": out[1], "tc": out[2], "nq": out[3], "smem": int(smem.value)}
+
 class SafetyFilter:
     """Handle over ``sf_create`` / ``sf_project`` / ``sf_destroy``."""
 
