@@ -9,7 +9,9 @@
 //    all robots, then every pair (i < j) by the alpha / beta / d closed forms,
 //    q = e - delta accumulated per robot in registers (E_i += q, E_j -= q).
 //    A pair that is inactive on all 32 lanes of a warp is skipped after its
-//    distance test. E_i(t) goes to a shared-memory chunk buffer.
+//    distance test. E_i(t) goes to a shared-memory chunk buffer. With pair
+//    pruning, only the rows recorded as candidates at the last full test
+//    are retested while a drift bound shows the others still inactive.
 //  * contraction phase — one thread per (sample, robot, range of t): the
 //    robot's coefficients in registers, velocity / acceleration and their
 //    ball projections, and the transposed contraction
@@ -19,7 +21,8 @@
 // Then the solve phase: lambda' = lambda + rho g (minus-sign reading),
 // r = rho g + lambda' + xi_bar, robot means, and the xi step
 //   c_i' = W1 c_i + S1 r_i + DW cbar + DS rbar + beta_i
-// with the operators pre-stored from the KKT system.
+// with the operators pre-stored from the KKT system; DW cbar + DS rbar is
+// the same for every robot of a (sample, axis) and formed once for it.
 // After the last iteration one more pass evaluates
 //   ||r_p|| = ||F xi^K - e(xi^{K-1})||  (Eq. primal_residual)
 // row by row as F(xi^K - xi^{K-1}) - q(xi^{K-1}).
