@@ -417,3 +417,70 @@ def test_residual_decreases_on_small_2d(oracle_lib):
     h = out["rp_hist"]
     assert np.all(h[:, -1] < 0.01 * h[:, 0])
     assert np.median(out["rp_final"]) < 2e-3
+
+
+# --- Eq. (primal_residual): the residual outputs ----------------------------------------
+
+def _dense_e(Fx, N, T, dim, a, v_max, a_max):
+    """e(F xi) row by row from the dense F's row order (per axis: pair rows
+    (i < j) x T, velocity rows N x T, acceleration rows N x T), with the
+    Euclidean projections the closed forms reduce to for a == b."""
+    npair = N * (N - 1) // 2
+    R = (npair + 2 * N) * T
+    X = Fx.reshape(dim, R)
+    E = X.copy()
+    viol = -np.inf
+    for blk, (count, kind) in enumerate(((npair, "pair"), (N, "v"), (N, "a"))):
+        off = (0, npair * T, (npair + N) * T)[blk]
+        for r in range(count):
+            for t in range(T):
+                col = off + r * T + t
+                d = X[:, col]
+                nrm = np.linalg.norm(d)
+                if kind == "pair":
+                    E[:, col] = d * max(1.0, a / nrm)
+                    viol = max(viol, a - nrm)
+                else:
+                    bound = v_max if kind == "v" else a_max
+                    E[:, col] = d * min(1.0, bound / nrm)
+                    viol = max(viol, nrm - bound)
+    return E.reshape(-1), viol
+
+
+def test_residual_outputs_match_their_definition(oracle_lib):
+    """rp_hist[k] = ||F xi^{k+1} - e(F xi^k)||, proj_hist[k] = ||F xi^k -
+    e(F xi^k)|| and viol = the largest violation of xi^K, evaluated here with
+    the dense F (pinned against the Kronecker form of the Appendix) and the
+    Euclidean projections, on an instance with active pair, velocity and
+    acceleration rows. Catches a residual paired with the wrong iterate, a
+    dropped block or a wrong norm."""
+    O = oracle_lib
+    N, dim, T, K = 3, 3, 24, 6
+    pb = _problem(O, n_robots=N, dim=dim, T=T, v_max=1.2, a_max=1.5, coll_a=0.8, coll_b=0.8, rho=0.3)
+    st = np.array([[-1.5, 0.1, 0.05], [1.5, -0.1, -0.05], [0.05, -1.6, 0.1]])
+    gl = np.array([[1.5, 0.1, 0.05], [-1.5, -0.1, -0.05], [0.05, 1.6, 0.1]])
+    rng = np.random.default_rng(31)
+    xb = np.zeros((dim, N, 11))
+    for i in range(N):
+        for ax in range(dim):
+            xb[ax, i] = np.linspace(st[i, ax], gl[i, ax], 11)
+    xb = xb.reshape(-1) + rng.normal(size=dim * N * 11) * 0.3
+    sf = O.OracleSF(pb, st, gl)
+    F = sf.dense_F()
+    out = sf.run(xb, K)
+    # the iterates one step at a time (the run is deterministic)
+    xs, lam = [xb.copy()], np.zeros_like(xb)
+    for k in range(K):
+        o = sf.run(xb, 1, xi0=xs[-1], lam0=lam)
+        xs.append(o["xi"])
+        lam = o["lam"]
+    np.testing.assert_allclose(xs[-1], out["xi"], atol=1e-12)
+    n_active = 0
+    for k in range(K):
+        e, _ = _dense_e(F @ xs[k], N, T, dim, 0.8, 1.2, 1.5)
+        n_active += int(np.sum(np.abs(e - F @ xs[k]) > 1e-12))
+        np.testing.assert_allclose(out["proj_hist"][k], np.linalg.norm(F @ xs[k] - e), rtol=1e-10, atol=1e-12)
+        np.testing.assert_allclose(out["rp_hist"][k], np.linalg.norm(F @ xs[k + 1] - e), rtol=1e-10, atol=1e-12)
+    assert n_active > 0
+    _, viol = _dense_e(F @ xs[K], N, T, dim, 0.8, 1.2, 1.5)
+    np.testing.assert_allclose(out["viol"], viol, rtol=1e-10, atol=1e-12)
