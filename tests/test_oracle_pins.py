@@ -484,3 +484,27 @@ def test_residual_outputs_match_their_definition(oracle_lib):
     assert n_active > 0
     _, viol = _dense_e(F @ xs[K], N, T, dim, 0.8, 1.2, 1.5)
     np.testing.assert_allclose(out["viol"], viol, rtol=1e-10, atol=1e-12)
+
+
+def test_batch_driver_equals_single_sample_runs(oracle_lib):
+    """The threaded batch driver (the reference of every GPU parity test)
+    returns, sample by sample and bit for bit, what single-sample runs
+    return: per-sample offsets, initial iterates and history rows are
+    wired correctly, and threads do not share state."""
+    O = oracle_lib
+    spec = si.config_n16_3d(n_robots=5, n_samples=7, T=30, box=(3.0, 3.0, 1.5), min_sep=0.8)
+    sc = si.scene(spec, 17)
+    pb = _problem(O, n_robots=5, T=30, coll_a=spec.coll, coll_b=spec.coll, rho=0.1)
+    K = 12
+    rng = np.random.default_rng(5)
+    x0 = sc.xi_bar + rng.normal(size=sc.xi_bar.shape) * 0.1
+    l0 = rng.normal(size=sc.xi_bar.shape) * 0.05
+    out = O.run_batch(pb, sc.start, sc.goal, sc.xi_bar, K=K, xi0=x0, lam0=l0, hist=True, n_threads=3)
+    sf = O.OracleSF(pb, sc.start, sc.goal)
+    for s in range(sc.xi_bar.shape[0]):
+        one = sf.run(sc.xi_bar[s].reshape(-1), K, xi0=x0[s].reshape(-1), lam0=l0[s].reshape(-1))
+        np.testing.assert_array_equal(out["xi"][s].reshape(-1), one["xi"])
+        np.testing.assert_array_equal(out["lam"][s].reshape(-1), one["lam"])
+        np.testing.assert_array_equal(out["rp_hist"][s], one["rp_hist"])
+        np.testing.assert_array_equal(out["proj_hist"][s], one["proj_hist"])
+        assert out["rp_final"][s] == one["rp_hist"][-1]
