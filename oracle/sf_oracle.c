@@ -588,7 +588,7 @@ int oracle_sf_run(oracle_sf *s, const double *xi_bar, const double *xi0, const d
 }
 
 /* ------------------------------------------------------------------------- */
-/* Batch driver: samples are independent, so they are spread over threads.    */
+/* Batch entry point: samples are independent, so they are spread over threads. */
 /* ------------------------------------------------------------------------- */
 
 typedef struct {

@@ -125,7 +125,7 @@ int oracle_sf_run(oracle_sf *s, const double *xi_bar, const double *xi0, const d
                   int K, double *xi_out, double *lam_out, double *rp_hist,
                   double *proj_hist, double *viol);
 
-/* Batch driver over S independent samples of one scene, on n_threads POSIX
+/* Batch entry point over S independent samples of one scene, on n_threads POSIX
  * threads (each sample gets its own context; arithmetic is unchanged).
  * Arrays are per-sample concatenations of the single-sample layouts. xi0 and
  * lam0 may be NULL. rp_final[s] = rp_hist[K-1] of sample s. */

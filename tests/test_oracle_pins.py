@@ -486,8 +486,8 @@ def test_residual_outputs_match_their_definition(oracle_lib):
     np.testing.assert_allclose(out["viol"], viol, rtol=1e-10, atol=1e-12)
 
 
-def test_batch_driver_equals_single_sample_runs(oracle_lib):
-    """The threaded batch driver (the reference of every GPU parity test)
+def test_batch_run_equals_single_sample_runs(oracle_lib):
+    """The threaded batch entry point (the reference of every GPU parity test)
     returns, sample by sample and bit for bit, what single-sample runs
     return: per-sample offsets, initial iterates and history rows are
     wired correctly, and threads do not share state."""
