@@ -21,9 +21,9 @@
  *  - Compute calls are asynchronous on the caller's stream (passed as a
  *    cudaStream_t cast to void*; NULL is the legacy default stream). No
  *    implicit host synchronisation, except where a function says so.
- *  - Device-side errors (a bounded wait that ran out, non-finite values) are
- *    latched in a device word; sf_sync_status() synchronises the stream and
- *    returns them.
+ *  - Device-side errors (non-finite values) are latched in a device word;
+ *    sf_sync_status() synchronises the stream and returns them. No kernel of
+ *    this build waits on another, so SF_ERR_TIMEOUT is not returned.
  *  - Layouts (row-major, float32 unless stated):
  *      coefficients (xi_bar, xi0, lambda0, xi_out, lambda_out, gradients):
  *        per sample [dim][N][nvar], nvar = order + 1 (the paper's xi vector,
@@ -53,7 +53,7 @@ typedef enum {
   SF_ERR_INVALID_ARG = 1,   /* bad size, shape, pointer or value */
   SF_ERR_CUDA = 2,          /* a CUDA runtime call failed */
   SF_ERR_OOM = 3,           /* handle-owned allocation failed */
-  SF_ERR_TIMEOUT = 4,       /* a bounded device wait ran out */
+  SF_ERR_TIMEOUT = 4,       /* a bounded device wait ran out (reserved) */
   SF_ERR_NONFINITE = 5,     /* a non-finite value reached the output */
   SF_ERR_UNSUPPORTED = 6,   /* valid request this build does not implement */
   SF_ERR_WORKSPACE = 7      /* workspace missing or too small */
