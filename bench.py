@@ -35,7 +35,7 @@ UNIT = "samples/s"
 FP32_LANES_PER_SM = 128
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one float32
 # fused_fwd_kernel launch on the bench workload, from one ncu capture of the
-# current kernel (profiles/fused_fwd_n16_3d_s1024_k200.md): the inputs once
+# current kernel (the forward's summary under profiles/): the inputs once
 FWD_TRAFFIC_BYTES = 2_455_552
 DTYPES = {"fp32": "f32",
           "bf16": "bf16 tensor-core products (three-term), f32 accumulation and element-wise work",

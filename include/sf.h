@@ -265,7 +265,10 @@ void sf_graph_destroy(sf_graph *g);
  *
  * The first call on a device looks up the device address of the buffer
  * (cudaGetSymbolAddress with that device current); make that first call
- * before capturing the stream into a graph. All calls share the one buffer
+ * before capturing the stream into a graph. The address is looked up again
+ * when the device's context has changed since (after cudaDeviceReset); a
+ * handle itself does not survive cudaDeviceReset (its device memory is
+ * gone), so destroy handles before a reset and create new ones after it. All calls share the one buffer
  * and it keeps the last call's contents; every kernel writes each scratch
  * element before reading it, so nothing has to be cleared between calls.
  * Two calls whose work overlaps on the GPU (different streams, or different

@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "sf_internal.cuh"
 
 struct sf_handle {
@@ -923,20 +925,58 @@ namespace {
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SF_NOALLOC_SCRATCH_BYTES];
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
-void* g_noalloc_addr[kMaxDevices] = {};
+struct NoallocSlot {
+  void* addr;                 // device address of the buffer
+  unsigned long long ctx_id;  // id of the context it was looked up in (0: unknown)
+};
+NoallocSlot g_noalloc[kMaxDevices] = {};
+
+// Id of the calling thread's current context, unique for the life of the
+// process (a context created after cudaDeviceReset gets a new one); 0 when
+// the driver does not provide it. The driver calls are reached through the
+// runtime's entry-point table, so the library needs no link to libcuda.
+unsigned long long current_context_id() {
+  typedef CUresult (*GetCurrentFn)(CUcontext*);
+  typedef CUresult (*GetIdFn)(CUcontext, unsigned long long*);
+  static GetCurrentFn get_current = nullptr;
+  static GetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {   // under g_noalloc_mu
+    looked_up = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetIdFn>(f);
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
 
 // Device address of the buffer on h->device (the caller has made that device
-// current). Looked up on the first call per device.
+// current and the runtime has initialised its context). Looked up on the
+// first call per device, and again whenever the current context is not the
+// one of the last lookup (after cudaDeviceReset the old address is stale).
 sf_status noalloc_scratch_address(sf_handle* h, void** out) {
   if (h->device < 0 || h->device >= kMaxDevices) return fail(h, SF_ERR_UNSUPPORTED, "device index too large");
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[h->device]) {
+  NoallocSlot& slot = g_noalloc[h->device];
+  const unsigned long long ctx = current_context_id();
+  if (!slot.addr || ctx == 0 || ctx != slot.ctx_id) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) return cuda_fail(h, e, "device address of the built-in scratch buffer");
-    g_noalloc_addr[h->device] = p;
+    slot.addr = p;
+    slot.ctx_id = ctx;
   }
-  *out = g_noalloc_addr[h->device];
+  *out = slot.addr;
   return SF_OK;
 }
 }  // namespace

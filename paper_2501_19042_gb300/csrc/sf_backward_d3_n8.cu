@@ -1,43 +1,11 @@
 // Adjoint kernel and the mask-writing training forward, instantiated for
 // dim = 3, up to 8 robots.
-#include <cstring>
-
 #include "sf_backward_kernel.cuh"
 
 namespace sf {
 cudaError_t launch_bwd_d3_n8(const FusedArgs& a, const BwdLaunchArgs& b, const FusedLaunch& l,
-                                  cudaStream_t st) {
-  fused_impl::BwdArgs x;
-  std::memset(&x, 0, sizeof(x));
-  x.pc = a.pc;
-  x.n_scenes = a.n_scenes;
-  x.basis = a.basis;
-  x.ops = a.ops;
-  x.start = a.start;
-  x.goal = a.goal;
-  x.start_va = a.start_va;
-  x.goal_va = a.goal_va;
-  x.xi_bar = a.xi_bar;
-  x.ckpt = b.ckpt;
-  x.ck_every = b.ck_every;
-  x.total_coefs = b.total_coefs;
-  x.ring = b.ring;
-  x.tail_mask = b.tail_mask;
-  x.ring_mask = b.ring_mask;
-  x.mask_slot = b.mask_slot;
-  x.g_xi = b.g_xi;
-  x.g_lam = b.g_lam;
-  x.g_fp = b.g_fp;
-  x.gx0 = b.gx0;
-  x.gl0 = b.gl0;
-  x.gxb = b.gxb;
-  x.xi0_is_xi_bar = b.xi0_is_xi_bar;
-  x.tc = l.tc;
-  x.nq = l.nq;
-  x.total_samples = a.total_samples;
-  x.status = a.status;
-  std::memcpy(x.sc, a.sc, sizeof(x.sc));
-  return fused_impl::launch_bwd_t<3, 8, 384>(x, l.n_ctas, l.warps, l.smem, st);
+                             cudaStream_t st) {
+  return fused_impl::launch_bwd_from<3, 8, 384>(a, b, l, st);
 }
 cudaError_t prepare_bwd_d3_n8(int smem) {
   return cudaFuncSetAttribute(fused_impl::fused_bwd_kernel<3, 8, 384>,

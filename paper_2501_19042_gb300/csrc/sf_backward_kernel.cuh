@@ -22,6 +22,7 @@
 // The CTA recomputes each segment of checkpoint_every iterations forward from
 // its checkpoint into a ring in global memory, then walks the segment back.
 #pragma once
+#include <cstring>
 #include "sf_fused_kernel.cuh"
 
 namespace sf {
@@ -491,6 +492,49 @@ cudaError_t launch_bwd_t(const BwdArgs& a, int n_ctas, int warps, size_t smem, c
   if (warps * 32 > MAXT) return cudaErrorInvalidConfiguration;
   k<<<n_ctas, warps * 32, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+// Kernel parameters of the adjoint from the forward's scene table and
+// problem constants plus the backward's own buffers and launch shape.
+inline BwdArgs make_bwd_args(const FusedArgs& a, const BwdLaunchArgs& b, const FusedLaunch& l) {
+  BwdArgs x;
+  std::memset(&x, 0, sizeof(x));
+  x.pc = a.pc;
+  x.n_scenes = a.n_scenes;
+  x.basis = a.basis;
+  x.ops = a.ops;
+  x.start = a.start;
+  x.goal = a.goal;
+  x.start_va = a.start_va;
+  x.goal_va = a.goal_va;
+  x.xi_bar = a.xi_bar;
+  x.ckpt = b.ckpt;
+  x.ck_every = b.ck_every;
+  x.total_coefs = b.total_coefs;
+  x.ring = b.ring;
+  x.tail_mask = b.tail_mask;
+  x.ring_mask = b.ring_mask;
+  x.mask_slot = b.mask_slot;
+  x.g_xi = b.g_xi;
+  x.g_lam = b.g_lam;
+  x.g_fp = b.g_fp;
+  x.gx0 = b.gx0;
+  x.gl0 = b.gl0;
+  x.gxb = b.gxb;
+  x.xi0_is_xi_bar = b.xi0_is_xi_bar;
+  x.tc = l.tc;
+  x.nq = l.nq;
+  x.total_samples = a.total_samples;
+  x.status = a.status;
+  std::memcpy(x.sc, a.sc, sizeof(x.sc));
+  return x;
+}
+
+// Adjoint of one (dim, robot-count bucket): BwdArgs from the forward's
+// arguments, then the launch.
+template <int DIM, int NMAX, int MAXT>
+cudaError_t launch_bwd_from(const FusedArgs& a, const BwdLaunchArgs& b, const FusedLaunch& l, cudaStream_t st) {
+  return launch_bwd_t<DIM, NMAX, MAXT>(make_bwd_args(a, b, l), l.n_ctas, l.warps, l.smem, st);
 }
 
 }  // namespace fused_impl

@@ -1,12 +1,13 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle on the
-same seeded inputs. Float32 path: per-sample relative L2 of xi^K <= 1e-4 and
-final ||r_p|| within 1e-3 (absolute) of the oracle's."""
+same seeded inputs. Float32 path: per-sample relative L2 of xi^K <= 1e-4,
+||lambda^K - lambda_ref|| <= 1e-4 ||xi_ref|| and final ||r_p|| within 1e-3
+(absolute) of the oracle's."""
 import numpy as np
 import pytest
 import torch
 
 import swarm_inputs as si
-from sfcase import RHO_2D, RHO_3D, TOL_RESID_ABS, TOL_XI_REL, rel_l2, run_oracle
+from sfcase import RHO_2D, RHO_3D, TOL_LAM, TOL_RESID_ABS, TOL_XI_REL, lam_err, rel_l2, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -36,12 +37,18 @@ def _gpu_run(P, sc, rho, K, form="fused", idx=None, hist=False, max_robots=None)
     return out
 
 
-def _check(out, ref, tol_xi=TOL_XI_REL, min_pass=1.0):
+def _check(out, ref, tol_xi=TOL_XI_REL, min_pass=1.0, idx=None):
     xi = out.xi.double().cpu().numpy()
+    lam = out.lam.double().cpu().numpy()
+    res = out.residual.double().cpu().numpy()
+    if idx is not None:
+        xi, lam, res = xi[idx], lam[idx], res[idx]
     err = rel_l2(xi, ref["xi"])
-    dres = np.abs(out.residual.double().cpu().numpy() - ref["rp_final"])
+    dres = np.abs(res - ref["rp_final"])
     frac = np.mean(err <= tol_xi)
     assert frac >= min_pass, f"xi rel L2: max {err.max():.3e}, median {np.median(err):.3e}, pass {frac:.3f}"
+    lerr = lam_err(lam, ref["lam"], ref["xi"])
+    assert lerr.max() <= TOL_LAM, f"lambda error max {lerr.max():.3e}, median {np.median(lerr):.3e}"
     assert dres.max() <= TOL_RESID_ABS, f"residual diff max {dres.max():.3e}"
     return err, dres
 
@@ -74,11 +81,7 @@ def test_n16_full_size_sampled(sfmod, oracle_lib):
     out = _gpu_run(sfmod, sc, RHO_3D, 200)
     idx = np.array([0, 1, 137, 300, 511, 700, 901, 1023])
     ref = run_oracle(oracle_lib, sc, RHO_3D, 200, idx=idx)
-    xi = out.xi.double().cpu().numpy()[idx]
-    err = rel_l2(xi, ref["xi"])
-    dres = np.abs(out.residual.double().cpu().numpy()[idx] - ref["rp_final"])
-    assert err.max() <= TOL_XI_REL, err
-    assert dres.max() <= TOL_RESID_ABS, dres
+    _check(out, ref, idx=idx)
     # properties at any size: finite, boundary conditions, residual small
     assert torch.isfinite(out.xi).all() and torch.isfinite(out.residual).all()
     assert float(out.residual.median()) < 1e-3
@@ -99,10 +102,7 @@ def test_n32_t120_full_size_sampled(sfmod, oracle_lib):
     out = _gpu_run(sfmod, sc, RHO_3D, 200)
     idx = np.array([0, 1, 2, 3, 250, 511, 777, 1024, 1500, 1901, 2046, 2047])
     ref = run_oracle(oracle_lib, sc, RHO_3D, 200, idx=idx)
-    err = rel_l2(out.xi.double().cpu().numpy()[idx], ref["xi"])
-    dres = np.abs(out.residual.double().cpu().numpy()[idx] - ref["rp_final"])
-    assert err.max() <= TOL_XI_REL, err
-    assert dres.max() <= TOL_RESID_ABS, dres
+    _check(out, ref, idx=idx)
     assert torch.isfinite(out.xi).all() and torch.isfinite(out.residual).all()
 
 
@@ -136,6 +136,7 @@ def test_ragged_multi_scene_batch(sfmod, oracle_lib):
         out = f.project(_dev(xb), _dev(starts), _dev(goals), 25, n_robots=nr, n_samples=ns, form=form)
         torch.cuda.synchronize()
         xi = out.xi.double().cpu().numpy()
+        lam = out.lam.double().cpu().numpy()
         res = out.residual.double().cpu().numpy()
         c0 = s0 = 0
         for sc in scenes:
@@ -145,6 +146,7 @@ def test_ragged_multi_scene_batch(sfmod, oracle_lib):
                 ref = run_oracle(O, sc, RHO_3D, 25)
                 err = rel_l2(xi[c0:c0 + n].reshape(S, -1), ref["xi"])
                 assert err.max() <= TOL_XI_REL, (N, err)
+                assert lam_err(lam[c0:c0 + n].reshape(S, -1), ref["lam"], ref["xi"]).max() <= TOL_LAM, N
                 assert np.abs(res[s0:s0 + S] - ref["rp_final"]).max() <= TOL_RESID_ABS
             c0 += n
             s0 += S
@@ -235,6 +237,7 @@ def test_ragged_64_scenes_full_size_sampled(sfmod, oracle_lib):
     torch.cuda.synchronize()
     f.sync_status()
     xi = out.xi.double().cpu().numpy()
+    lam = out.lam.double().cpu().numpy()
     res = out.residual.double().cpu().numpy()
     assert np.isfinite(xi).all() and np.isfinite(res).all()
     offs_c = np.cumsum([0] + [s * 3 * n * 11 for n, s in zip(nr, ns)])
@@ -247,6 +250,8 @@ def test_ragged_64_scenes_full_size_sampled(sfmod, oracle_lib):
         ref = run_oracle(oracle_lib, sc, RHO_3D, 150, idx=np.array([smp]))
         got = xi[offs_c[q]:offs_c[q + 1]].reshape(S, -1)[smp:smp + 1]
         assert rel_l2(got, ref["xi"]).max() <= TOL_XI_REL, (q, N)
+        got_l = lam[offs_c[q]:offs_c[q + 1]].reshape(S, -1)[smp:smp + 1]
+        assert lam_err(got_l, ref["lam"], ref["xi"]).max() <= TOL_LAM, (q, N)
         assert abs(res[offs_s[q] + smp] - ref["rp_final"][0]) <= TOL_RESID_ABS
     g.close()
 

@@ -1,17 +1,19 @@
 """Parity of the tensor-core form (bf16 / fp16 operands, float32
 accumulation) with the FP64 oracle on the same seeded inputs: per-sample
-relative L2 of xi^K <= 5e-3 and final ||r_p|| within 1e-3 (absolute) of the
-oracle's. The float32 form's bound (1e-4) is not asked of these modes."""
+relative L2 of xi^K <= 5e-3, ||lambda^K - lambda_ref|| <= 5e-3 ||xi_ref||
+and final ||r_p|| within 1e-3 (absolute) of the oracle's. The float32 form's
+bound (1e-4) is not asked of these modes."""
 import numpy as np
 import pytest
 import torch
 
 import swarm_inputs as si
-from sfcase import RHO_2D, RHO_3D, TOL_RESID_ABS, rel_l2, run_oracle
+from sfcase import RHO_2D, RHO_3D, TOL_RESID_ABS, lam_err, rel_l2, run_oracle
 
 pytestmark = pytest.mark.gpu
 
 TOL_XI_REL_MIXED = 5e-3
+TOL_LAM_MIXED = TOL_XI_REL_MIXED   # lambda in units of ||xi_ref||, as in the float32 tests
 PRECS = ("bf16", "fp16")
 
 
@@ -42,12 +44,15 @@ def _run(P, sc, rho, K, prec, max_robots=None, hist=False):
 
 def _check(out, ref, idx=None):
     xi = out.xi.double().cpu().numpy()
+    lam = out.lam.double().cpu().numpy()
     res = out.residual.double().cpu().numpy()
     if idx is not None:
-        xi, res = xi[idx], res[idx]
+        xi, lam, res = xi[idx], lam[idx], res[idx]
     err = rel_l2(xi, ref["xi"])
     dres = np.abs(res - ref["rp_final"])
     assert err.max() <= TOL_XI_REL_MIXED, f"xi rel L2 max {err.max():.3e} median {np.median(err):.3e}"
+    lerr = lam_err(lam, ref["lam"], ref["xi"])
+    assert lerr.max() <= TOL_LAM_MIXED, f"lambda error max {lerr.max():.3e} median {np.median(lerr):.3e}"
     assert dres.max() <= TOL_RESID_ABS, f"residual diff max {dres.max():.3e}"
     return err, dres
 
@@ -104,6 +109,7 @@ def test_ragged_multi_scene_batch(sfmod, oracle_lib, prec):
                     _dev(np.concatenate([s.goal for s in scenes])), 25, n_robots=nr, n_samples=ns)
     torch.cuda.synchronize()
     xi = out.xi.double().cpu().numpy()
+    lam = out.lam.double().cpu().numpy()
     res = out.residual.double().cpu().numpy()
     c0 = s0 = 0
     for s in scenes:
@@ -112,6 +118,8 @@ def test_ragged_multi_scene_batch(sfmod, oracle_lib, prec):
             ref = run_oracle(oracle_lib, s, RHO_3D, 25)
             err = rel_l2(xi[c0:c0 + n].reshape(s.xi_bar.shape), ref["xi"])
             assert err.max() <= TOL_XI_REL_MIXED, (s.spec.n_robots, err.max())
+            lerr = lam_err(lam[c0:c0 + n].reshape(s.xi_bar.shape), ref["lam"], ref["xi"])
+            assert lerr.max() <= TOL_LAM_MIXED, (s.spec.n_robots, lerr.max())
             assert np.abs(res[s0:s0 + s.spec.n_samples] - ref["rp_final"]).max() <= TOL_RESID_ABS
         c0 += n
         s0 += s.spec.n_samples

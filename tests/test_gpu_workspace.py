@@ -7,7 +7,7 @@ import pytest
 import torch
 
 import swarm_inputs as si
-from sfcase import RHO_2D, RHO_3D, TOL_RESID_ABS, TOL_XI_REL, rel_l2
+from sfcase import RHO_2D, RHO_3D, TOL_RESID_ABS, TOL_XI_REL, lam_err, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -58,9 +58,13 @@ def _scene3(n_robots=16, n_samples=24, T=100, seed=61, ws=WS3):
 
 
 def _check(out, ref, tol):
+    """tol bounds the xi relative L2 and lambda in units of ||xi_ref|| (the
+    tolerance of the mode, as in the other parity tests)."""
     err = rel_l2(out.xi.double().cpu().numpy(), ref["xi"])
     dres = np.abs(out.residual.double().cpu().numpy() - ref["rp_final"])
     assert err.max() <= tol, f"xi rel L2 max {err.max():.3e}"
+    lerr = lam_err(out.lam.double().cpu().numpy(), ref["lam"], ref["xi"])
+    assert lerr.max() <= tol, f"lambda error max {lerr.max():.3e}"
     assert dres.max() <= TOL_RESID_ABS, f"residual diff max {dres.max():.3e}"
 
 

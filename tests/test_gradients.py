@@ -76,6 +76,26 @@ def test_torch_unroll_forward_and_gradient_match_oracle_fd(oracle_lib, ws):
             assert abs(fd - float(g[0][idx])) <= 1e-6 + 1e-5 * abs(fd), (which, idx, fd, float(g[0][idx]))
 
 
+@pytest.mark.parametrize("coll_b", [0.35, 0.8])
+def test_torch_unroll_ellipsoid_matches_oracle(oracle_lib, coll_b):
+    """With unequal collision semi-axes (a, a, b) the FP64 unroll equals the
+    oracle's forward (the literal atan2 / sin / cos closed forms of the
+    alpha / beta / d steps) on an input whose pair rows are active."""
+    O = oracle_lib
+    sc = _instance(N=4, S=2, T=30, seed=5)
+    K = 12
+    P_, Pd_, Pdd_ = O.basis(10, sc.spec.T, sc.spec.t_final)
+    ts = TorchSF(P_, Pd_, Pdd_, sc.start, sc.goal, RHO_3D, sc.spec.coll, coll_b, sc.spec.v_max, sc.spec.a_max)
+    xb = torch.tensor(sc.xi_bar)
+    q0 = ts.project_q(xb)["pair"]
+    assert (q0.abs() > 0).any()
+    xi, lam, _ = ts.unroll(xb.clone(), torch.zeros_like(xb), xb, K)
+    pb = O.Problem(dim=3, n_robots=sc.spec.n_robots, T=sc.spec.T, rho=RHO_3D, coll_a=sc.spec.coll, coll_b=coll_b)
+    ref = O.run_batch(pb, sc.start, sc.goal, sc.xi_bar, K=K)
+    np.testing.assert_allclose(xi.numpy(), ref["xi"], atol=1e-11)
+    np.testing.assert_allclose(lam.numpy(), ref["lam"], atol=1e-11)
+
+
 def _dev(a):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
 
