@@ -7,10 +7,11 @@ init, rho=0.1), inputs resident in HBM. Metric: SF-projected samples/s.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--form fused|plain]
 
-Prints one JSON line (rank 0). Under torchrun each rank runs its own
-1024-sample batch (weak scaling, no collective on the data path); the timed
-region is bracketed by a barrier and a synchronize, and the slowest rank's
-time is reported.
+Prints one JSON line (rank 0). Under torchrun the global batch holds one
+1024-sample scene per rank and is split into contiguous sample ranges
+(sharding.shard_batch), one per rank (weak scaling, no collective on the
+data path); the timed region is bracketed by a barrier and a synchronize,
+and the slowest rank's time is reported.
 """
 from __future__ import annotations
 
@@ -140,12 +141,23 @@ def run_gpu(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     P.build()
     spec = workload_spec()
-    sc = si.scene(spec, 1 + rank)
+    # the global batch: one scene of the workload per rank (seeds 1..world),
+    # split into contiguous sample ranges by shard_batch; each rank projects
+    # its own range with no collective on the data path
+    from paper_2501_19042_gb300.sharding import shard_batch
+    scenes = [si.scene(spec, 1 + q) for q in range(world)]
+    host = lambda arrs: torch.tensor(np.concatenate([np.asarray(a, np.float32).reshape(-1) for a in arrs]))
+    sh = shard_batch(host([s.xi_bar for s in scenes]), host([s.start for s in scenes]).reshape(-1, spec.dim),
+                     host([s.goal for s in scenes]).reshape(-1, spec.dim), [spec.n_robots] * world,
+                     [spec.n_samples] * world, spec.dim, rank, world)
+    assert sh.n_robots == [spec.n_robots] and sh.n_samples == [spec.n_samples]
+    sc = scenes[sh.scenes[0][0]]
     S, K = spec.n_samples, spec.K
     f = P.SafetyFilter(dim=spec.dim, T=spec.T, rho=RHO, coll_a=spec.coll, v_max=spec.v_max, a_max=spec.a_max,
                        max_robots=spec.n_robots, t_final=spec.t_final, precision=args.precision, device=dev.index)
-    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
-    xb, st, gl = t(sc.xi_bar), t(sc.start), t(sc.goal)
+    f.set_tensor_memory(args.tensor_memory)
+    xb = sh.xi_bar.reshape(sc.xi_bar.shape).to(dev)
+    st, gl = sh.start.contiguous().to(dev), sh.goal.contiguous().to(dev)
     stream = torch.cuda.current_stream(dev)
     out = f.project(xb, st, gl, K, form=args.form)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
@@ -239,6 +251,8 @@ def run_gpu(args):
             line["batching"] = batching_timing(P, dev)
         if not args.no_precision:
             line["precision"] = precision_timing(P, dev)
+        if not args.no_init:
+            line["init"] = init_timing(P, dev)
         if not args.no_workspace:
             line["workspace"] = workspace_timing(P, dev)
         if not args.no_sweep:
@@ -306,6 +320,40 @@ def diff_timing(P, dev):
     bwd = timed(lambda: f.project_backward(xb, st, gl, spec.K, ck, grad_xi=g))
     return {"workload": f"3D N={spec.n_robots}, S={spec.n_samples}, T={spec.T}, K={spec.K}, checkpoint every 10",
             "fwd_ms": fwd, "train_fwd_ms": trn, "bwd_ms": bwd, "bwd_over_fwd": bwd / fwd}
+
+
+def init_timing(P, dev, steps: int = 300, eval_scenes: int = 64):
+    """The learned initialisations (Sec. III-C, Eq. NN_loss; Sec. V,
+    initialisation efficacy) on the differentiation workload's shape (3D
+    N=16, T=100, 8 samples per scene): the 3-layer MLP and the paper's
+    PointNet-like network, each trained for `steps` steps of 64 seeded scenes
+    through the differentiable SF (K=50, checkpoint every 10), then the
+    held-out median final ||r_p|| after K=50 for the sample, zero and learned
+    initialisations, and the median projection residual at k = 1, 5, 20, 50."""
+    import torch
+    from paper_2501_19042_gb300 import init_mlp as im
+    spec = si.config_diff(n_samples=8, K=50)
+    sf = P.SafetyFilter(dim=3, T=spec.T, rho=RHO, coll_a=spec.coll, v_max=spec.v_max, a_max=spec.a_max,
+                        max_robots=spec.n_robots, checkpoint_every=10, device=dev.index)
+    out, nets = {}, {}
+    for arch in ("mlp", "pointnet"):
+        torch.manual_seed(0)
+        net = im.make_init_net(arch, spec.n_robots).to(dev)
+        t0 = time.perf_counter()
+        hist = im.train(sf, net, spec, K=spec.K, n_train_scenes=steps * 64, scenes_per_step=64, max_steps=steps)
+        torch.cuda.synchronize()
+        ev = im.evaluate(sf, net, spec, spec.K, n_scenes=eval_scenes)
+        out[arch] = {"train_steps": len(hist), "train_scenes": len(hist) * 64,
+                     "train_seconds": time.perf_counter() - t0, "loss_first": hist[0], "loss_last": hist[-1],
+                     "heldout_median_rp_K50": ev["learned_init"]["median"],
+                     "better_than_sample_init_frac": ev["learned_better_frac"]}
+        out["sample_init_median_rp_K50"] = ev["sample_init"]["median"]
+        out["zero_init_median_rp_K50"] = ev["zero_init"]["median"]
+        nets[arch] = net
+    out["residual_curves_median"] = im.residual_curves(sf, nets, spec, spec.K, n_scenes=eval_scenes, at=(1, 5, 20, 50))
+    out["workload"] = (f"3D N={spec.n_robots}, T={spec.T}, 8 samples per scene, K={spec.K}; held-out "
+                       f"{eval_scenes} scenes ({eval_scenes * 8} samples)")
+    return out
 
 
 def precision_timing(P, dev, n_check: int = 64, steps: int = 3):
@@ -588,11 +636,14 @@ def main():
     ap.add_argument("--form", default="fused", choices=["fused", "plain"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"],
                     help="contraction precision of the timed forward (the metric is quoted in fp32)")
+    ap.add_argument("--tensor-memory", type=int, default=0, choices=[0, 1],
+                    help="1: coefficient-to-state products on tcgen05 tensor cores through TMEM")
     ap.add_argument("--cpu-samples", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--no-batching", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-init", action="store_true")
     ap.add_argument("--no-workspace", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-qp", action="store_true")

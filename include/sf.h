@@ -183,7 +183,11 @@ unsigned long long sf_launch_count(const sf_handle *h);
  * steps per chunk (tc; even in the 16-bit modes). Values <= 0 leave that
  * choice to the library's cost model. Applies to later sf_project calls on
  * the handle; a shape that does not fit in shared memory (or an odd tc in a
- * 16-bit mode) makes them fail with SF_ERR_UNSUPPORTED. */
+ * 16-bit mode) makes them fail with SF_ERR_UNSUPPORTED. With the shape
+ * forced, the order of every reduction follows from the shape and the
+ * robot-count bucket alone, so a sample's results do not depend on which
+ * other scenes and samples share the call (a batch split over ranks gives
+ * the same bits as the whole batch). */
 sf_status sf_set_launch_shape(sf_handle *h, int samples_per_cta, int warps, int time_chunk);
 
 /* Options of a handle (sf_set_option). */
@@ -199,7 +203,18 @@ typedef enum {
    * In the 16-bit modes the retests use float32 positions and the MMA
    * positions are computed only for full tests. No effect in the plain form
    * and the backward's recompute. */
-  SF_OPT_PAIR_PRUNING = 1
+  SF_OPT_PAIR_PRUNING = 1,
+  /* 1: the fused forward of sf_project (no checkpoints) runs its
+   * coefficient-to-state products (positions, velocities and accelerations
+   * of Eq. (poly)) on the tensor cores through tensor memory (tcgen05 MMAs,
+   * the coefficient rows of a CTA's samples as the A operand in TMEM, the
+   * basis rows of a time chunk as the B operand in shared memory, three-term
+   * split of both operands); the operands are tf32 for SF_PREC_FP32 and the
+   * handle's 16-bit type otherwise. F^T of the residual, the projections,
+   * the multiplier and xi steps stay on the float32 lanes. 0 (default): the
+   * float32 form (SF_PREC_FP32) or the warp-MMA form (16-bit modes).
+   * sf_project_train and sf_project_backward are not affected. */
+  SF_OPT_TENSOR_MEMORY = 2
 } sf_option;
 
 /* Sets option `option` of the handle to `value` (for later calls).
@@ -346,6 +361,17 @@ sf_status sf_eq_project_backward(sf_handle *h, void *stream, const sf_batch *bat
 /* Synchronises `stream` and returns any device-side error latched by earlier
  * calls on the handle (SF_ERR_TIMEOUT, SF_ERR_NONFINITE), clearing it. */
 sf_status sf_sync_status(sf_handle *h, void *stream);
+
+/* Measurement, not part of the solver: throughput of the float32-lane pipes
+ * that bound the fused forward, on device `device` (made current for the
+ * call, restored after). Writes fused multiply-adds per second (an FMA
+ * counts once; whole-GPU launch of 8 independent chains per thread, 2048
+ * threads per SM, best of 5 CUDA-event-timed launches), reciprocal square
+ * roots per second (the same on rsqrt), and the clock in MHz at which 128
+ * lanes per SM, one FMA each per cycle, give the measured FMA rate.
+ * Allocates and frees a few kB of device memory; synchronises the device.
+ * SF_ERR_INVALID_ARG for a NULL output, SF_ERR_CUDA on a CUDA error. */
+sf_status sf_lane_peaks(int device, double *fma_per_s, double *mufu_per_s, double *lane_mhz);
 
 #ifdef __cplusplus
 }

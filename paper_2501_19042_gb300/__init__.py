@@ -8,7 +8,7 @@ from .build import build  # noqa: F401
 
 
 def __getattr__(name):
-    if name in ("SafetyFilter", "ProjectResult", "plan_launch"):
+    if name in ("SafetyFilter", "ProjectResult", "plan_launch", "lane_peaks"):
         from . import safety_filter
         return getattr(safety_filter, name)
     raise AttributeError(name)

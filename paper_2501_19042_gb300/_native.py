@@ -25,7 +25,8 @@ EXPORTS = ("sf_create", "sf_destroy", "sf_last_error", "sf_workspace_bytes", "sf
            "sf_project_plain_noalloc", "sf_set_launch_shape", "sf_get_launch_shape",
            "sf_project_train", "sf_backward_workspace_bytes", "sf_project_backward",
            "sf_autotune", "sf_graph_capture", "sf_graph_launch", "sf_graph_destroy", "sf_sync_status",
-           "sf_eq_project", "sf_eq_project_backward", "sf_set_option", "sf_plan_launch")
+           "sf_eq_project", "sf_eq_project_backward", "sf_set_option", "sf_plan_launch",
+           "sf_lane_peaks")
 
 
 class SfProblem(C.Structure):
@@ -123,6 +124,9 @@ def load(path: str = LIB_PATH):
         lib.sf_graph_destroy.restype = None
         lib.sf_sync_status.argtypes = [vp, vp]
         lib.sf_sync_status.restype = C.c_int
+        dp = C.POINTER(C.c_double)
+        lib.sf_lane_peaks.argtypes = [C.c_int, dp, dp, dp]
+        lib.sf_lane_peaks.restype = C.c_int
         _lib = lib
         return lib
 

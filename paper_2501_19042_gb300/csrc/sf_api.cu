@@ -28,6 +28,7 @@ struct sf_handle {
   std::map<std::string, sf::FusedPlan> tuned;      // autotuned shapes per launch-group key
   bool use_tuned = true;
   int prune = 1;                                   // SF_OPT_PAIR_PRUNING
+  int tm = 0;                                      // SF_OPT_TENSOR_MEMORY
   cudaStream_t aux[2] = {nullptr, nullptr};        // extra streams for concurrent launch groups
   cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
   float eq_pi[sf::NV * sf::NV] = {};               // QP layer operators (host copy of slot 0)
@@ -132,6 +133,15 @@ struct FusedRequest {
   int prec = 0;             // forward only: 0 float32 form, 1 / 2 tensor-core form
   BwdLaunchArgs bwd{};
 };
+
+// Form code of a fused forward launch (FusedLaunch::prec): the handle's
+// precision, moved to the tensor-memory form when that option is on and the
+// call writes no checkpoints (the training forward and the adjoint are the
+// float32 form's).
+int forward_form(const sf_handle* h, bool checkpoints) {
+  const int p = h->pb.precision;
+  return (h->tm && !checkpoints) ? PREC_TM_TF32 + p : p;
+}
 
 long long total_coefs(const sf_handle* h, const sf_batch* b) {
   long long c = 0;
@@ -509,7 +519,7 @@ sf_status sf_project(sf_handle* h, void* stream, const sf_batch* b, int K, int f
   rq.resid_out = resid_out;
   rq.hist = resid_hist;
   rq.ckpt = reinterpret_cast<float*>(checkpoints);
-  rq.prec = h->pb.precision;
+  rq.prec = forward_form(h, checkpoints != nullptr);
   if (checkpoints && h->pb.checkpoint_every <= 0)
     return fail(h, SF_ERR_INVALID_ARG, "checkpoints need a handle with checkpoint_every > 0");
   if (checkpoints && h->pb.precision != SF_PREC_FP32)
@@ -679,7 +689,7 @@ sf_status sf_autotune(sf_handle* h, void* stream, const sf_batch* b, int K_probe
   rq.xi_out = xi_out;
   rq.lam_out = lam_out;
   rq.resid_out = resid_out;
-  rq.prec = h->pb.precision;
+  rq.prec = forward_form(h, false);
   const int fG = h->force_G, fW = h->force_warps, fT = h->force_tc;
   h->force_G = h->force_warps = h->force_tc = 0;
   h->use_tuned = false;
@@ -1034,6 +1044,11 @@ sf_status sf_set_option(sf_handle* h, int option, int value) {
   if (option == SF_OPT_PAIR_PRUNING) {
     if (value != 0 && value != 1) return fail(h, SF_ERR_INVALID_ARG, "SF_OPT_PAIR_PRUNING takes 0 or 1");
     h->prune = value;
+    return SF_OK;
+  }
+  if (option == SF_OPT_TENSOR_MEMORY) {
+    if (value != 0 && value != 1) return fail(h, SF_ERR_INVALID_ARG, "SF_OPT_TENSOR_MEMORY takes 0 or 1");
+    h->tm = value;
     return SF_OK;
   }
   return fail(h, SF_ERR_INVALID_ARG, "unknown option");

@@ -4,7 +4,7 @@
 #include <algorithm>
 #include <cmath>
 
-#include "sf_fused_kernel.cuh"
+#include "sf_tm_kernel.cuh"
 
 namespace sf {
 
@@ -19,8 +19,14 @@ namespace sf {
 SF_DECL(2, 8) SF_DECL(2, 16) SF_DECL(2, 24) SF_DECL(2, 32) SF_DECL(3, 8) SF_DECL(3, 16) SF_DECL(3, 24) SF_DECL(3, 32)
 SF_DECL_TC(2, 8) SF_DECL_TC(2, 16) SF_DECL_TC(2, 24) SF_DECL_TC(2, 32)
 SF_DECL_TC(3, 8) SF_DECL_TC(3, 16) SF_DECL_TC(3, 24) SF_DECL_TC(3, 32)
+#define SF_DECL_TM(D, NM) \
+  cudaError_t launch_tm_d##D##_n##NM(const FusedArgs&, const FusedLaunch&, cudaStream_t); \
+  cudaError_t prepare_tm_d##D##_n##NM(int, int);
+SF_DECL_TM(2, 8) SF_DECL_TM(2, 16) SF_DECL_TM(2, 24) SF_DECL_TM(2, 32)
+SF_DECL_TM(3, 8) SF_DECL_TM(3, 16) SF_DECL_TM(3, 24) SF_DECL_TM(3, 32)
 #undef SF_DECL
 #undef SF_DECL_TC
+#undef SF_DECL_TM
 #define SF_PREP(D, NM) cudaError_t prepare_fused_d##D##_n##NM(int); cudaError_t prepare_bwd_d##D##_n##NM(int); \
   cudaError_t prepare_fused_train_d##D##_n##NM(int); \
   cudaError_t prepare_fused_tc1_d##D##_n##NM(int); cudaError_t prepare_fused_tc2_d##D##_n##NM(int);
@@ -47,6 +53,14 @@ cudaError_t prepare_kernels(int dim, int smem, int prec) {
     chk(prepare_fused_tc2_d2_n8(smem)); chk(prepare_fused_tc2_d2_n16(smem)); chk(prepare_fused_tc2_d2_n24(smem));
     chk(prepare_fused_tc2_d2_n32(smem));
   }
+  // tensor-memory form with the handle's operand format (tf32 for float32)
+  if (dim == 3) {
+    chk(prepare_tm_d3_n8(smem, prec)); chk(prepare_tm_d3_n16(smem, prec)); chk(prepare_tm_d3_n24(smem, prec));
+    chk(prepare_tm_d3_n32(smem, prec));
+  } else {
+    chk(prepare_tm_d2_n8(smem, prec)); chk(prepare_tm_d2_n16(smem, prec)); chk(prepare_tm_d2_n24(smem, prec));
+    chk(prepare_tm_d2_n32(smem, prec));
+  }
   if (dim == 3) {
     chk(prepare_fused_d3_n8(smem)); chk(prepare_fused_d3_n16(smem)); chk(prepare_fused_d3_n24(smem));
     chk(prepare_fused_d3_n32(smem));
@@ -68,7 +82,8 @@ cudaError_t prepare_kernels(int dim, int smem, int prec) {
 int fused_max_warps(int nmax, bool bwd) { return (bwd && nmax > 16) ? 8 : 12; }
 
 size_t fused_smem_bytes(int dim, int nmax, int T, int gmax, int tc, int nq, bool bwd, int prec) {
-  const fused_impl::Lay L(dim, nmax, T, tc, nq, bwd, prec != 0, !bwd);
+  const bool tm = prec >= PREC_TM_TF32;
+  const fused_impl::Lay L(dim, nmax, T, tc, nq, bwd, prec == 1 || prec == 2, !bwd, tm ? prec - PREC_TM_TF32 : -1);
   return sizeof(float) * ((size_t)L.head + (size_t)gmax * L.SB);
 }
 
@@ -123,6 +138,42 @@ FusedPlan plan_fused(int dim, int nmax, int T, const int* nr, const int* ns, int
     long long ctas = 0;
     for (int q = 0; q < n_scenes; ++q) ctas += (ns[q] + std::min(G, std::max(ns[q], 1)) - 1) / std::min(G, std::max(ns[q], 1));
     const double waves = std::ceil((double)ctas / num_sms);
+    if (prec >= PREC_TM_TF32) {
+      // tensor-memory form: G (sample, robot) rows in the 128 TMEM lanes,
+      // warps in groups of four (one per lane quarter), one partial of F^T q
+      // per group, time chunks within the TMEM columns (the velocity and
+      // acceleration states of a chunk beside the coefficient operand)
+      if (G * nmax > 128) continue;
+      const int fmt = prec - PREC_TM_TF32;
+      int prev_tc = 0;
+      for (int nch = 1; nch <= 8; ++nch) {
+        const int tc = (T + nch - 1) / nch;
+        if (tc == prev_tc) continue;
+        prev_tc = tc;
+        if (fused_impl::tm_cols(dim, tc, fmt) > 512) continue;
+        if (force_tc > 0 && tc != force_tc) continue;
+        const int real_nch = (T + tc - 1) / tc;
+        const int nb = (tc + 7) / 8;
+        for (int w = 8; w <= maxw; w += 4) {
+          if (force_warps > 0 && w != force_warps) continue;
+          const int ncg = w / 4;
+          const size_t smem = fused_smem_bytes(dim, nmax, T, G, tc, ncg, bwd, prec);
+          if (smem + TM_STATIC_SMEM_RESERVE > smem_cap) continue;
+          const double rate = std::min(4.0, w / 2.0);
+          // TMEM pass: every warp walks its 8-step blocks (about 22 issue
+          // slots per step: two ball tests, the E flag, votes), issue-bound
+          // over the CTA or latency-bound per warp
+          const double rounds = std::ceil((double)nb / ncg);
+          const double tPass = std::max(4.0 * ncg * rounds * 8.0 * 22.0 / rate, rounds * 8.0 * 22.0 * 2.0);
+          const double a_rounds = std::ceil((double)G * tc / (32.0 * w));
+          const double tPair = a_rounds * w * cA / rate;
+          const double per_iter = real_nch * (tPass + tPair) + (2.0 * real_nch + 3.0) * 400.0 +
+                                  24.0 * G * Nbig * dim * 4.0 / rate;
+          add_top(FusedPlan{G, w, tc, ncg, smem, waves * per_iter});
+        }
+      }
+      continue;
+    }
     if (prec != 0) {
       int prev_tc = 0;
       for (int nch = 1; nch <= 6; ++nch) {
@@ -161,7 +212,11 @@ FusedPlan plan_fused(int dim, int nmax, int T, const int* nr, const int* ns, int
       for (int w = 4; w <= maxw; ++w) {
         if (force_warps > 0 && w != force_warps) continue;
         const int nthr = 32 * w;
-        const int nq = std::max(1, std::min(tc, nthr / std::max(1, G * Nbig)));
+        // a forced shape fixes the reduction order of F^T q for every batch
+        // of the bucket: the time ranges follow from the bucket size then,
+        // not from the batch's largest swarm
+        const int nbase = (force_G > 0 || force_warps > 0 || force_tc > 0) ? nmax : Nbig;
+        const int nq = std::max(1, std::min(tc, nthr / std::max(1, G * nbase)));
         const size_t smem = fused_smem_bytes(dim, nmax, T, G, tc, nq, bwd);
         if (smem > smem_cap) continue;
         const int real_nch = (T + tc - 1) / tc;
@@ -196,6 +251,13 @@ cudaError_t launch_backward(const FusedArgs& a, const BwdLaunchArgs& b, const Fu
 
 cudaError_t launch_fused(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st) {
   const int dim = a.pc.dim;
+  if (l.prec >= PREC_TM_TF32) {
+#define SF_TM(D, NM) \
+  if (dim == D && l.nmax == NM) return launch_tm_d##D##_n##NM(a, l, st);
+    SF_TM(3, 8) SF_TM(3, 16) SF_TM(3, 24) SF_TM(3, 32) SF_TM(2, 8) SF_TM(2, 16) SF_TM(2, 24) SF_TM(2, 32)
+#undef SF_TM
+    return cudaErrorInvalidValue;
+  }
   if (l.prec != 0) {
 #define SF_TC(P, D, NM) \
   if (l.prec == P && dim == D && l.nmax == NM) return launch_fused_tc##P##_d##D##_n##NM(a, l, st);

@@ -54,6 +54,30 @@ constexpr float kWsMargin = 0.1f;
 constexpr float kWsCandS2 = (1.0f - kWsMargin) * (1.0f - kWsMargin);
 constexpr float kWsDriftLimit = kWsMargin - 1e-3f;
 
+// ---- tensor-memory form: sizes ------------------------------------------
+// Per time chunk the velocity / acceleration products run as M = 128 MMAs
+// (rows = (sample, robot) of the CTA, columns = time steps of the chunk,
+// padded to TCW = a multiple of 16) for Pd, Pdd and every axis, A = the
+// coefficient rows in TMEM (rounded and remainder copies of 16 k), B =
+// per-chunk basis tables in shared memory. Operand format 0: tf32 (K = 8
+// per instruction, tables of 12 k per row, three 128-byte core matrices per
+// 8 rows); 1 / 2: bf16 / fp16 (K = 16, two core matrices per 8 rows).
+constexpr int TM_TABLES = 4;   // Pd, Pdd; rounded and remainder
+__host__ __device__ constexpr int tm_tcw(int tc) { return (tc + 15) / 16 * 16; }
+__host__ __device__ constexpr int tm_ka(int fmt) { return fmt == 0 ? 16 : 8; }
+__host__ __device__ constexpr int tm_sbo(int fmt) { return fmt == 0 ? 384 : 256; }
+// TMEM columns: the states [2][dim][TCW], then A [dim][2][KA]
+__host__ __device__ constexpr int tm_cols(int dim, int tc, int fmt) { return 2 * dim * tm_tcw(tc) + 2 * dim * tm_ka(fmt); }
+__host__ __device__ constexpr int tm_alloc_cols(int cols) {
+  return cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
+}
+// Bytes of one B table: chunk c's rows at c * TCW, plus one zero 8-row group
+// (the tf32 form's second K step reads one core matrix past a group; the
+// coefficients' k >= 11 are zero, so any finite value there adds nothing).
+__host__ __device__ constexpr int tm_tab_bytes(int T, int tc, int fmt) {
+  return ((T + tc - 1) / tc * tm_tcw(tc) / 8 + 1) * tm_sbo(fmt);
+}
+
 // Shared-memory layout (floats). Head, float32 form: basis [T][36],
 // operators, beta. Head, tensor-core form: the basis as 16-bit operand
 // tables BN [T][3][4][4] words (rows of P, Pd, Pdd by time step: per lane
@@ -80,10 +104,13 @@ struct Lay {
   int C, LAM, XIB, PG, MC, MR, EB, RS2, RSB, FPP, FPR, XB, LB, GXB, U, CW, CF, CR, CM, WC, RF, CMW, SB;
   int head, TH, bno, bto, opso, betao;
   __host__ __device__ Lay(int dim_, int nmax_, int T_, int TC_, int NQ_, bool bwd = false, bool tcm = false,
-                          bool cand = false) {
+                          bool cand = false, int tmp = -1) {
     dim = dim_; nmax = nmax_; T = T_; TC = TC_; NQ = NQ_;
     RS = dim * NP;
-    EP = nmax * dim + (tcm ? 4 : 1);
+    // tmp >= 0: tensor-memory form with operand format tmp (0 tf32, 1 bf16,
+    // 2 fp16): chunk-buffer rows as in the tensor-core form (positions
+    // first, 16-byte aligned, the active-pair flag at NMAX * DIM)
+    EP = nmax * dim + ((tcm || tmp >= 0) ? 4 : 1);
     C = 0;
     LAM = C + nmax * RS;
     XIB = LAM + nmax * RS;
@@ -114,7 +141,11 @@ struct Lay {
     SB = RF + (cand ? 4 : 0);
     TH = (T + 1) / 2;
     bno = 0;
-    if (tcm) {
+    if (tmp >= 0) {
+      // the MMA B tables (Pd, Pdd; rounded and remainder)
+      bto = 0;
+      opso = TM_TABLES * tm_tab_bytes(T, TC, tmp) / 4;
+    } else if (tcm) {
       bto = T * 48;
       opso = bto + ((6 * NV * TH + 3) / 4) * 4;
     } else {
@@ -299,7 +330,10 @@ __device__ __forceinline__ void ws_row(const float (&ps)[DIM], float (&Ei)[DIM],
 // accumulated in the row; otherwise every sample gets a full test, records
 // its candidates and (in the first chunk) copies C to the reference
 // coefficients.
-template <int DIM, int NMAX, bool TCM = false, bool MASKS = false, bool CAND = false>
+// FLAG (default: as TCM) writes the row's active-pair flag and stores the
+// row in 16-byte pieces (rows of NMAX*DIM + 4 floats) without the positions
+// being pre-staged (the tensor-memory form).
+template <int DIM, int NMAX, bool TCM = false, bool MASKS = false, bool CAND = false, bool FLAG = TCM>
 __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G, int N, int t0, int TCc,
                            const ProblemConsts& pc, bool want_res, int warp, int nwarps, int lane,
                            unsigned* mk = nullptr, bool prune = false) {
@@ -632,8 +666,8 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
       float* eb = blk + L.EB + tl * L.EP;
       if (e_in_row) {
         // candidate path: E is already in the row
-        if (TCM) eb[NMAX * DIM] = res2 > 0.0f ? 1.0f : 0.0f;
-      } else if (TCM) {
+        if (FLAG) eb[NMAX * DIM] = res2 > 0.0f ? 1.0f : 0.0f;
+      } else if (FLAG) {
         // whole row in 16-byte stores (E of robots >= N is zero); the row
         // stride is a multiple of 4 floats, scalar stores would conflict
         float Ef[NMAX * DIM];
@@ -1196,8 +1230,8 @@ struct Cta {
   uint32_t *BN, *BT;
   int tid, nthr, warp, lane, nwarps;
   __device__ Cta(const SceneDesc* sc, int n_scenes, int T, int tc, int nq, bool bwd, float* sm, bool tcm = false,
-                 bool cand = false)
-      : L(DIM, NMAX, T, tc, nq, bwd, tcm, cand) {
+                 bool cand = false, int tmp = -1)
+      : L(DIM, NMAX, T, tc, nq, bwd, tcm, cand, tmp) {
     int sidx = 0;
     for (int q = 1; q < n_scenes; ++q) {
       if (sc[q].cta_begin <= (int)blockIdx.x) sidx = q;
@@ -1212,7 +1246,7 @@ struct Cta {
     per_sample = (long long)DIM * N * NV;
     coef0 = sc[sidx].coef_off + (long long)s_first * per_sample;
     mask0 = sc[sidx].mask_off + (long long)s_first * T * mask_words(NMAX);
-    BASIS = tcm ? nullptr : sm;
+    BASIS = (tcm || tmp >= 0) ? nullptr : sm;
     BN = tcm ? reinterpret_cast<uint32_t*>(sm + L.bno) : nullptr;
     BT = tcm ? reinterpret_cast<uint32_t*>(sm + L.bto) : nullptr;
     OPS = sm + L.opso;
@@ -1264,7 +1298,9 @@ __device__ void tc_tables(const Lay& L, int T, const float* gb, uint32_t* BN, ui
   }
 }
 
-// Basis table, operators of this N and beta_i = R1 b_i + (R0 - R1) bbar.
+// Basis table (PREC 0: float32 copy; 1 / 2: 16-bit operand tables of the
+// warp-MMA form; 3: none), operators of this N and
+// beta_i = R1 b_i + (R0 - R1) bbar.
 template <int DIM, int NMAX, int PREC = 0>
 __device__ void prologue(const Cta<DIM, NMAX>& c, int T, const float4* basis, const float* ops,
                          const float* start, const float* goal, const float* start_va, const float* goal_va) {
@@ -1273,9 +1309,9 @@ __device__ void prologue(const Cta<DIM, NMAX>& c, int T, const float4* basis, co
     const float4* b4 = basis;
     float4* s4 = reinterpret_cast<float4*>(c.BASIS);
     for (int v = c.tid; v < T * 9; v += c.nthr) s4[v] = b4[v];
-  } else {
+  } else if constexpr (PREC == 1 || PREC == 2) {
     tc_tables<PREC>(c.L, T, reinterpret_cast<const float*>(basis), c.BN, c.BT, c.tid, c.nthr);
-  }
+  }   // PREC 3: the tensor-memory form builds its own tables
   const float* gops = ops + (size_t)c.N * OPS_STRIDE;
   for (int v = c.tid; v < 4 * NV * NP; v += c.nthr) c.OPS[v] = gops[v];
   const int N = c.N;
@@ -1366,47 +1402,20 @@ __device__ __forceinline__ bool cta_refresh(const Cta<DIM, NMAX>& c, const Lay& 
   return false;
 }
 
-// One iteration of f_FP on every sample of the CTA (time chunks, then the
-// lambda step and the xi step). keep_prev stores xi^k in the EB region for
-// the final residual. fp (when set) adds ||z^{k+1} - z^k||^2 per sample to FPR.
-template <int DIM, int NMAX, int PREC = 0, bool MASKS = false, bool CAND = false>
-__device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, const float* xi_bar, int it,
-                              bool keep_prev, float* hist, int total_samples, bool fp, unsigned* mslot = nullptr,
-                              bool prune = false, const float* gbasis = nullptr) {
+// Solve phase 1 of one iteration on every sample of the CTA: the lambda step
+// lambda' = lambda + rho g (minus-sign reading of Eq. lambda_step), r = rho g +
+// lambda' + xi_bar (kept in PG, partial 0), the robot means and the xi step's
+// mean term DW mean(c) + DS mean(r) per (sample, axis) in MR, the history
+// entry and (fp) the lambda part of ||z^{k+1} - z^k||^2.
+template <int DIM, int NMAX, bool CAND>
+__device__ void solve_lambda_means(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, int it, float* hist,
+                                   int total_samples, bool fp) {
   constexpr int RS = DIM * NP;
   const Lay& L = c.L;
-  const int T = pc.T, N = c.N, G = c.G, TC = L.TC;
+  const int T = pc.T, N = c.N, G = c.G;
   const bool want_res = hist != nullptr;
   const float rho = pc.rho;
   const float invN = 1.0f / (float)N;
-  for (int t0 = 0; t0 < T; t0 += TC) {
-    const int TCc = min(TC, T - t0);
-    if constexpr (PREC != 0) {
-      // the positions from the MMAs are needed only by a full pair test
-      if (!CAND || cta_refresh<DIM>(c, L, pc, prune)) {
-        tc_positions_phase<DIM, NMAX, PREC>(c.SAMP, L, c.BN, G, N, t0, TCc, pc, c.warp, c.nwarps, c.lane);
-        __syncthreads();
-      }
-      pair_phase<DIM, NMAX, true, false, CAND>(c.SAMP, L, gbasis, G, N, t0, TCc, pc, want_res, c.warp, c.nwarps,
-                                               c.lane, nullptr, prune);
-      __syncthreads();
-      tc_contract_phase<DIM, NMAX, PREC>(c.SAMP, L, c.BN, c.BT, G, N, t0, TCc, t0 == 0, pc, want_res, c.warp,
-                                         c.nwarps, c.lane);
-    } else if (MASKS && mslot != nullptr) {
-      unsigned* mk = mslot + c.mask0;
-      pair_phase<DIM, NMAX, false, true, CAND>(c.SAMP, L, c.BASIS, G, N, t0, TCc, pc, want_res, c.warp, c.nwarps,
-                                               c.lane, mk, prune);
-      __syncthreads();
-      contract_phase<DIM, NMAX, true>(c.SAMP, L, c.BASIS, G, N, t0, TCc, t0 == 0, pc, want_res, c.tid, c.nthr,
-                                      mk);
-    } else {
-      pair_phase<DIM, NMAX, false, false, CAND>(c.SAMP, L, c.BASIS, G, N, t0, TCc, pc, want_res, c.warp,
-                                                c.nwarps, c.lane, nullptr, prune);
-      __syncthreads();
-      contract_phase<DIM>(c.SAMP, L, c.BASIS, G, N, t0, TCc, t0 == 0, pc, want_res, c.tid, c.nthr);
-    }
-    __syncthreads();
-  }
   // ---- solve phase 1: lambda step, r, robot means, and the mean term of
   // the xi step (and the history entry). Lanes (s, x, k) with k padded to 16,
   // so that the 11 k of one (s, x) share a half-warp: after the robot loop
@@ -1486,64 +1495,122 @@ __device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, 
       }
     }
   }
+}
+
+// Solve phase 2 for one coefficient row (sample s, robot i, axis x): the xi
+// step xi_i = W1 c_i + S1 r_i + (DW mean(c) + DS mean(r)) + beta_i with the
+// operators pre-stored from the KKT system (Eq. xi_step). Writes the new row
+// to C (and the old one to the EB region when keep_prev), raises the
+// sample's drift word (pair pruning) and (fp) records ||xi' - xi||^2 of the
+// row; out receives the new row (entry NV zero).
+template <int DIM, int NMAX, bool CAND>
+__device__ __forceinline__ void xi_step_row(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, int s, int i, int x,
+                                            bool keep_prev, bool fp, float (&out)[NP]) {
+  constexpr int RS = DIM * NP;
+  const Lay& L = c.L;
+  float* blk = c.blk(s);
+  const int o = i * RS + x * NP;
+  float cc[NP], r[NP], mt[NP];
+  const float4* c4 = reinterpret_cast<const float4*>(blk + L.C + o);
+  const float4* r4 = reinterpret_cast<const float4*>(blk + L.PG + o);
+  const float4* mt4 = reinterpret_cast<const float4*>(blk + L.MR + x * NP);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const float4 a = c4[q], b = r4[q], e = mt4[q];
+    cc[4 * q] = a.x; cc[4 * q + 1] = a.y; cc[4 * q + 2] = a.z; cc[4 * q + 3] = a.w;
+    r[4 * q] = b.x; r[4 * q + 1] = b.y; r[4 * q + 2] = b.z; r[4 * q + 3] = b.w;
+    mt[4 * q] = e.x; mt[4 * q + 1] = e.y; mt[4 * q + 2] = e.z; mt[4 * q + 3] = e.w;
+  }
+  float dx2 = 0.0f;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    float w1[NV], s1[NV];
+    row_from(c.OPS + OPS_W1 + k * NP, w1);
+    row_from(c.OPS + OPS_S1 + k * NP, s1);
+    float a0 = c.BETA[o + k] + mt[k], a1 = 0.0f;
+#pragma unroll
+    for (int m = 0; m < NV; ++m) {
+      a0 = fmaf(w1[m], cc[m], a0);
+      a1 = fmaf(s1[m], r[m], a1);
+    }
+    const float acc = a0 + a1;
+    out[k] = acc;
+    dx2 = fmaf(acc - cc[k], acc - cc[k], dx2);
+  }
+  out[NV] = 0.0f;
+  if constexpr (CAND) {
+    // drift of this coefficient row from the reference, in scaled units
+    const float inv = x == 2 ? pc.inv_b : pc.inv_a;
+    float d = 0.0f;
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const float e = fabsf(out[k] - blk[L.CR + o + k]) * inv;
+      d = fmaxf(d, e);
+      bad |= !(e == e);
+    }
+    atomicMax(reinterpret_cast<int*>(blk + L.RF), __float_as_int(bad ? INFINITY : d));
+  }
+  float4* o4 = reinterpret_cast<float4*>(blk + L.C + o);
+  float4* p4 = reinterpret_cast<float4*>(blk + L.EB + o);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    if (keep_prev) p4[q] = make_float4(cc[4 * q], cc[4 * q + 1], cc[4 * q + 2], cc[4 * q + 3]);
+    o4[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+  }
+  if (fp) blk[L.FPP + DIM * NV + i * DIM + x] = dx2;
+}
+
+// One iteration of f_FP on every sample of the CTA (time chunks, then the
+// lambda step and the xi step). keep_prev stores xi^k in the EB region for
+// the final residual. fp (when set) adds ||z^{k+1} - z^k||^2 per sample to FPR.
+template <int DIM, int NMAX, int PREC = 0, bool MASKS = false, bool CAND = false>
+__device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, const float* xi_bar, int it,
+                              bool keep_prev, float* hist, int total_samples, bool fp, unsigned* mslot = nullptr,
+                              bool prune = false, const float* gbasis = nullptr) {
+  constexpr int RS = DIM * NP;
+  const Lay& L = c.L;
+  const int T = pc.T, N = c.N, G = c.G, TC = L.TC;
+  const bool want_res = hist != nullptr;
+  const float rho = pc.rho;
+  const float invN = 1.0f / (float)N;
+  for (int t0 = 0; t0 < T; t0 += TC) {
+    const int TCc = min(TC, T - t0);
+    if constexpr (PREC != 0) {
+      // the positions from the MMAs are needed only by a full pair test
+      if (!CAND || cta_refresh<DIM>(c, L, pc, prune)) {
+        tc_positions_phase<DIM, NMAX, PREC>(c.SAMP, L, c.BN, G, N, t0, TCc, pc, c.warp, c.nwarps, c.lane);
+        __syncthreads();
+      }
+      pair_phase<DIM, NMAX, true, false, CAND>(c.SAMP, L, gbasis, G, N, t0, TCc, pc, want_res, c.warp, c.nwarps,
+                                               c.lane, nullptr, prune);
+      __syncthreads();
+      tc_contract_phase<DIM, NMAX, PREC>(c.SAMP, L, c.BN, c.BT, G, N, t0, TCc, t0 == 0, pc, want_res, c.warp,
+                                         c.nwarps, c.lane);
+    } else if (MASKS && mslot != nullptr) {
+      unsigned* mk = mslot + c.mask0;
+      pair_phase<DIM, NMAX, false, true, CAND>(c.SAMP, L, c.BASIS, G, N, t0, TCc, pc, want_res, c.warp, c.nwarps,
+                                               c.lane, mk, prune);
+      __syncthreads();
+      contract_phase<DIM, NMAX, true>(c.SAMP, L, c.BASIS, G, N, t0, TCc, t0 == 0, pc, want_res, c.tid, c.nthr,
+                                      mk);
+    } else {
+      pair_phase<DIM, NMAX, false, false, CAND>(c.SAMP, L, c.BASIS, G, N, t0, TCc, pc, want_res, c.warp,
+                                                c.nwarps, c.lane, nullptr, prune);
+      __syncthreads();
+      contract_phase<DIM>(c.SAMP, L, c.BASIS, G, N, t0, TCc, t0 == 0, pc, want_res, c.tid, c.nthr);
+    }
+    __syncthreads();
+  }
+  solve_lambda_means<DIM, NMAX, CAND>(c, pc, it, hist, total_samples, fp);
   __syncthreads();
   // ---- solve phase 2: xi step, xi_i = W1 c_i + S1 r_i + (DW mean(c) +
   // DS mean(r)) + beta_i per (sample, robot, axis)
   for (int v = c.tid; v < G * N * DIM; v += c.nthr) {
     const int s = v / (N * DIM), i = (v / DIM) % N, x = v % DIM;
-    float* blk = c.blk(s);
-    const int o = i * RS + x * NP;
-    float cc[NP], r[NP], mt[NP];
-    const float4* c4 = reinterpret_cast<const float4*>(blk + L.C + o);
-    const float4* r4 = reinterpret_cast<const float4*>(blk + L.PG + o);
-    const float4* mt4 = reinterpret_cast<const float4*>(blk + L.MR + x * NP);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const float4 a = c4[q], b = r4[q], e = mt4[q];
-      cc[4 * q] = a.x; cc[4 * q + 1] = a.y; cc[4 * q + 2] = a.z; cc[4 * q + 3] = a.w;
-      r[4 * q] = b.x; r[4 * q + 1] = b.y; r[4 * q + 2] = b.z; r[4 * q + 3] = b.w;
-      mt[4 * q] = e.x; mt[4 * q + 1] = e.y; mt[4 * q + 2] = e.z; mt[4 * q + 3] = e.w;
-    }
     float out[NP];
-    float dx2 = 0.0f;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      float w1[NV], s1[NV];
-      row_from(c.OPS + OPS_W1 + k * NP, w1);
-      row_from(c.OPS + OPS_S1 + k * NP, s1);
-      float a0 = c.BETA[o + k] + mt[k], a1 = 0.0f;
-#pragma unroll
-      for (int m = 0; m < NV; ++m) {
-        a0 = fmaf(w1[m], cc[m], a0);
-        a1 = fmaf(s1[m], r[m], a1);
-      }
-      const float acc = a0 + a1;
-      out[k] = acc;
-      dx2 = fmaf(acc - cc[k], acc - cc[k], dx2);
-    }
-    out[NV] = 0.0f;
-    if constexpr (PREC != 0) cf_write_row<PREC>(blk + L.CF, x * NMAX + i, out);
-    if constexpr (CAND) {
-      // drift of this coefficient row from the reference, in scaled units
-      const float inv = x == 2 ? pc.inv_b : pc.inv_a;
-      float d = 0.0f;
-      bool bad = false;
-#pragma unroll
-      for (int k = 0; k < NV; ++k) {
-        const float e = fabsf(out[k] - blk[L.CR + o + k]) * inv;
-        d = fmaxf(d, e);
-        bad |= !(e == e);
-      }
-      atomicMax(reinterpret_cast<int*>(blk + L.RF), __float_as_int(bad ? INFINITY : d));
-    }
-    float4* o4 = reinterpret_cast<float4*>(blk + L.C + o);
-    float4* p4 = reinterpret_cast<float4*>(blk + L.EB + o);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      if (keep_prev) p4[q] = make_float4(cc[4 * q], cc[4 * q + 1], cc[4 * q + 2], cc[4 * q + 3]);
-      o4[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
-    }
-    if (fp) blk[L.FPP + DIM * NV + i * DIM + x] = dx2;
+    xi_step_row<DIM, NMAX, CAND>(c, pc, s, i, x, keep_prev, fp, out);
+    if constexpr (PREC != 0) cf_write_row<PREC>(c.blk(s) + L.CF, x * NMAX + i, out);
   }
   __syncthreads();
   if (fp) {

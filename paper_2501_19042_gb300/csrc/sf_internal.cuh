@@ -186,8 +186,13 @@ struct FusedLaunch {
   int n_ctas;
   int tc, nq;   // time chunk, contraction ranges
   size_t smem;  // dynamic shared memory bytes
-  int prec;     // 0 float32 form, 1 / 2 tensor-core form with bf16 / fp16 operands
+  int prec;     // 0 float32 form, 1 / 2 warp-MMA form with bf16 / fp16 operands,
+                // 3 / 4 / 5 tensor-memory form with tf32 / bf16 / fp16 operands
 };
+// Internal form codes (FusedLaunch::prec) of the tensor-memory form.
+constexpr int PREC_TM_TF32 = 3, PREC_TM_BF16 = 4, PREC_TM_FP16 = 5;
+// Dynamic shared memory the tensor-memory form leaves to its static part.
+constexpr size_t TM_STATIC_SMEM_RESERVE = 256;
 size_t fused_smem_bytes(int dim, int nmax, int T, int gmax, int tc, int nq, bool bwd = false, int prec = 0);
 cudaError_t launch_fused(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st);
 int fused_max_warps(int nmax, bool bwd);

@@ -52,6 +52,17 @@ def plan_launch(dim: int, T: int, n_robots, n_samples, precision: str = "fp32", 
         raise nat.SfError(code, "sf_plan_launch failed")
     return {"G": out[0], "warps": out[1], "tc": out[2], "nq": out[3], "smem": int(smem.value)}
 
+def lane_peaks(device: int = 0) -> dict:
+    """``sf_lane_peaks``: measured float32 FMA and rsqrt throughput of the
+    GPU (per second) and the lane clock that the FMA rate implies."""
+    lib = nat.load()
+    f, m, c = C.c_double(), C.c_double(), C.c_double()
+    code = lib.sf_lane_peaks(int(device), C.byref(f), C.byref(m), C.byref(c))
+    if code != nat.SF_OK:
+        raise nat.SfError(code, "sf_lane_peaks failed")
+    return {"fma_per_s": f.value, "mufu_per_s": m.value, "lane_mhz": c.value}
+
+
 class SafetyFilter:
     """Handle over ``sf_create`` / ``sf_project`` / ``sf_destroy``."""
 
@@ -216,6 +227,12 @@ class SafetyFilter:
         """``sf_set_option(SF_OPT_PAIR_PRUNING)``: exact pruning of far pair
         rows between full tests (default on)."""
         nat.check(self._lib, self._h, self._lib.sf_set_option(self._h, 1, int(bool(on))))
+
+    def set_tensor_memory(self, on: bool):
+        """``sf_set_option(SF_OPT_TENSOR_MEMORY)``: the forward's
+        coefficient-to-state products on tcgen05 tensor cores through tensor
+        memory (tf32 operands in float32, the handle's 16-bit type otherwise)."""
+        nat.check(self._lib, self._h, self._lib.sf_set_option(self._h, 2, int(bool(on))))
 
     def launch_shape(self):
         out = (C.c_int * 4)()

@@ -1,0 +1,176 @@
+"""Parity of the tensor-memory form of the fused forward (coefficient-to-state
+products on tcgen05 tensor cores, accumulators in TMEM; option
+SF_OPT_TENSOR_MEMORY) with the FP64 oracle on the same seeded inputs.
+float32 handles (tf32 operands, three-term split): the float32 bounds
+(xi relative L2 <= 1e-4, lambda <= 1e-4 ||xi_ref||, final ||r_p|| within
+1e-3); bf16 / fp16 handles: the mixed-precision bounds (5e-3)."""
+import numpy as np
+import pytest
+import torch
+
+import swarm_inputs as si
+from sfcase import RHO_2D, RHO_3D, TOL_RESID_ABS, TOL_XI_REL, lam_err, rel_l2, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": TOL_XI_REL, "bf16": 5e-3, "fp16": 5e-3}
+
+
+@pytest.fixture(scope="module")
+def sfmod():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2501_19042_gb300 as P
+    P.build()
+    return P
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+
+
+def _filter(P, spec, rho, prec="fp32", max_robots=None, coll_b=None, tm=True):
+    f = P.SafetyFilter(dim=spec.dim, T=spec.T, rho=rho, coll_a=spec.coll, coll_b=coll_b, v_max=spec.v_max,
+                       a_max=spec.a_max, max_robots=max_robots or spec.n_robots, t_final=spec.t_final,
+                       precision=prec)
+    f.set_tensor_memory(tm)
+    return f
+
+
+def _run(P, sc, rho, K, prec="fp32", hist=False, coll_b=None):
+    f = _filter(P, sc.spec, rho, prec, coll_b=coll_b)
+    x0 = _dev(np.zeros_like(sc.xi_bar)) if sc.spec.init == "zero" else None
+    out = f.project(_dev(sc.xi_bar), _dev(sc.start), _dev(sc.goal), K, xi0=x0, hist=hist)
+    torch.cuda.synchronize()
+    f.sync_status()
+    return out
+
+
+def _check(out, ref, tol, idx=None):
+    xi = out.xi.double().cpu().numpy()
+    lam = out.lam.double().cpu().numpy()
+    res = out.residual.double().cpu().numpy()
+    if idx is not None:
+        xi, lam, res = xi[idx], lam[idx], res[idx]
+    err = rel_l2(xi, ref["xi"])
+    assert err.max() <= tol, f"xi rel L2 max {err.max():.3e} median {np.median(err):.3e}"
+    lerr = lam_err(lam, ref["lam"], ref["xi"])
+    assert lerr.max() <= tol, f"lambda error max {lerr.max():.3e}"
+    dres = np.abs(res - ref["rp_final"])
+    assert dres.max() <= TOL_RESID_ABS, f"residual diff max {dres.max():.3e}"
+    return err
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
+def test_small_2d_zero_init(sfmod, oracle_lib, prec):
+    """2D, N=4, zero init (every pair at delta = 0 in iteration 1), with the
+    residual history."""
+    sc = si.scene(si.config_small_2d(), 0)
+    ref = run_oracle(oracle_lib, sc, RHO_2D, 100, hist=True)
+    out = _run(sfmod, sc, RHO_2D, 100, prec, hist=True)
+    _check(out, ref, TOL[prec])
+    h = out.hist.double().cpu().numpy().T
+    if prec == "fp32":
+        np.testing.assert_allclose(h, ref["proj_hist"], rtol=1e-3, atol=1e-4)
+    else:
+        assert np.abs(h - ref["proj_hist"]).max() <= 5e-3
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
+def test_n16_3d_small_batch(sfmod, oracle_lib, prec):
+    """3D, N=16, 24 samples (several CTAs, a ragged time tail), K=60."""
+    sc = si.scene(si.config_n16_3d(n_samples=24), 1)
+    ref = run_oracle(oracle_lib, sc, RHO_3D, 60)
+    _check(_run(sfmod, sc, RHO_3D, 60, prec), ref, TOL[prec])
+
+
+@pytest.mark.parametrize("N,T", [(1, 50), (2, 33), (5, 64), (9, 31), (17, 97), (27, 120)])
+def test_edge_sizes(sfmod, oracle_lib, N, T):
+    """Robot counts across the buckets and off the lane quarters, time steps
+    below, at and off the chunk and 8-step block sizes."""
+    spec = si.config_n16_3d(n_robots=N, n_samples=5, T=T, box=(6.0, 6.0, 3.0), min_sep=0.8)
+    sc = si.scene(spec, 40 + N)
+    ref = run_oracle(oracle_lib, sc, RHO_3D, 30)
+    _check(_run(sfmod, sc, RHO_3D, 30), ref, TOL_XI_REL)
+
+
+def test_n32_t120(sfmod, oracle_lib):
+    sc = si.scene(si.config_n32_3d(n_samples=16), 3)
+    ref = run_oracle(oracle_lib, sc, RHO_3D, 40)
+    _check(_run(sfmod, sc, RHO_3D, 40), ref, TOL_XI_REL)
+
+
+def test_ellipsoid(sfmod, oracle_lib):
+    sc = si.scene(si.config_n16_3d(n_samples=24), 1)
+    ref = run_oracle(oracle_lib, sc, RHO_3D, 60, coll_b=0.35)
+    _check(_run(sfmod, sc, RHO_3D, 60, coll_b=0.35), ref, TOL_XI_REL)
+
+
+def test_n16_full_size_sampled(sfmod, oracle_lib):
+    """The bench workload at full size (S=1024, K=200): 8 sampled outputs
+    against the oracle one by one, and the median final residual below 1e-3."""
+    sc = si.scene(si.config_n16_3d(), 1)
+    out = _run(sfmod, sc, RHO_3D, 200)
+    idx = np.array([0, 1, 137, 300, 511, 700, 901, 1023])
+    ref = run_oracle(oracle_lib, sc, RHO_3D, 200, idx=idx)
+    _check(out, ref, TOL_XI_REL, idx)
+    assert torch.isfinite(out.xi).all() and float(out.residual.median()) < 1e-3
+
+
+def test_ragged_multi_scene_batch(sfmod, oracle_lib):
+    """Scenes of every bucket (one empty) in one call, each against its own
+    oracle run."""
+    P = sfmod
+    specs = [si.config_n16_3d(n_robots=n, n_samples=s, K=25) for n, s in
+             [(8, 7), (13, 3), (16, 0), (24, 5), (32, 2), (3, 9)]]
+    st = si.Stream(7)
+    scenes = [si.make_scene(sp, st) for sp in specs]
+    f = P.SafetyFilter(dim=3, T=100, rho=RHO_3D, coll_a=0.5, max_robots=32)
+    f.set_tensor_memory(True)
+    xb = np.concatenate([s.xi_bar.reshape(-1) for s in scenes])
+    nr = [s.spec.n_robots for s in scenes]
+    ns = [s.spec.n_samples for s in scenes]
+    out = f.project(_dev(xb), _dev(np.concatenate([s.start for s in scenes])),
+                    _dev(np.concatenate([s.goal for s in scenes])), 25, n_robots=nr, n_samples=ns)
+    torch.cuda.synchronize()
+    f.sync_status()
+    xi = out.xi.double().cpu().numpy()
+    lam = out.lam.double().cpu().numpy()
+    res = out.residual.double().cpu().numpy()
+    c0 = s0 = 0
+    for s in scenes:
+        S, N = s.spec.n_samples, s.spec.n_robots
+        n = S * 3 * N * 11
+        if S:
+            ref = run_oracle(oracle_lib, s, RHO_3D, 25)
+            assert rel_l2(xi[c0:c0 + n].reshape(S, -1), ref["xi"]).max() <= TOL_XI_REL, N
+            assert lam_err(lam[c0:c0 + n].reshape(S, -1), ref["lam"], ref["xi"]).max() <= TOL_XI_REL, N
+            assert np.abs(res[s0:s0 + S] - ref["rp_final"]).max() <= TOL_RESID_ABS
+        c0 += n
+        s0 += S
+
+
+def test_pruning_is_exact_in_tensor_memory_form(sfmod):
+    """With the tensor-memory form too, testing only candidate pair rows
+    between full tests gives the same xi, lambda and residual as testing
+    every row."""
+    P = sfmod
+    sc = si.scene(si.config_n16_3d(n_samples=40), 1)
+    outs = []
+    for prune in (True, False):
+        f = _filter(P, sc.spec, RHO_3D)
+        f.set_pair_pruning(prune)
+        outs.append(f.project(_dev(sc.xi_bar), _dev(sc.start), _dev(sc.goal), 120))
+        torch.cuda.synchronize()
+    a, b = outs
+    assert torch.equal(a.xi, b.xi) and torch.equal(a.lam, b.lam) and torch.equal(a.residual, b.residual)
+
+
+def test_deterministic(sfmod):
+    P = sfmod
+    sc = si.scene(si.config_n16_3d(n_samples=40), 9)
+    f = _filter(P, sc.spec, RHO_3D)
+    a = f.project(_dev(sc.xi_bar), _dev(sc.start), _dev(sc.goal), 20)
+    b = f.project(_dev(sc.xi_bar), _dev(sc.start), _dev(sc.goal), 20)
+    torch.cuda.synchronize()
+    assert torch.equal(a.xi, b.xi) and torch.equal(a.lam, b.lam) and torch.equal(a.residual, b.residual)
