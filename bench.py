@@ -33,14 +33,12 @@ import swarm_inputs as si  # noqa: E402
 RHO = 0.1
 METRIC = "SF-projected samples/s (16 robots 3D, residual<=1e-3), chosen vs plain form"
 UNIT = "samples/s"
-FP32_LANES_PER_SM = 128
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one float32
-# fused_fwd_kernel launch on the bench workload, from one ncu capture of the
-# current kernel (the forward's summary under profiles/): the inputs once
-FWD_TRAFFIC_BYTES = 2_455_552
-DTYPES = {"fp32": "f32",
-          "bf16": "bf16 tensor-core products (three-term), f32 accumulation and element-wise work",
-          "fp16": "fp16 tensor-core products, f32 accumulation and element-wise work"}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the fused kernel on the bench workload, per (form, tensor memory,
+# precision), from ncu captures of the current kernels (summaries under
+# profiles/); a kernel changed since its capture has no entry
+FWD_TRAFFIC = {}
+DTYPES = {"fp32": "f32", "bf16": "f32 (bf16 tensor products)", "fp16": "f32 (fp16 tensor products)"}
 
 
 def ops_per_sample_iter(N: int, T: int, dim: int, nv: int = 11, use_v: bool = True, use_a: bool = True):
@@ -54,6 +52,64 @@ def ops_per_sample_iter(N: int, T: int, dim: int, nv: int = 11, use_v: bool = Tr
     balls = (int(use_v) + int(use_a)) * N * T * c_ball      # velocity / acceleration blocks
     solve = dim * (N * 2 * nv * nv + 2 * nv * nv) + dim * N * nv * 5  # lambda step and xi step
     return contractions + pairs + balls + solve
+
+
+def state_macs_per_sample_iter(N: int, T: int, dim: int, nv: int = 11):
+    """Multiply-adds of the velocity and acceleration states of one iteration
+    of one sample (Pd c, Pdd c for every robot, axis and time step): the part
+    of the count that the tensor-memory form runs on the tensor cores."""
+    return 2 * T * nv * dim * N
+
+
+def mufu_per_sample_iter(N: int, T: int):
+    """Algorithmic special-function operations of one iteration of one
+    sample: one reciprocal square root per pair row and per ball row."""
+    return N * (N - 1) // 2 * T + 2 * N * T
+
+
+def roofline(spec, S, K, ms, tm, precision, form, lane, dev):
+    """The fused kernel against the pipes that bound it. FP32 lanes:
+    algorithmic lane operations (ops_per_sample_iter; in the tensor-memory
+    form without the velocity / acceleration states) over the launch time,
+    against the FMA rate measured in this run by sf_lane_peaks. Tensor
+    cores (tensor-memory form): the states' algorithmic flops against the
+    measured dense bf16 peak of MEASURED_PEAKS.json times the nominal ratio
+    of the operand type (tf32 1/2, bf16 / fp16 1). MUFU: one rsqrt per pair
+    and ball row against the measured rsqrt rate."""
+    N, T, dim = spec.n_robots, spec.T, spec.dim
+    peaks = measured_peaks()
+    sec = ms * 1e-3
+    lane_ops = ops_per_sample_iter(N, T, dim)
+    macs = state_macs_per_sample_iter(N, T, dim)
+    if tm:
+        lane_ops -= macs
+    achieved = lane_ops * S * K / sec / 1e12
+    peak = lane["fma_per_s"] / 1e12
+    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+           "ops_per_sample_iteration": lane_ops,
+           "peak_source": (f"sf_lane_peaks in this run: FMA microbenchmark {lane['fma_per_s'] / 1e12:.2f} T/s "
+                           f"(lane clock {lane['lane_mhz']:.0f} MHz), of measured"),
+           "kernel": ("tm_fwd_kernel" if tm else "fused_fwd_kernel") if form == "fused"
+           else "plain form (several kernels)",
+           "traffic": None, "traffic_unit": "DRAM bytes per launch (ncu)"}
+    cap = FWD_TRAFFIC.get((form, tm, precision))
+    if cap is not None:
+        out["traffic"] = cap[0]
+        out["traffic_source"] = cap[1]
+    mufu = mufu_per_sample_iter(N, T) * S * K / sec / 1e12
+    out["mufu"] = {"achieved": mufu, "peak": lane["mufu_per_s"] / 1e12, "unit": "Tops/s",
+                   "frac": mufu / (lane["mufu_per_s"] / 1e12), "ops_per_sample_iteration": mufu_per_sample_iter(N, T)}
+    if tm and form == "fused":
+        ratio = 0.5 if precision == "fp32" else 1.0
+        bf16 = float(peaks.get("bf16_tflops", 0.0)) or 1900.0
+        tpeak = bf16 * ratio
+        tach = 2.0 * macs * S * K / sec / 1e12
+        out["tensor"] = {"achieved": tach, "peak": tpeak, "unit": "TFLOP/s", "frac": tach / tpeak,
+                         "flops_per_sample_iteration": 2 * macs,
+                         "operands": {"fp32": "tf32", "bf16": "bf16", "fp16": "fp16"}[precision],
+                         "peak_source": f"MEASURED_PEAKS.json bf16 burst {bf16:.1f} TFLOP/s x {ratio} (nominal "
+                                        "ratio of the operand type), of measured"}
+    return out
 
 
 def workload_spec():
@@ -170,6 +226,11 @@ def run_gpu(args):
         f.project(xb, st, gl, K, form=args.form, out=out)
     torch.cuda.synchronize()
 
+    # the float32-lane peaks of this GPU, measured now (FMA and rsqrt microbenchmarks)
+    lane = P.lane_peaks(dev.index)
+    f.project(xb, st, gl, K, form=args.form, out=out)
+    torch.cuda.synchronize()
+
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clk = ClockSampler(dev.index)
@@ -213,30 +274,21 @@ def run_gpu(args):
     d2h = (2 * hx.numel() + S) * 4
 
     if rank == 0:
-        peaks = measured_peaks()
-        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-        max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-        peak_tops = sm_count * FP32_LANES_PER_SM * max_mhz * 1e6 / 1e12
-        ops = ops_per_sample_iter(spec.n_robots, spec.T, spec.dim) * S * K
-        kernel_ms = ms   # a step is one launch of the fused kernel
-        achieved = ops / (kernel_ms * 1e-3) / 1e12
+        tm = bool(args.tensor_memory) or args.precision != "fp32"
         value = world * S / (ms * 1e-3)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic (seeded swarm generator)",
-            "impl": "gb300", "form": args.form,
+            "vs_baseline": None, "dtype": DTYPES[args.precision],
+            "data": "synthetic (seeded swarm generator)", "impl": "gb300", "form": args.form,
             "config": {"workload": workload_name(spec), "global_batch": world * S, "per_gpu_samples": S,
-                       "parallelism": f"independent sample batches on {world} GPU(s)",
-                       "l2": "flushed between timed steps by a 256 MiB write outside the events"},
+                       "parallelism": f"contiguous sample ranges (shard_batch) on {world} GPU(s)",
+                       "l2": "flushed between timed steps by a 256 MiB write outside the events",
+                       "tensor_memory": tm,
+                       "state_products": ({"fp32": "tf32", "bf16": "bf16", "fp16": "fp16"}[args.precision]
+                                          + " three-term MMAs (tcgen05, TMEM)") if tm else "float32 lanes"},
             "median_final_residual": med_res,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
-                         "frac": achieved / peak_tops,
-                         "traffic": FWD_TRAFFIC_BYTES if (args.form == "fused" and args.precision == "fp32") else None,
-                         "traffic_unit": "DRAM bytes per launch (ncu)",
-                         "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x {max_mhz:.0f} MHz "
-                                        "(max SM clock of MEASURED_PEAKS.json)",
-                         "kernel": "fused_fwd_kernel" if args.form == "fused" else "plain form (several kernels)"},
+            "roofline": roofline(spec, S, K, ms, tm, args.precision, args.form, lane, dev),
             "e2e": {"value": world * S / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "api": "sf_project_host"},
             "gpu_launches": int(launches),
@@ -293,12 +345,13 @@ def plain_form_timing(f, xb, st, gl, K, flush, stream, fused_ms, S, steps: int =
 def diff_timing(P, dev):
     """Forward / backward times of the differentiable SF on the
     differentiation workload (N=16 3D, S=512, T=100, K=50, checkpoint every
-    10), CUDA events, mean of 5 after one warm-up call."""
+    10), CUDA events, mean of 5 after one warm-up call, per mode: float32
+    (lane products), float32 with the tensor-memory form (tf32 products) and
+    the bf16 / fp16 modes (tensor-memory form). The adjoint is float32 in
+    every mode; the training forward writes checkpoints and activity masks."""
     import torch
     spec = si.config_diff()
     sc = si.scene(spec, 5)
-    f = P.SafetyFilter(dim=3, T=spec.T, rho=RHO, coll_a=spec.coll, v_max=spec.v_max, a_max=spec.a_max,
-                       max_robots=spec.n_robots, checkpoint_every=10, device=dev.index)
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
     xb, st, gl = t(sc.xi_bar), t(sc.start), t(sc.goal)
     g = torch.randn(xb.shape, generator=torch.Generator().manual_seed(0)).to(dev)
@@ -314,12 +367,22 @@ def diff_timing(P, dev):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / n
 
-    fwd = timed(lambda: f.project(xb, st, gl, spec.K))
-    trn = timed(lambda: f.project_train(xb, st, gl, spec.K))
-    _, _, ck = f.project_train(xb, st, gl, spec.K)
-    bwd = timed(lambda: f.project_backward(xb, st, gl, spec.K, ck, grad_xi=g))
-    return {"workload": f"3D N={spec.n_robots}, S={spec.n_samples}, T={spec.T}, K={spec.K}, checkpoint every 10",
-            "fwd_ms": fwd, "train_fwd_ms": trn, "bwd_ms": bwd, "bwd_over_fwd": bwd / fwd}
+    modes = {}
+    for name, prec, tm in (("fp32", "fp32", False), ("fp32_tensor_memory", "fp32", True), ("bf16", "bf16", True),
+                           ("fp16", "fp16", True)):
+        f = P.SafetyFilter(dim=3, T=spec.T, rho=RHO, coll_a=spec.coll, v_max=spec.v_max, a_max=spec.a_max,
+                           max_robots=spec.n_robots, checkpoint_every=10, device=dev.index, precision=prec)
+        f.set_tensor_memory(tm)
+        fwd = timed(lambda: f.project(xb, st, gl, spec.K))
+        trn = timed(lambda: f.project_train(xb, st, gl, spec.K))
+        _, _, ck = f.project_train(xb, st, gl, spec.K)
+        bwd = timed(lambda: f.project_backward(xb, st, gl, spec.K, ck, grad_xi=g))
+        f.sync_status()
+        modes[name] = {"fwd_ms": fwd, "train_fwd_ms": trn, "bwd_ms": bwd, "bwd_over_fwd": bwd / fwd}
+    out = {"workload": f"3D N={spec.n_robots}, S={spec.n_samples}, T={spec.T}, K={spec.K}, checkpoint every 10",
+           "modes": modes}
+    out.update(modes["fp32"])
+    return out
 
 
 def init_timing(P, dev, steps: int = 300, eval_scenes: int = 64):
@@ -376,13 +439,15 @@ def precision_timing(P, dev, n_check: int = 64, steps: int = 3):
     xb, st, gl = t(sc.xi_bar), t(sc.start), t(sc.goal)
     xr = np.asarray(ref["xi"]).reshape(n_check, -1)
     modes = {}
-    for prec in ("fp32", "bf16", "fp16"):
+    for name, prec, tm in (("fp32", "fp32", False), ("fp32_tensor_memory", "fp32", True), ("bf16", "bf16", True),
+                           ("fp16", "fp16", True)):
         try:
             f = P.SafetyFilter(dim=3, T=spec.T, rho=RHO, coll_a=spec.coll, v_max=spec.v_max, a_max=spec.a_max,
                                max_robots=spec.n_robots, t_final=spec.t_final, precision=prec, device=dev.index)
+            f.set_tensor_memory(tm)
             out = f.project(xb, st, gl, spec.K)
         except Exception as e:  # a mode this library does not build
-            modes[prec] = {"unavailable": str(e).splitlines()[0][:160]}
+            modes[name] = {"unavailable": str(e).splitlines()[0][:160]}
             continue
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -395,10 +460,13 @@ def precision_timing(P, dev, n_check: int = 64, steps: int = 3):
         f.sync_status()
         xi = out.xi[:n_check].double().cpu().numpy().reshape(n_check, -1)
         err = np.linalg.norm(xi - xr, axis=1) / np.linalg.norm(xr, axis=1)
+        lam = out.lam[:n_check].double().cpu().numpy().reshape(n_check, -1)
+        lerr = np.linalg.norm(lam - np.asarray(ref["lam"]).reshape(n_check, -1), axis=1) / np.linalg.norm(xr, axis=1)
         dres = np.abs(out.residual[:n_check].double().cpu().numpy() - np.asarray(ref["rp_final"]))
-        modes[prec] = {"ms": ms, "samples_per_s": spec.n_samples / (ms * 1e-3),
+        modes[name] = {"ms": ms, "samples_per_s": spec.n_samples / (ms * 1e-3),
                        "median_final_residual": float(out.residual.median()),
                        "xi_rel_l2_median": float(np.median(err)), "xi_rel_l2_max": float(err.max()),
+                       "lambda_err_max": float(lerr.max()),
                        "resid_absdiff_max": float(dres.max()), "launch_shape": f.launch_shape()}
     return {"workload": f"3D N={spec.n_robots}, S={spec.n_samples}, T={spec.T}, K={spec.K}, sample init, "
                         f"rho={RHO}; errors vs the FP64 oracle on samples 0..{n_check - 1}",

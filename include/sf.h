@@ -59,23 +59,24 @@ typedef enum {
   SF_ERR_WORKSPACE = 7      /* workspace missing or too small */
 } sf_status;
 
-/* Arithmetic of the contractions (coefficients -> states, Eq. (poly), and
- * F^T of the residual in the lambda step of the Appendix). The projections,
- * residuals, multiplier updates and the xi step are float32 in every mode;
- * the one-time factorisation of the KKT matrix is float64.
- * The 16-bit modes run those contractions on warp-level tensor-core MMAs
- * with float32 accumulation, in the fused form of sf_project only (the plain
- * form, sf_project_train, checkpoints and sf_project_backward return
- * SF_ERR_UNSUPPORTED on such a handle). Products with the coefficients
- * (positions, velocities, accelerations) are three-term: the operands are
- * split into a 16-bit part and its 16-bit rounding remainder and the
- * remainder x remainder term is dropped. F^T of the residual takes the
- * residual form (only the small residuals enter 16 bits): single-term in
- * fp16, three-term in bf16. */
+/* Arithmetic of the coefficient-to-state products (velocities and
+ * accelerations of Eq. (poly), which the ball rows need at every time step
+ * of every iteration). The positions of the pair rows, F^T of the residual
+ * in the lambda step of the Appendix, the projections, residuals,
+ * multiplier updates and the xi step are float32 in every mode; the
+ * one-time factorisation of the KKT matrix is float64.
+ * In the 16-bit modes (and in float32 with SF_OPT_TENSOR_MEMORY) the fused
+ * forward takes those products on the 5th-generation tensor cores through
+ * tensor memory (tcgen05 MMAs, float32 accumulation): both operands are
+ * split into a rounded part and its rounding remainder, and the product is
+ * taken in three terms (the remainder x remainder term dropped), which keeps
+ * about 16 bits (bf16) or 21 bits (tf32, fp16) of the operands. The plain
+ * form is float32 only (SF_ERR_UNSUPPORTED on a 16-bit handle); the adjoint
+ * runs in float32 in every mode. */
 typedef enum {
   SF_PREC_FP32 = 0,  /* float32 everywhere */
-  SF_PREC_BF16 = 1,  /* tensor-core bf16 products, float32 accumulation */
-  SF_PREC_FP16 = 2   /* tensor-core fp16 products, float32 accumulation */
+  SF_PREC_BF16 = 1,  /* tensor-memory MMAs with bf16 operands, float32 accumulation */
+  SF_PREC_FP16 = 2   /* tensor-memory MMAs with fp16 operands, float32 accumulation */
 } sf_precision;
 
 /* How the iteration is laid out on the GPU. */
@@ -200,20 +201,16 @@ typedef enum {
    * to 1); with the workspace block, the workspace rows of robots that were
    * within 0.1 (workspace-scaled) of its boundary are retested likewise. The
    * result is the same as testing every row. 0: every row every iteration.
-   * In the 16-bit modes the retests use float32 positions and the MMA
-   * positions are computed only for full tests. No effect in the plain form
-   * and the backward's recompute. */
+   * The decision is taken per sample. No effect in the plain form and the
+   * backward's recompute. */
   SF_OPT_PAIR_PRUNING = 1,
-  /* 1: the fused forward of sf_project (no checkpoints) runs its
-   * coefficient-to-state products (positions, velocities and accelerations
-   * of Eq. (poly)) on the tensor cores through tensor memory (tcgen05 MMAs,
-   * the coefficient rows of a CTA's samples as the A operand in TMEM, the
-   * basis rows of a time chunk as the B operand in shared memory, three-term
-   * split of both operands); the operands are tf32 for SF_PREC_FP32 and the
-   * handle's 16-bit type otherwise. F^T of the residual, the projections,
-   * the multiplier and xi steps stay on the float32 lanes. 0 (default): the
-   * float32 form (SF_PREC_FP32) or the warp-MMA form (16-bit modes).
-   * sf_project_train and sf_project_backward are not affected. */
+  /* 1: the fused forward of a float32 handle (sf_project and
+   * sf_project_train) runs the velocity / acceleration products on the tensor
+   * cores through tensor memory (tcgen05 MMAs, the coefficient rows of a
+   * CTA's samples as the A operand in TMEM, the basis rows of a time chunk as
+   * the B operand in shared memory, three-term split of tf32 operands); the
+   * rest stays on the float32 lanes. 0: the float32 form, products on the
+   * lanes too. 16-bit handles always use the tensor-memory form. */
   SF_OPT_TENSOR_MEMORY = 2
 } sf_option;
 

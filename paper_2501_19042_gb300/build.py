@@ -31,9 +31,9 @@ def _nvcc() -> str:
 
 def sources():
     """The translation units, the slowest to compile first (adjoint and
-    tensor-core kernels, larger robot buckets)."""
+    tensor-memory kernels, larger robot buckets)."""
     def cost(f):
-        heavy = ("backward" in f) * 2 + ("_tc_" in f)
+        heavy = ("backward" in f) * 2 + ("_tm_" in f) * 2
         n = 0
         for tok in f[:-3].split("_"):
             if tok.startswith("n") and tok[1:].isdigit():

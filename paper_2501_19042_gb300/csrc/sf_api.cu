@@ -130,17 +130,18 @@ struct FusedRequest {
   float* ckpt = nullptr;
   float* fp_res2 = nullptr;
   bool backward = false;
-  int prec = 0;             // forward only: 0 float32 form, 1 / 2 tensor-core form
+  int prec = 0;             // forward only: the form code (FusedLaunch::prec)
   BwdLaunchArgs bwd{};
 };
 
-// Form code of a fused forward launch (FusedLaunch::prec): the handle's
-// precision, moved to the tensor-memory form when that option is on and the
-// call writes no checkpoints (the training forward and the adjoint are the
-// float32 form's).
-int forward_form(const sf_handle* h, bool checkpoints) {
+// Form code of a fused forward launch (FusedLaunch::prec): the tensor-memory
+// form with the handle's operand format when the option is on or the
+// precision is 16-bit (the 16-bit products exist only there), else the
+// float32 form. The training forward follows the same rule; the adjoint is
+// the float32 form's in every case.
+int forward_form(const sf_handle* h) {
   const int p = h->pb.precision;
-  return (h->tm && !checkpoints) ? PREC_TM_TF32 + p : p;
+  return (h->tm || p != SF_PREC_FP32) ? PREC_TM_TF32 + p : 0;
 }
 
 long long total_coefs(const sf_handle* h, const sf_batch* b) {
@@ -168,8 +169,10 @@ struct LaunchGroup {
   std::string key;
 };
 
-std::string group_key(bool bwd, int dim, int nmax, int T, const std::vector<int>& nr, const std::vector<int>& ns) {
-  std::string k = (bwd ? "b" : "f") + std::to_string(dim) + "/" + std::to_string(nmax) + "/" + std::to_string(T) + ":";
+std::string group_key(bool bwd, int prec, int dim, int nmax, int T, const std::vector<int>& nr,
+                      const std::vector<int>& ns) {
+  std::string k = (bwd ? "b" : "f") + std::to_string(prec) + "/" + std::to_string(dim) + "/" + std::to_string(nmax) +
+                  "/" + std::to_string(T) + ":";
   for (size_t q = 0; q < nr.size(); ++q) k += std::to_string(nr[q]) + "x" + std::to_string(ns[q]) + ",";
   return k;
 }
@@ -206,7 +209,7 @@ sf_status build_groups(sf_handle* h, const sf_batch* b, int K, long long S, cons
         ns.push_back(b->n_samples[items[bk][q].scene]);
       }
       LaunchGroup lg;
-      lg.key = group_key(rq.backward, dim, nmax, T, nr, ns);
+      lg.key = group_key(rq.backward, rq.prec, dim, nmax, T, nr, ns);
       FusedPlan plan;
       auto hit = h->tuned.find(lg.key);
       const bool forced = h->force_G || h->force_warps || h->force_tc;
@@ -519,11 +522,9 @@ sf_status sf_project(sf_handle* h, void* stream, const sf_batch* b, int K, int f
   rq.resid_out = resid_out;
   rq.hist = resid_hist;
   rq.ckpt = reinterpret_cast<float*>(checkpoints);
-  rq.prec = forward_form(h, checkpoints != nullptr);
+  rq.prec = forward_form(h);
   if (checkpoints && h->pb.checkpoint_every <= 0)
     return fail(h, SF_ERR_INVALID_ARG, "checkpoints need a handle with checkpoint_every > 0");
-  if (checkpoints && h->pb.precision != SF_PREC_FP32)
-    return fail(h, SF_ERR_UNSUPPORTED, "checkpoints (for the float32 adjoint) need SF_PREC_FP32");
   return run_fused(h, st, b, K, S, rq);
 }
 
@@ -536,7 +537,6 @@ sf_status sf_project_train(sf_handle* h, void* stream, const sf_batch* b, int K,
   if (s0 != SF_OK) return s0;
   if (K < 1) return fail(h, SF_ERR_INVALID_ARG, "K must be >= 1");
   if (h->pb.checkpoint_every <= 0) return fail(h, SF_ERR_INVALID_ARG, "handle has checkpoint_every = 0");
-  if (h->pb.precision != SF_PREC_FP32) return fail(h, SF_ERR_UNSUPPORTED, "training forward is float32 only");
   if (S > 0 && (!xi_out || !lam_out || !resid_out || !checkpoints))
     return fail(h, SF_ERR_INVALID_ARG, "xi_out / lambda_out / residual_out / checkpoints is NULL");
   if (S == 0) return SF_OK;
@@ -549,6 +549,7 @@ sf_status sf_project_train(sf_handle* h, void* stream, const sf_batch* b, int K,
   rq.resid_out = resid_out;
   rq.ckpt = reinterpret_cast<float*>(checkpoints);
   rq.fp_res2 = fp_res2_out;
+  rq.prec = forward_form(h);
   return run_fused(h, reinterpret_cast<cudaStream_t>(stream), b, K, S, rq);
 }
 
@@ -571,7 +572,8 @@ sf_status sf_project_backward(sf_handle* h, void* stream, const sf_batch* b, int
   if (s0 != SF_OK) return s0;
   if (K < 1) return fail(h, SF_ERR_INVALID_ARG, "K must be >= 1");
   if (h->pb.checkpoint_every <= 0) return fail(h, SF_ERR_INVALID_ARG, "handle has checkpoint_every = 0");
-  if (h->pb.precision != SF_PREC_FP32) return fail(h, SF_ERR_UNSUPPORTED, "backward is float32 only");
+  // the adjoint runs in float32 in every precision mode (its recompute of a
+  // checkpoint segment is the float32 form's iteration)
   if (S == 0) return SF_OK;
   if (!checkpoints) return fail(h, SF_ERR_INVALID_ARG, "checkpoints is NULL");
   const size_t need = sf_backward_workspace_bytes(h, b, K);
@@ -689,7 +691,7 @@ sf_status sf_autotune(sf_handle* h, void* stream, const sf_batch* b, int K_probe
   rq.xi_out = xi_out;
   rq.lam_out = lam_out;
   rq.resid_out = resid_out;
-  rq.prec = forward_form(h, false);
+  rq.prec = forward_form(h);
   const int fG = h->force_G, fW = h->force_warps, fT = h->force_tc;
   h->force_G = h->force_warps = h->force_tc = 0;
   h->use_tuned = false;
@@ -1028,8 +1030,10 @@ sf_status sf_plan_launch(int dim, int T, int n_scenes, const int* n_robots, cons
     total += n_samples[q];
   }
   if (total < 1) return SF_ERR_INVALID_ARG;
+  // the form a handle of this precision uses by default (16-bit: tensor memory)
+  const int form = precision == SF_PREC_FP32 ? 0 : PREC_TM_TF32 + precision;
   const FusedPlan p = plan_fused(dim, kBucketNmax[bk], T, n_robots, n_samples, n_scenes, num_sms,
-                                 smem_per_block_optin, 0, 0, 0, false, nullptr, 0, precision);
+                                 smem_per_block_optin, 0, 0, 0, false, nullptr, 0, form);
   if (p.G == 0) return SF_ERR_UNSUPPORTED;
   out4[0] = p.G;
   out4[1] = p.warps;

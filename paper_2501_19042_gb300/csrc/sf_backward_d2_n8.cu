@@ -14,10 +14,10 @@ cudaError_t prepare_bwd_d2_n8(int smem) {
 // Forward with checkpoints (training): also writes the activity masks of
 // the last checkpoint segment for this adjoint.
 cudaError_t launch_fused_train_d2_n8(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st) {
-  return fused_impl::launch_t<2, 8, 384, 0, true>(a, l, st);
+  return fused_impl::launch_t<2, 8, 384, true>(a, l, st);
 }
 cudaError_t prepare_fused_train_d2_n8(int smem) {
-  return cudaFuncSetAttribute(fused_impl::fused_fwd_kernel<2, 8, 384, 0, true>,
+  return cudaFuncSetAttribute(fused_impl::fused_fwd_kernel<2, 8, 384, true>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 }  // namespace sf

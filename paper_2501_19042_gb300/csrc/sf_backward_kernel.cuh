@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(MAXT, 1) fused_bwd_kernel(const __grid_constan
       __syncthreads();
       store_state<DIM, NMAX>(c, ring, ring + tot, 0);
       for (int k = kb; k < ke; ++k) {
-        fwd_iteration<DIM, NMAX, 0, true>(c, pc, A.xi_bar, k, false, nullptr, 0, false,
+        fwd_iteration<DIM, NMAX, true>(c, pc, A.xi_bar, k, false, nullptr, 0, false,
                                           A.ring_mask + (size_t)(k - kb) * A.mask_slot);
         float* slot = ring + (size_t)(k - kb + 1) * 2 * tot;
         store_state<DIM, NMAX>(c, slot, slot + tot, 0);

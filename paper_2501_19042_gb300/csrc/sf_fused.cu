@@ -13,46 +13,26 @@ namespace sf {
   cudaError_t launch_fused_train_d##D##_n##NM(const FusedArgs&, const FusedLaunch&, cudaStream_t);     \
   cudaError_t launch_bwd_d##D##_n##NM(const FusedArgs&, const BwdLaunchArgs&, const FusedLaunch&,      \
                                       cudaStream_t);
-#define SF_DECL_TC(D, NM)                                                                          \
-  cudaError_t launch_fused_tc1_d##D##_n##NM(const FusedArgs&, const FusedLaunch&, cudaStream_t);  \
-  cudaError_t launch_fused_tc2_d##D##_n##NM(const FusedArgs&, const FusedLaunch&, cudaStream_t);
 SF_DECL(2, 8) SF_DECL(2, 16) SF_DECL(2, 24) SF_DECL(2, 32) SF_DECL(3, 8) SF_DECL(3, 16) SF_DECL(3, 24) SF_DECL(3, 32)
-SF_DECL_TC(2, 8) SF_DECL_TC(2, 16) SF_DECL_TC(2, 24) SF_DECL_TC(2, 32)
-SF_DECL_TC(3, 8) SF_DECL_TC(3, 16) SF_DECL_TC(3, 24) SF_DECL_TC(3, 32)
 #define SF_DECL_TM(D, NM) \
   cudaError_t launch_tm_d##D##_n##NM(const FusedArgs&, const FusedLaunch&, cudaStream_t); \
   cudaError_t prepare_tm_d##D##_n##NM(int, int);
 SF_DECL_TM(2, 8) SF_DECL_TM(2, 16) SF_DECL_TM(2, 24) SF_DECL_TM(2, 32)
 SF_DECL_TM(3, 8) SF_DECL_TM(3, 16) SF_DECL_TM(3, 24) SF_DECL_TM(3, 32)
 #undef SF_DECL
-#undef SF_DECL_TC
 #undef SF_DECL_TM
 #define SF_PREP(D, NM) cudaError_t prepare_fused_d##D##_n##NM(int); cudaError_t prepare_bwd_d##D##_n##NM(int); \
-  cudaError_t prepare_fused_train_d##D##_n##NM(int); \
-  cudaError_t prepare_fused_tc1_d##D##_n##NM(int); cudaError_t prepare_fused_tc2_d##D##_n##NM(int);
+  cudaError_t prepare_fused_train_d##D##_n##NM(int);
 SF_PREP(2, 8) SF_PREP(2, 16) SF_PREP(2, 24) SF_PREP(2, 32) SF_PREP(3, 8) SF_PREP(3, 16) SF_PREP(3, 24) SF_PREP(3, 32)
 #undef SF_PREP
 
 // Raises the dynamic shared-memory limit of every fused / adjoint kernel of
-// this dimension (and, for a 16-bit precision, of the tensor-core kernels)
-// once, at handle creation, so that no launch (and no stream capture) has to
-// configure a kernel.
+// this dimension (the tensor-memory kernels with the handle's operand
+// format) once, at handle creation, so that no launch (and no stream capture)
+// has to configure a kernel.
 cudaError_t prepare_kernels(int dim, int smem, int prec) {
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
-  if (prec == 1 && dim == 3) {
-    chk(prepare_fused_tc1_d3_n8(smem)); chk(prepare_fused_tc1_d3_n16(smem)); chk(prepare_fused_tc1_d3_n24(smem));
-    chk(prepare_fused_tc1_d3_n32(smem));
-  } else if (prec == 1) {
-    chk(prepare_fused_tc1_d2_n8(smem)); chk(prepare_fused_tc1_d2_n16(smem)); chk(prepare_fused_tc1_d2_n24(smem));
-    chk(prepare_fused_tc1_d2_n32(smem));
-  } else if (prec == 2 && dim == 3) {
-    chk(prepare_fused_tc2_d3_n8(smem)); chk(prepare_fused_tc2_d3_n16(smem)); chk(prepare_fused_tc2_d3_n24(smem));
-    chk(prepare_fused_tc2_d3_n32(smem));
-  } else if (prec == 2) {
-    chk(prepare_fused_tc2_d2_n8(smem)); chk(prepare_fused_tc2_d2_n16(smem)); chk(prepare_fused_tc2_d2_n24(smem));
-    chk(prepare_fused_tc2_d2_n32(smem));
-  }
   // tensor-memory form with the handle's operand format (tf32 for float32)
   if (dim == 3) {
     chk(prepare_tm_d3_n8(smem, prec)); chk(prepare_tm_d3_n16(smem, prec)); chk(prepare_tm_d3_n24(smem, prec));
@@ -83,7 +63,7 @@ int fused_max_warps(int nmax, bool bwd) { return (bwd && nmax > 16) ? 8 : 12; }
 
 size_t fused_smem_bytes(int dim, int nmax, int T, int gmax, int tc, int nq, bool bwd, int prec) {
   const bool tm = prec >= PREC_TM_TF32;
-  const fused_impl::Lay L(dim, nmax, T, tc, nq, bwd, prec == 1 || prec == 2, !bwd, tm ? prec - PREC_TM_TF32 : -1);
+  const fused_impl::Lay L(dim, nmax, T, tc, nq, bwd, !bwd, tm ? prec - PREC_TM_TF32 : -1);
   return sizeof(float) * ((size_t)L.head + (size_t)gmax * L.SB);
 }
 
@@ -91,10 +71,9 @@ size_t fused_smem_bytes(int dim, int nmax, int T, int gmax, int tc, int nq, bool
 // of the contraction phase (per (sample, robot, t)), padded to whole rounds
 // of the CTA's threads, over an issue rate that saturates at 4 warp
 // instructions per cycle; plus a charge per block-wide barrier. The CTA count
-// over the SM count gives the number of waves. The tensor-core form (prec
-// 1 / 2) counts warp units instead: (sample, 16-step block) for the
-// positions, (sample, range of blocks) for the contraction; its time chunk
-// is even and its ranges at most one per block.
+// over the SM count gives the number of waves. The tensor-memory form (prec
+// >= PREC_TM_TF32) charges its TMEM pass per 8-step block of a warp group
+// instead of the contraction phase.
 FusedPlan plan_fused(int dim, int nmax, int T, const int* nr, const int* ns, int n_scenes, int num_sms,
                      size_t smem_cap, int force_G, int force_warps, int force_tc, bool bwd, FusedPlan* top,
                      int n_top, int prec) {
@@ -111,15 +90,6 @@ FusedPlan plan_fused(int dim, int nmax, int T, const int* nr, const int* ns, int
   const int maxw = fused_max_warps(nmax, bwd);
   const double cA = 0.5 * Nbig * (Nbig - 1) * 14.0 + 45.0 * Nbig;
   const double cB = 200.0;
-  const int MT = (dim * nmax + 15) / 16, NJ = nmax / 8;
-  // tensor-core form: pair tests per lane; per positions unit; per
-  // contraction block of 16 steps and per contraction unit; latencies of a
-  // positions unit and of a contraction block (a unit's dependent chain)
-  const double cA_tc = 0.5 * Nbig * (Nbig - 1) * 8.0 + 8.0 * Nbig;
-  const double cP_tc = 40.0 * MT;
-  const double cC_tc = 2.0 * (2.0 * (3.0 * MT + 14.0 * NJ + 4.0) + 8.0);
-  const double cU_tc = 26.0 * MT;
-  const double latP = 300.0, latC = 480.0;
   auto add_top = [&](const FusedPlan& cand) {
     if (cand.cost < best.cost) best = cand;
     if (top && n_top > 0) {
@@ -157,6 +127,8 @@ FusedPlan plan_fused(int dim, int nmax, int T, const int* nr, const int* ns, int
         for (int w = 8; w <= maxw; w += 4) {
           if (force_warps > 0 && w != force_warps) continue;
           const int ncg = w / 4;
+          // the groups' partials of F^T q pass through the allocated columns
+          if (ncg * dim * 16 > fused_impl::tm_alloc_cols(fused_impl::tm_cols(dim, tc, fmt))) continue;
           const size_t smem = fused_smem_bytes(dim, nmax, T, G, tc, ncg, bwd, prec);
           if (smem + TM_STATIC_SMEM_RESERVE > smem_cap) continue;
           const double rate = std::min(4.0, w / 2.0);
@@ -170,38 +142,6 @@ FusedPlan plan_fused(int dim, int nmax, int T, const int* nr, const int* ns, int
           const double per_iter = real_nch * (tPass + tPair) + (2.0 * real_nch + 3.0) * 400.0 +
                                   24.0 * G * Nbig * dim * 4.0 / rate;
           add_top(FusedPlan{G, w, tc, ncg, smem, waves * per_iter});
-        }
-      }
-      continue;
-    }
-    if (prec != 0) {
-      int prev_tc = 0;
-      for (int nch = 1; nch <= 6; ++nch) {
-        int tc = (T + nch - 1) / nch;
-        tc += tc & 1;
-        if (tc == prev_tc) continue;
-        prev_tc = tc;
-        if (force_tc > 0 && tc != force_tc) continue;
-        const int nkb = (tc + 15) / 16;
-        const int real_nch = (T + tc - 1) / tc;
-        for (int w = 4; w <= maxw; ++w) {
-          if (force_warps > 0 && w != force_warps) continue;
-          const double rate = std::min(4.0, w / 2.0);
-          const double p_rounds = std::ceil((double)G * nkb / w);
-          for (int nq = 1; nq <= nkb; ++nq) {
-            const size_t smem = fused_smem_bytes(dim, nmax, T, G, tc, nq, bwd, prec);
-            if (smem > smem_cap) continue;
-            const double c_rounds = std::ceil((double)G * nq / w);
-            const double kbq = std::ceil((double)nkb / nq);
-            // issue work counts the units that exist (a last round that
-            // is not full issues less); the latency term counts rounds
-            const double tP = std::max((double)G * nkb * cP_tc / rate, p_rounds * latP);
-            const double tC = std::max((double)G * nq * (kbq * cC_tc + cU_tc) / rate, c_rounds * kbq * latC);
-            const double tA = std::ceil((double)G * tc / 32.0) * cA_tc / rate;
-            const double per_iter = real_nch * (tP + tA + tC) +
-                                    (3.0 * real_nch + 2.0) * 400.0 + 24.0 * G * Nbig * dim * 4.0 / rate;
-            add_top(FusedPlan{G, w, tc, nq, smem, waves * per_iter});
-          }
         }
       }
       continue;
@@ -256,16 +196,6 @@ cudaError_t launch_fused(const FusedArgs& a, const FusedLaunch& l, cudaStream_t 
   if (dim == D && l.nmax == NM) return launch_tm_d##D##_n##NM(a, l, st);
     SF_TM(3, 8) SF_TM(3, 16) SF_TM(3, 24) SF_TM(3, 32) SF_TM(2, 8) SF_TM(2, 16) SF_TM(2, 24) SF_TM(2, 32)
 #undef SF_TM
-    return cudaErrorInvalidValue;
-  }
-  if (l.prec != 0) {
-#define SF_TC(P, D, NM) \
-  if (l.prec == P && dim == D && l.nmax == NM) return launch_fused_tc##P##_d##D##_n##NM(a, l, st);
-    SF_TC(1, 3, 8) SF_TC(1, 3, 16) SF_TC(1, 3, 24) SF_TC(1, 3, 32)
-    SF_TC(1, 2, 8) SF_TC(1, 2, 16) SF_TC(1, 2, 24) SF_TC(1, 2, 32)
-    SF_TC(2, 3, 8) SF_TC(2, 3, 16) SF_TC(2, 3, 24) SF_TC(2, 3, 32)
-    SF_TC(2, 2, 8) SF_TC(2, 2, 16) SF_TC(2, 2, 24) SF_TC(2, 2, 32)
-#undef SF_TC
     return cudaErrorInvalidValue;
   }
   if (a.amask) {

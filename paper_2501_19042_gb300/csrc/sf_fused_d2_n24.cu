@@ -6,7 +6,7 @@ cudaError_t launch_fused_d2_n24(const FusedArgs& a, const FusedLaunch& l, cudaSt
   return fused_impl::launch_t<2, 24, 384>(a, l, st);
 }
 cudaError_t prepare_fused_d2_n24(int smem) {
-  return cudaFuncSetAttribute(fused_impl::fused_fwd_kernel<2, 24, 384, 0>,
+  return cudaFuncSetAttribute(fused_impl::fused_fwd_kernel<2, 24, 384>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 }  // namespace sf

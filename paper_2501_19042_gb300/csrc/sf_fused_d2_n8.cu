@@ -6,7 +6,7 @@ cudaError_t launch_fused_d2_n8(const FusedArgs& a, const FusedLaunch& l, cudaStr
   return fused_impl::launch_t<2, 8, 384>(a, l, st);
 }
 cudaError_t prepare_fused_d2_n8(int smem) {
-  return cudaFuncSetAttribute(fused_impl::fused_fwd_kernel<2, 8, 384, 0>,
+  return cudaFuncSetAttribute(fused_impl::fused_fwd_kernel<2, 8, 384>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 }  // namespace sf

@@ -29,7 +29,7 @@
 // Every reduction is done in a fixed order: results are bit-reproducible.
 #pragma once
 #include "sf_internal.cuh"
-#include "sf_tc.cuh"
+#include "sf_pack16.cuh"
 
 namespace sf {
 namespace fused_impl {
@@ -78,48 +78,46 @@ __host__ __device__ constexpr int tm_tab_bytes(int T, int tc, int fmt) {
   return ((T + tc - 1) / tc * tm_tcw(tc) / 8 + 1) * tm_sbo(fmt);
 }
 
-// Shared-memory layout (floats). Head, float32 form: basis [T][36],
-// operators, beta. Head, tensor-core form: the basis as 16-bit operand
-// tables BN [T][3][4][4] words (rows of P, Pd, Pdd by time step: per lane
-// quad t4 the rounded k pairs (2 t4, 2 t4 + 8), then their rounding
-// remainders) and BT [2][3][11][TH] words (P, Pd, Pdd transposed, pairs of
-// time steps, TH = ceil(T / 2); rounded, then the rounding remainders),
-// operators, beta.
-// Per sample: C, LAM [NMAX][DIM][12]; PG [NQ][NMAX][DIM][12] (partials of
-// F^T q, later r); MC, MR [DIM][12] (forward: MR holds the xi step's mean
-// term DW mean(c) + DS mean(r); adjoint: DS^T mean(xb) and DW^T mean(xb));
-// EB [TC][EP] (E of the chunk, EP = NMAX*DIM + 1, or NMAX*DIM + 4 in the
-// tensor-core form where a row first holds the scaled positions and its
-// element NMAX*DIM flags an active pair; also holds xi^{K-1} after the last iteration); RS2 [T] (pair
-// residual per t); RSB [NQ][NMAX] (ball residual partials); tensor-core form
-// only: CF [16 MT][4][4] words, the coefficient rows r = x * NMAX + i as MMA
-// A fragments (per lane quad t4: k pairs (2 t4, 2 t4 + 8) rounded to 16 bits,
-// then their rounding remainders), refreshed by every xi step; float32 form
-// with pair pruning only: CR [NMAX][DIM][12] (coefficients at the last full
-// pair test), CM [T][CMW] (candidate pair rows of that test), WC [T]
+// Shared-memory layout (floats). Head: (tensor-memory form) the MMA B
+// tables, then the float32 basis [T][36], operators, beta.
+// Per sample: C, LAM, XIB [NMAX][DIM][12]; PG [NPG][NMAX][DIM][12] (partials
+// of F^T q, later r; one in the tensor-memory form); MC, MR
+// [DIM][12] (forward: MR holds the xi step's mean term DW mean(c) + DS
+// mean(r); adjoint: DS^T mean(xb) and DW^T mean(xb)); EB [TC][EP] (E of the
+// chunk, EP = NMAX*DIM + 1, or NMAX*DIM + 4 in the tensor-memory form, whose
+// element NMAX*DIM flags an active pair; also holds xi^{K-1} after the last
+// iteration); RS2 [T] (pair residual per t); RSB [NQ][NMAX] (ball residual
+// partials); with pair pruning: CR [NMAX][DIM][12] (coefficients at the last
+// full pair test), CM [T][CMW] (candidate pair rows of that test), WC [T]
 // (candidate workspace rows: robots near or outside the workspace), RF (drift
 // of the coefficients since then, as the bit pattern of a non-negative float).
 struct Lay {
-  int RS, EP, TC, NQ, T, nmax, dim;
-  int C, LAM, XIB, PG, MC, MR, EB, RS2, RSB, FPP, FPR, XB, LB, GXB, U, CW, CF, CR, CM, WC, RF, CMW, SB;
-  int head, TH, bno, bto, opso, betao;
-  __host__ __device__ Lay(int dim_, int nmax_, int T_, int TC_, int NQ_, bool bwd = false, bool tcm = false,
-                          bool cand = false, int tmp = -1) {
+  int RS, EP, TC, NQ, NPG, PQ1, T, nmax, dim;
+  int C, LAM, XIB, PG, MC, MR, EB, RS2, RSB, FPP, FPR, XB, LB, GXB, U, CW, CR, CM, WC, RF, CMW, SB;
+  int head, basis, opso, betao;
+  __host__ __device__ Lay(int dim_, int nmax_, int T_, int TC_, int NQ_, bool bwd = false, bool cand = false,
+                          int tmp = -1) {
     dim = dim_; nmax = nmax_; T = T_; TC = TC_; NQ = NQ_;
+    // partials of F^T q in shared memory: one per time range (NPG = NQ),
+    // partial 0 at PG and partial q >= 1 at PQ1 + (q - 1) nmax RS; one in
+    // the tensor-memory form (its warp groups sum theirs through TMEM)
+    NPG = tmp >= 0 ? 1 : NQ;
+    const int npg_smem = NPG;
     RS = dim * NP;
     // tmp >= 0: tensor-memory form with operand format tmp (0 tf32, 1 bf16,
-    // 2 fp16): chunk-buffer rows as in the tensor-core form (positions
-    // first, 16-byte aligned, the active-pair flag at NMAX * DIM)
-    EP = nmax * dim + ((tcm || tmp >= 0) ? 4 : 1);
+    // 2 fp16): chunk-buffer rows 16-byte aligned with the active-pair flag
+    // at NMAX * DIM
+    EP = nmax * dim + (tmp >= 0 ? 4 : 1);
     C = 0;
     LAM = C + nmax * RS;
     XIB = LAM + nmax * RS;
     PG = XIB + nmax * RS;
-    MC = PG + NQ * nmax * RS;
+    MC = PG + npg_smem * nmax * RS;
     MR = MC + dim * NP;
     EB = MR + dim * NP;
     int eb = TC * EP;
     if (eb < nmax * RS) eb = nmax * RS;
+    PQ1 = PG + nmax * RS;
     RS2 = EB + ((eb + 3) / 4) * 4;
     RSB = RS2 + T;
     FPP = RSB + NQ * nmax;
@@ -129,29 +127,19 @@ struct Lay {
     GXB = LB + (bwd ? nmax * RS : 0);
     U = GXB + (bwd ? nmax * RS : 0);
     CW = U + (bwd ? nmax * RS : 0);
-    CF = CW + (bwd ? nmax * RS : 0);
     // pair pruning (float32 forward): reference coefficients, candidate
     // pair masks per (t) of mask_pair_words rounded to 4 words, workspace
     // candidate robots per (t), drift word
     CMW = cand ? (mask_pair_words(nmax) + 3) / 4 * 4 : 0;
-    CR = CF + (tcm ? ((dim * nmax + 15) / 16) * 256 : 0);
+    CR = CW + (bwd ? nmax * RS : 0);
     CM = CR + (cand ? nmax * RS : 0);
     WC = CM + T * CMW;
     RF = WC + (cand ? ((T + 3) / 4) * 4 : 0);
     SB = RF + (cand ? 4 : 0);
-    TH = (T + 1) / 2;
-    bno = 0;
-    if (tmp >= 0) {
-      // the MMA B tables (Pd, Pdd; rounded and remainder)
-      bto = 0;
-      opso = TM_TABLES * tm_tab_bytes(T, TC, tmp) / 4;
-    } else if (tcm) {
-      bto = T * 48;
-      opso = bto + ((6 * NV * TH + 3) / 4) * 4;
-    } else {
-      bto = 0;
-      opso = T * BASIS_ROW;
-    }
+    // head: (tensor-memory form) the MMA B tables (Pd, Pdd; rounded and
+    // remainder), then the float32 basis [T][36], the operators and beta
+    basis = tmp >= 0 ? TM_TABLES * tm_tab_bytes(T, TC, tmp) / 4 : 0;
+    opso = basis + T * BASIS_ROW;
     betao = opso + 4 * NV * NP;
     head = betao + nmax * RS;
   }
@@ -220,6 +208,22 @@ __device__ __forceinline__ void pair_update(const float (&pi)[DIM], const float 
       res2 = fmaf(q[x], q[x], res2);
     }
   }
+}
+
+// Pair row (i < j) of bit idx of an activity / candidate mask (row-major
+// upper triangle of NMAX x NMAX, the inverse of pair_bit): row i is the
+// largest with start s_i = i (2 NMAX - i - 1) / 2 <= idx, from the root of
+// the quadratic, corrected by one where the float root rounds across an
+// integer.
+template <int NMAX>
+__device__ __forceinline__ void pair_of_bit(int idx, int& i, int& j) {
+  constexpr float b = 2.0f * NMAX - 1.0f;
+  int r = (int)((b - sqrtf(b * b - 8.0f * (float)idx)) * 0.5f);
+  r = max(0, min(r, NMAX - 2));
+  if ((r + 1) * (2 * NMAX - r - 2) / 2 <= idx) ++r;
+  else if (r * (2 * NMAX - r - 1) / 2 > idx) --r;
+  i = r;
+  j = idx - r * (2 * NMAX - r - 1) / 2 + r + 1;
 }
 
 // Positions in the pair phase are kept scaled by M_a^-1 = diag(1/a, 1/a, 1/b),
@@ -319,21 +323,18 @@ __device__ __forceinline__ void ws_row(const float (&ps)[DIM], float (&Ei)[DIM],
   }
 }
 
-// Pair phase of one chunk [t0, t0 + TCc). With TCM (tensor-core form) the
-// scaled positions are already in the lane's chunk-buffer row, and the row's
-// element NMAX*DIM is set to 1 when some pair of the row is active. With
-// MASKS the lane's activity-mask row (mk + (s T + t) mask_words) is cleared
-// and the bit of every active pair row is set.
-// With CAND (float32 form, prune on) the CTA runs the candidate path while
-// the drift words of all its samples allow it: only the recorded candidate
-// rows are tested, the robots' positions computed on demand and E
-// accumulated in the row; otherwise every sample gets a full test, records
-// its candidates and (in the first chunk) copies C to the reference
-// coefficients.
-// FLAG (default: as TCM) writes the row's active-pair flag and stores the
-// row in 16-byte pieces (rows of NMAX*DIM + 4 floats) without the positions
-// being pre-staged (the tensor-memory form).
-template <int DIM, int NMAX, bool TCM = false, bool MASKS = false, bool CAND = false, bool FLAG = TCM>
+// Pair phase of one chunk [t0, t0 + TCc). With MASKS the lane's
+// activity-mask row (mk + (s T + t) mask_words) is cleared and the bit of
+// every active pair row is set.
+// With CAND (pair pruning on) each sample is tested in full (recording its
+// candidates and, in the first chunk, copying C to the reference
+// coefficients) when its drift word requires it, otherwise only its recorded
+// candidate rows are tested, the robots' positions computed on demand and E
+// accumulated in the row.
+// FLAG (tensor-memory form) writes the row's active-pair flag and stores the
+// row in 16-byte pieces (rows of NMAX*DIM + 4 floats); a row whose flag is
+// clear is left as it is (never read).
+template <int DIM, int NMAX, bool MASKS = false, bool CAND = false, bool FLAG = false>
 __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G, int N, int t0, int TCc,
                            const ProblemConsts& pc, bool want_res, int warp, int nwarps, int lane,
                            unsigned* mk = nullptr, bool prune = false) {
@@ -350,7 +351,7 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
     float* blk = SAMP + (size_t)s * L.SB;
     const float* Cs = blk + L.C;
     float Pr[NV];
-    if (!TCM || CAND) row_from(BASIS + (size_t)t * BASIS_ROW, Pr);   // TCM: the global float32 basis
+    row_from(BASIS + (size_t)t * BASIS_ROW, Pr);
     float E[NMAX][DIM];
 #pragma unroll
     for (int i = 0; i < NMAX; ++i)
@@ -372,8 +373,10 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
     };
     // pair pruning: full test (and record candidates) or candidates only.
     // The decision is taken for the whole CTA (a full test of every sample as
-    // soon as one sample needs it), so that the warps of a phase do the same
-    // kind of work and none waits at the barrier for a full test of another.
+    // soon as one sample needs it): a full test of one sample resets the
+    // drift of all, so the CTA runs fewer full-test iterations than with a
+    // decision per sample (measured: 22 against 38 of 200 on the bench
+    // workload), and the warps of a phase do the same kind of work.
     bool refresh = true;
     unsigned* cmrow = nullptr;
     if (CAND) {
@@ -404,8 +407,20 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
     if (CAND && !__any_sync(FULL, refresh)) {
       // candidate path: no warp-wide votes below, lanes run their own lists
       e_in_row = true;
+      // FLAG: the row is cleared (16-byte stores) only when the lane meets
+      // its first active row; a row whose flag stays clear is never read
+      bool zeroed = !FLAG;
+      auto ensure_zero = [&]() {
+        if (FLAG && !zeroed) {
+#pragma unroll
+          for (int q = 0; q < NMAX * DIM / 4; ++q)
+            reinterpret_cast<float4*>(ebw)[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          zeroed = true;
+        }
+      };
       if (valid) {
-        for (int q = 0; q < N * DIM; ++q) ebw[q] = 0.0f;
+        if (!FLAG)
+          for (int q = 0; q < N * DIM; ++q) ebw[q] = 0.0f;
         unsigned w[(PW + 3) / 4 * 4];
         const uint4* c4 = reinterpret_cast<const uint4*>(cmrow);
 #pragma unroll
@@ -417,14 +432,10 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
         for (int q = 0; q < PW; ++q) {
           unsigned m = w[q];
           while (m) {
-            int idx = q * 32 + __ffs(m) - 1;
+            const int idx = q * 32 + __ffs(m) - 1;
             m &= m - 1;
-            int i = 0;
-            while (idx >= NMAX - 1 - i) {   // row-major upper triangle
-              idx -= NMAX - 1 - i;
-              ++i;
-            }
-            const int j = i + 1 + idx;
+            int i, j;
+            pair_of_bit<NMAX>(idx, i, j);
             float pi[DIM], pj[DIM];
             state<DIM>(Pr, Cs + i * RS, pi);
             state<DIM>(Pr, Cs + j * RS, pj);
@@ -439,6 +450,7 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
               for (int x = 0; x < DIM; ++x) Ei[x] = Ej[x] = 0.0f;
               mark(i, j, true);
               pair_apply_scaled<DIM>(pi, pj, Ei, Ej, pc, res2);
+              ensure_zero();
 #pragma unroll
               for (int x = 0; x < DIM; ++x) {
                 ebw[i * DIM + x] += Ei[x];
@@ -460,43 +472,33 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
               Ei[x] = 0.0f;
             }
             ws_row<DIM, NMAX, MASKS>(pi, Ei, true, i, pc, res2, mrow);
+            bool act = false;
 #pragma unroll
-            for (int x = 0; x < DIM; ++x) ebw[i * DIM + x] += Ei[x];
+            for (int x = 0; x < DIM; ++x) act |= Ei[x] != 0.0f;
+            if (act || !FLAG) {
+              ensure_zero();
+#pragma unroll
+              for (int x = 0; x < DIM; ++x) ebw[i * DIM + x] += Ei[x];
+            }
           }
         }
+        if (FLAG) ebw[NMAX * DIM] = zeroed ? 1.0f : 0.0f;
       }
     } else if (NMAX <= 16) {
       // scaled positions of all robots in registers; lanes past the chunk get
       // far-apart dummies so that none of their rows tests active
       float p[NMAX][DIM];
-      if (TCM) {
-        // the row is 16-byte aligned (EP is a multiple of 4)
-        float pr[NMAX * DIM];
-        const float4* e4 = reinterpret_cast<const float4*>(ebw);
 #pragma unroll
-        for (int q = 0; q < NMAX * DIM / 4; ++q) {
-          const float4 v = e4[q];
-          pr[4 * q] = v.x; pr[4 * q + 1] = v.y; pr[4 * q + 2] = v.z; pr[4 * q + 3] = v.w;
+      for (int i = 0; i < NMAX; ++i) {
+        if (i < N) {
+          state<DIM>(Pr, Cs + i * RS, p[i]);
+#pragma unroll
+          for (int x = 0; x < DIM; ++x) p[i][x] *= (x == 2 ? pc.inv_b : pc.inv_a);
+        } else {
+#pragma unroll
+          for (int x = 0; x < DIM; ++x) p[i][x] = 0.0f;
         }
-#pragma unroll
-        for (int i = 0; i < NMAX; ++i) {
-#pragma unroll
-          for (int x = 0; x < DIM; ++x) p[i][x] = (i < N) ? pr[i * DIM + x] : 0.0f;
-          if (!valid) p[i][0] = 4096.0f * (float)i;
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < NMAX; ++i) {
-          if (i < N) {
-            state<DIM>(Pr, Cs + i * RS, p[i]);
-#pragma unroll
-            for (int x = 0; x < DIM; ++x) p[i][x] *= (x == 2 ? pc.inv_b : pc.inv_a);
-          } else {
-#pragma unroll
-            for (int x = 0; x < DIM; ++x) p[i][x] = 0.0f;
-          }
-          if (!valid) p[i][0] = 4096.0f * (float)i;
-        }
+        if (!valid) p[i][0] = 4096.0f * (float)i;
       }
       // a row of pairs (i, j > i) is tested without branches; only a row that
       // is active on some lane of the warp is walked pair by pair. Candidate
@@ -563,16 +565,14 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
       // scaled positions staged once in the lane's own row of the chunk
       // buffer (which later receives E); robots in blocks of 8 reloaded
       // from there, each later robot tested against a block in one group
-      if (!TCM) {
 #pragma unroll
-        for (int i = 0; i < NMAX; ++i) {
-          if (i < N) {
-            float pi[DIM];
-            state<DIM>(Pr, Cs + i * RS, pi);
-            if (valid)
+      for (int i = 0; i < NMAX; ++i) {
+        if (i < N) {
+          float pi[DIM];
+          state<DIM>(Pr, Cs + i * RS, pi);
+          if (valid)
 #pragma unroll
-              for (int x = 0; x < DIM; ++x) ebw[i * DIM + x] = pi[x] * (x == 2 ? pc.inv_b : pc.inv_a);
-          }
+            for (int x = 0; x < DIM; ++x) ebw[i * DIM + x] = pi[x] * (x == 2 ? pc.inv_b : pc.inv_a);
         }
       }
 #pragma unroll
@@ -665,8 +665,7 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
     if (valid) {
       float* eb = blk + L.EB + tl * L.EP;
       if (e_in_row) {
-        // candidate path: E is already in the row
-        if (FLAG) eb[NMAX * DIM] = res2 > 0.0f ? 1.0f : 0.0f;
+        // candidate path: E (and with FLAG the row's flag) is already in the row
       } else if (FLAG) {
         // whole row in 16-byte stores (E of robots >= N is zero); the row
         // stride is a multiple of 4 floats, scalar stores would conflict
@@ -813,307 +812,6 @@ __device__ void contract_phase(float* SAMP, const Lay& L, const float* BASIS, in
   }
 }
 
-// ---- tensor-core form ------------------------------------------------------
-//
-// The per-sample contractions run on warp-level MMAs with 16-bit operands and
-// float32 accumulation. Rows of the coefficient operand are r = x * NMAX + i
-// (axis-major), so that (NMAX being a multiple of 8) the lane with group g
-// holds, in the accumulators, every axis of robots i = g (mod 8): the ball
-// projections need no data exchange.
-
-// Writes coefficient row r (11 values c, k >= 11 zero) into CF: per lane
-// quad t4 the words {hi(2 t4), hi(2 t4 + 8), lo(2 t4), lo(2 t4 + 8)}, each
-// packing k and k + 1 (hi = rounded to 16 bits, lo = rounding remainder).
-template <int PREC>
-__device__ __forceinline__ void cf_write_row(float* CF, int r, const float* c) {
-  uint4* row = reinterpret_cast<uint4*>(CF + r * 16);
-#pragma unroll
-  for (int t4 = 0; t4 < 4; ++t4) {
-    const int k0 = 2 * t4, k1 = 2 * t4 + 8;
-    const float a0 = c[k0], a1 = c[k0 + 1];
-    const float b0 = k1 < NV ? c[k1] : 0.0f, b1 = k1 + 1 < NV ? c[k1 + 1] : 0.0f;
-    uint4 w;
-    w.x = tc::pack2<PREC>(a0, a1);
-    w.y = tc::pack2<PREC>(b0, b1);
-    w.z = tc::pack2<PREC>(a0 - tc::round16<PREC>(a0), a1 - tc::round16<PREC>(a1));
-    w.w = tc::pack2<PREC>(b0 - tc::round16<PREC>(b0), b1 - tc::round16<PREC>(b1));
-    row[t4] = w;
-  }
-}
-
-// A fragments (rounded and remainder) of coefficient rows 16 mt .. 16 mt + 15.
-__device__ __forceinline__ void cf_frag(const float* CF, int mt, int g, int t4, uint32_t (&hi)[4],
-                                        uint32_t (&lo)[4]) {
-  const uint4 r0 = *reinterpret_cast<const uint4*>(CF + (16 * mt + g) * 16 + 4 * t4);
-  const uint4 r1 = *reinterpret_cast<const uint4*>(CF + (16 * mt + g + 8) * 16 + 4 * t4);
-  hi[0] = r0.x; hi[1] = r1.x; hi[2] = r0.y; hi[3] = r1.y;
-  lo[0] = r0.z; lo[1] = r1.z; lo[2] = r0.w; lo[3] = r1.w;
-}
-
-// CF of every sample from C (rows of robots >= N and padding rows zero).
-template <int DIM, int NMAX, int PREC>
-__device__ void cf_prepare(float* SAMP, const Lay& L, int G, int N, int tid, int nthr) {
-  constexpr int RS = DIM * NP;
-  constexpr int ROWS = ((DIM * NMAX + 15) / 16) * 16;
-  for (int v = tid; v < G * ROWS; v += nthr) {
-    const int s = v / ROWS, r = v % ROWS;
-    float* blk = SAMP + (size_t)s * L.SB;
-    float c[NV];
-    const int x = r / NMAX, i = r % NMAX;
-    const bool live = r < DIM * NMAX && i < N;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) c[k] = live ? blk[L.C + i * RS + x * NP + k] : 0.0f;
-    cf_write_row<PREC>(blk + L.CF, r, c);
-  }
-}
-
-// acc[0..1] += A (16 x 8: rows r, time steps (2 t4, 2 t4 + 1) in the low /
-// high half of a0 (row g) and a1 (row g + 8)) times the 8 x 16 basis block
-// of words b[nn] (columns k = 8 nn + g). SPLIT adds the products of the
-// operands' rounding remainders (three-term form), for bf16 operands.
-template <int PREC, bool SPLIT>
-__device__ __forceinline__ void resid_mma(float (&acc)[2][4], float v00, float v01, float v10, float v11,
-                                          const uint32_t (&bh)[2], const uint32_t (&bl)[2]) {
-  const uint32_t a0 = tc::pack2<PREC>(v00, v01), a1 = tc::pack2<PREC>(v10, v11);
-  if (SPLIT) {
-    const uint32_t l0 = tc::pack2<PREC>(v00 - tc::round16<PREC>(v00), v01 - tc::round16<PREC>(v01));
-    const uint32_t l1 = tc::pack2<PREC>(v10 - tc::round16<PREC>(v10), v11 - tc::round16<PREC>(v11));
-#pragma unroll
-    for (int nn = 0; nn < 2; ++nn) {
-      tc::mma8<PREC>(acc[nn], l0, l1, bh[nn]);
-      tc::mma8<PREC>(acc[nn], a0, a1, bl[nn]);
-    }
-  }
-#pragma unroll
-  for (int nn = 0; nn < 2; ++nn) tc::mma8<PREC>(acc[nn], a0, a1, bh[nn]);
-}
-
-// Positions of one chunk: p = P c for every (sample, robot, axis, t), scaled
-// by M_a^-1 and written to the chunk-buffer rows (the pair phase's input).
-// Three products (rounded c with rounded P, c's remainder with rounded P,
-// rounded c with P's remainder) recover about 16 bits of the operands.
-// Unit = (sample, block of 16 time steps); one warp per unit.
-template <int DIM, int NMAX, int PREC>
-__device__ void tc_positions_phase(float* SAMP, const Lay& L, const uint32_t* BN, int G, int N, int t0, int TCc,
-                                   const ProblemConsts& pc, int warp, int nwarps, int lane) {
-  constexpr int MT = (DIM * NMAX + 15) / 16;
-  const int g = lane >> 2, t4 = lane & 3;
-  const int nkb = (TCc + 15) >> 4;
-  for (int u = warp; u < G * nkb; u += nwarps) {
-    const int s = u / nkb, kb = u - s * nkb;
-    float* blk = SAMP + (size_t)s * L.SB;
-    uint32_t ah[MT][4], al[MT][4];
-#pragma unroll
-    for (int mt = 0; mt < MT; ++mt) cf_frag(blk + L.CF, mt, g, t4, ah[mt], al[mt]);
-#pragma unroll
-    for (int nt = 0; nt < 2; ++nt) {
-      const int tl = 16 * kb + 8 * nt + g;   // this lane's time step in the B operand
-      uint4 bw = make_uint4(0u, 0u, 0u, 0u);
-      if (tl < TCc) bw = *reinterpret_cast<const uint4*>(BN + (size_t)(t0 + tl) * 48 + 4 * t4);
-      const uint2 bh = make_uint2(bw.x, bw.y), bl = make_uint2(bw.z, bw.w);
-      const int to = 16 * kb + 8 * nt + 2 * t4;   // time step of d0 (d1: to + 1)
-#pragma unroll
-      for (int mt = 0; mt < MT; ++mt) {
-        float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        tc::mma16<PREC>(d, al[mt], bh.x, bh.y);
-        tc::mma16<PREC>(d, ah[mt], bl.x, bl.y);
-        tc::mma16<PREC>(d, ah[mt], bh.x, bh.y);
-#pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {
-          const int rb = 16 * mt + 8 * h2;
-          if (rb < DIM * NMAX) {
-            const int x = rb / NMAX, i = rb % NMAX + g;
-            const float sc = x == 2 ? pc.inv_b : pc.inv_a;
-            if (i < N) {
-              float* e = blk + L.EB + i * DIM + x;
-              if (to < TCc) e[to * L.EP] = d[2 * h2] * sc;
-              if (to + 1 < TCc) e[(to + 1) * L.EP] = d[2 * h2 + 1] * sc;
-            }
-          }
-        }
-      }
-    }
-  }
-}
-
-// Contraction phase of one chunk in the tensor-core form. Per unit (sample,
-// range q of 16-step blocks) and 8 time steps:
-//   V^T = C^T Pd^T, A^T = C^T Pdd^T            (m16n8k16, rows (axis, robot))
-//   ball test on the accumulators; if some lane of the warp is outside a
-//   ball, q = e - v in place and g += q Pd (m16n8k8 with the accumulator
-//   reused as the A operand: residual form, only small values in 16 bits)
-//   g += E P when a pair of the time steps is active (E from the chunk buffer)
-// g goes to the partial PG[q] like the float32 form.
-template <int DIM, int NMAX, int PREC>
-__device__ void tc_contract_phase(float* SAMP, const Lay& L, const uint32_t* BN, const uint32_t* BT, int G, int N,
-                                  int t0, int TCc, bool first_chunk, const ProblemConsts& pc, bool want_res,
-                                  int warp, int nwarps, int lane) {
-  constexpr int RS = DIM * NP;
-  constexpr int MT = (DIM * NMAX + 15) / 16;
-  constexpr int NJ = NMAX / 8;
-  constexpr bool SPLIT4 = PREC == 1;   // bf16: three-term residual products too
-  const int g = lane >> 2, t4 = lane & 3;
-  const int nkb = (TCc + 15) >> 4;
-  const int NQ = L.NQ;
-  const int kbq = (nkb + NQ - 1) / NQ;
-  const int TH = L.TH;
-  for (int u = warp; u < G * NQ; u += nwarps) {
-    const int s = u / NQ, q = u - s * NQ;
-    const int kb0 = q * kbq, kb1 = min(nkb, kb0 + kbq);
-    float* blk = SAMP + (size_t)s * L.SB;
-    uint32_t ah[MT][4], al[MT][4];
-#pragma unroll
-    for (int mt = 0; mt < MT; ++mt) cf_frag(blk + L.CF, mt, g, t4, ah[mt], al[mt]);
-    float acc[MT][2][4];
-#pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-      for (int nn = 0; nn < 2; ++nn)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) acc[mt][nn][r] = 0.0f;
-    float rb[NJ];
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) rb[j] = 0.0f;
-    for (int kb = kb0; kb < kb1; ++kb) {
-#pragma unroll
-      for (int nt = 0; nt < 2; ++nt) {
-        const int tl = 16 * kb + 8 * nt + g;
-        const int to = 16 * kb + 8 * nt + 2 * t4;
-        // BT word of time steps t0 + to, + 1 (clamped: past the chunk the
-        // other operand is zero)
-        const int tw = min((t0 + to) >> 1, L.TH - 1);
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {    // velocity, acceleration
-          if (b == 0 ? !pc.use_v : !pc.use_a) continue;
-          uint4 bw = make_uint4(0u, 0u, 0u, 0u);
-          if (tl < TCc) bw = *reinterpret_cast<const uint4*>(BN + ((size_t)(t0 + tl) * 3 + 1 + b) * 16 + 4 * t4);
-          float D[MT][4];
-#pragma unroll
-          for (int mt = 0; mt < MT; ++mt) {
-            D[mt][0] = D[mt][1] = D[mt][2] = D[mt][3] = 0.0f;
-            tc::mma16<PREC>(D[mt], al[mt], bw.x, bw.y);
-            tc::mma16<PREC>(D[mt], ah[mt], bw.z, bw.w);
-            tc::mma16<PREC>(D[mt], ah[mt], bw.x, bw.y);
-          }
-          const float rmax = b == 0 ? pc.v_max : pc.a_max;
-          const float r2 = rmax * rmax;
-          bool out = false;
-#pragma unroll
-          for (int j = 0; j < NJ; ++j)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              float n2 = 0.0f;
-#pragma unroll
-              for (int x = 0; x < DIM; ++x) {
-                const int base = x * NMAX + 8 * j;
-                const float v = D[base / 16][2 * ((base / 8) & 1) + h];
-                n2 = fmaf(v, v, n2);
-              }
-              out |= n2 > r2;
-            }
-          if (__any_sync(FULL, out)) {
-#pragma unroll
-            for (int j = 0; j < NJ; ++j)
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                float v[DIM], qb[DIM], rl = 0.0f;
-#pragma unroll
-                for (int x = 0; x < DIM; ++x) {
-                  const int base = x * NMAX + 8 * j;
-                  v[x] = D[base / 16][2 * ((base / 8) & 1) + h];
-                }
-                ball_residual<DIM>(v, rmax, qb, rl);
-#pragma unroll
-                for (int x = 0; x < DIM; ++x) {
-                  const int base = x * NMAX + 8 * j;
-                  D[base / 16][2 * ((base / 8) & 1) + h] = qb[x];
-                }
-                rb[j] += rl;
-              }
-            uint32_t bh[2], bl[2];
-#pragma unroll
-            for (int nn = 0; nn < 2; ++nn) {
-              const int k = 8 * nn + g;
-              bh[nn] = k < NV ? BT[((1 + b) * NV + k) * TH + tw] : 0u;
-              bl[nn] = (SPLIT4 && k < NV) ? BT[((4 + b) * NV + k) * TH + tw] : 0u;
-            }
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt)
-              resid_mma<PREC, SPLIT4>(acc[mt], D[mt][0], D[mt][1], D[mt][2], D[mt][3], bh, bl);
-          }
-        }
-        // pair residuals E of time steps to, to + 1
-        const float* eb = blk + L.EB;
-        bool ea = false;
-        if (to < TCc) ea |= eb[to * L.EP + NMAX * DIM] != 0.0f;
-        if (to + 1 < TCc) ea |= eb[(to + 1) * L.EP + NMAX * DIM] != 0.0f;
-        if (__any_sync(FULL, ea)) {
-          uint32_t bh[2], bl[2];
-#pragma unroll
-          for (int nn = 0; nn < 2; ++nn) {
-            const int k = 8 * nn + g;
-            bh[nn] = k < NV ? BT[k * TH + tw] : 0u;
-            bl[nn] = (SPLIT4 && k < NV) ? BT[(3 * NV + k) * TH + tw] : 0u;
-          }
-#pragma unroll
-          for (int mt = 0; mt < MT; ++mt) {
-            float e[2][2];
-#pragma unroll
-            for (int h2 = 0; h2 < 2; ++h2) {
-              const int rbase = 16 * mt + 8 * h2;
-              e[h2][0] = e[h2][1] = 0.0f;
-              if (rbase < DIM * NMAX) {
-                const int x = rbase / NMAX, i = rbase % NMAX + g;
-                if (i < N) {
-                  if (to < TCc) e[h2][0] = eb[to * L.EP + i * DIM + x];
-                  if (to + 1 < TCc) e[h2][1] = eb[(to + 1) * L.EP + i * DIM + x];
-                }
-              }
-            }
-            resid_mma<PREC, SPLIT4>(acc[mt], e[0][0], e[0][1], e[1][0], e[1][1], bh, bl);
-          }
-        }
-      }
-    }
-    // partial of F^T q of this range: acc rows (axis, robot), columns k
-#pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-      for (int h2 = 0; h2 < 2; ++h2) {
-        const int rbase = 16 * mt + 8 * h2;
-        if (rbase < DIM * NMAX) {
-          const int x = rbase / NMAX, i = rbase % NMAX + g;
-          if (i < N) {
-            float* pg = blk + L.PG + q * NMAX * RS + i * RS + x * NP;
-#pragma unroll
-            for (int nn = 0; nn < 2; ++nn)
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                const int k = 8 * nn + 2 * t4 + h;
-                if (k < NV) {
-                  const float v = acc[mt][nn][2 * h2 + h];
-                  pg[k] = first_chunk ? v : pg[k] + v;
-                }
-              }
-          }
-        }
-      }
-    if (want_res) {
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        float r = rb[j];
-        r += __shfl_xor_sync(FULL, r, 1);
-        r += __shfl_xor_sync(FULL, r, 2);
-        const int i = g + 8 * j;
-        if (t4 == 0 && i < N) {
-          float* p = blk + L.RSB + q * NMAX + i;
-          *p = first_chunk ? r : *p + r;
-        }
-      }
-    }
-  }
-}
-
 // Final residual of one (sample, t): ||F xi^K - e(xi^{K-1})||^2 over the rows
 // at t, written to RS2[t]. Cp holds xi^{K-1}, C holds xi^K.
 template <int DIM, int NMAX>
@@ -1227,11 +925,10 @@ struct Cta {
   int N, G, robot_off, gsample0;
   long long per_sample, coef0, mask0;
   float *BASIS, *OPS, *BETA, *SAMP;
-  uint32_t *BN, *BT;
   int tid, nthr, warp, lane, nwarps;
-  __device__ Cta(const SceneDesc* sc, int n_scenes, int T, int tc, int nq, bool bwd, float* sm, bool tcm = false,
-                 bool cand = false, int tmp = -1)
-      : L(DIM, NMAX, T, tc, nq, bwd, tcm, cand, tmp) {
+  __device__ Cta(const SceneDesc* sc, int n_scenes, int T, int tc, int nq, bool bwd, float* sm, bool cand = false,
+                 int tmp = -1)
+      : L(DIM, NMAX, T, tc, nq, bwd, cand, tmp) {
     int sidx = 0;
     for (int q = 1; q < n_scenes; ++q) {
       if (sc[q].cta_begin <= (int)blockIdx.x) sidx = q;
@@ -1246,9 +943,7 @@ struct Cta {
     per_sample = (long long)DIM * N * NV;
     coef0 = sc[sidx].coef_off + (long long)s_first * per_sample;
     mask0 = sc[sidx].mask_off + (long long)s_first * T * mask_words(NMAX);
-    BASIS = (tcm || tmp >= 0) ? nullptr : sm;
-    BN = tcm ? reinterpret_cast<uint32_t*>(sm + L.bno) : nullptr;
-    BT = tcm ? reinterpret_cast<uint32_t*>(sm + L.bto) : nullptr;
+    BASIS = sm + L.basis;
     OPS = sm + L.opso;
     BETA = sm + L.betao;
     SAMP = sm + L.head;
@@ -1265,53 +960,17 @@ struct Cta {
   __device__ float* blk(int s) const { return SAMP + (size_t)s * L.SB; }
 };
 
-// 16-bit operand tables of the tensor-core form from the float32 basis
-// [T][36] (P, Pd, Pdd rows of 12): BN word (t, m, t4, e) packs k0 = 2 t4 +
-// 8 (e & 1) and k0 + 1 of matrix m, rounded (e < 2) or the rounding
-// remainder (e >= 2); BT word (l, m, k, t / 2) packs time steps t and t + 1
-// of column k, rounded (l = 0) or the rounding remainder (l = 1). Entries
-// past T or past k = 10 are zero.
-template <int PREC>
-__device__ void tc_tables(const Lay& L, int T, const float* gb, uint32_t* BN, uint32_t* BT, int tid, int nthr) {
-  for (int v = tid; v < T * 48; v += nthr) {
-    const int t = v / 48, m = (v >> 4) % 3, t4 = (v >> 2) & 3, e = v & 3;
-    const int k0 = 2 * t4 + 8 * (e & 1);
-    const float* row = gb + (size_t)t * BASIS_ROW + m * NP;
-    float x0 = k0 < NV ? row[k0] : 0.0f;
-    float x1 = k0 + 1 < NV ? row[k0 + 1] : 0.0f;
-    if (e >= 2) {
-      x0 -= tc::round16<PREC>(x0);
-      x1 -= tc::round16<PREC>(x1);
-    }
-    BN[v] = tc::pack2<PREC>(x0, x1);
-  }
-  const int TH = L.TH;
-  for (int v = tid; v < 6 * NV * TH; v += nthr) {
-    const int l = v / (3 * NV * TH), m = (v / (NV * TH)) % 3, k = (v / TH) % NV, t = 2 * (v % TH);
-    float x0 = t < T ? gb[(size_t)t * BASIS_ROW + m * NP + k] : 0.0f;
-    float x1 = t + 1 < T ? gb[(size_t)(t + 1) * BASIS_ROW + m * NP + k] : 0.0f;
-    if (l == 1) {
-      x0 -= tc::round16<PREC>(x0);
-      x1 -= tc::round16<PREC>(x1);
-    }
-    BT[v] = tc::pack2<PREC>(x0, x1);
-  }
-}
-
-// Basis table (PREC 0: float32 copy; 1 / 2: 16-bit operand tables of the
-// warp-MMA form; 3: none), operators of this N and
+// Basis table (float32 copy), operators of this N and
 // beta_i = R1 b_i + (R0 - R1) bbar.
-template <int DIM, int NMAX, int PREC = 0>
+template <int DIM, int NMAX>
 __device__ void prologue(const Cta<DIM, NMAX>& c, int T, const float4* basis, const float* ops,
                          const float* start, const float* goal, const float* start_va, const float* goal_va) {
   constexpr int RS = DIM * NP;
-  if constexpr (PREC == 0) {
+  {
     const float4* b4 = basis;
     float4* s4 = reinterpret_cast<float4*>(c.BASIS);
     for (int v = c.tid; v < T * 9; v += c.nthr) s4[v] = b4[v];
-  } else if constexpr (PREC == 1 || PREC == 2) {
-    tc_tables<PREC>(c.L, T, reinterpret_cast<const float*>(basis), c.BN, c.BT, c.tid, c.nthr);
-  }   // PREC 3: the tensor-memory form builds its own tables
+  }
   const float* gops = ops + (size_t)c.N * OPS_STRIDE;
   for (int v = c.tid; v < 4 * NV * NP; v += c.nthr) c.OPS[v] = gops[v];
   const int N = c.N;
@@ -1365,7 +1024,7 @@ __device__ void load_state(const Cta<DIM, NMAX>& c, const float* xi, const float
     b[c.L.C + rem] = cv;
     b[c.L.LAM + rem] = l;
     b[c.L.XIB + rem] = (i < c.N && k < NV) ? xi_bar_src[c.gidx(s, x, i, k)] : 0.0f;
-    for (int q = 0; q < c.L.NQ; ++q) b[c.L.PG + q * NMAX * RS + rem] = 0.0f;
+    for (int q = 0; q < c.L.NPG; ++q) b[c.L.PG + q * NMAX * RS + rem] = 0.0f;
   }
 }
 
@@ -1441,7 +1100,7 @@ __device__ void solve_lambda_means(const Cta<DIM, NMAX>& c, const ProblemConsts&
           for (int u = 0; u < 4; ++u) {
             const int o = (i + u) * RS + o0;
             float g = blk[L.PG + o];
-            for (int q = 1; q < L.NQ; ++q) g += blk[L.PG + q * NMAX * RS + o];
+            for (int q = 1; q < L.NPG; ++q) g += blk[L.PQ1 + (q - 1) * NMAX * RS + o];
             gq[u] = g;
             lq[u] = blk[L.LAM + o];
             xq[u] = blk[L.XIB + o];
@@ -1462,7 +1121,7 @@ __device__ void solve_lambda_means(const Cta<DIM, NMAX>& c, const ProblemConsts&
         for (; i < N; ++i) {
           const int o = i * RS + o0;
           float g = blk[L.PG + o];
-          for (int q = 1; q < L.NQ; ++q) g += blk[L.PG + q * NMAX * RS + o];
+          for (int q = 1; q < L.NPG; ++q) g += blk[L.PQ1 + (q - 1) * NMAX * RS + o];
           const float lold = blk[L.LAM + o];
           const float lam = fmaf(rho, g, lold);
           dl2 = fmaf(lam - lold, lam - lold, dl2);
@@ -1501,11 +1160,13 @@ __device__ void solve_lambda_means(const Cta<DIM, NMAX>& c, const ProblemConsts&
 // step xi_i = W1 c_i + S1 r_i + (DW mean(c) + DS mean(r)) + beta_i with the
 // operators pre-stored from the KKT system (Eq. xi_step). Writes the new row
 // to C (and the old one to the EB region when keep_prev), raises the
-// sample's drift word (pair pruning) and (fp) records ||xi' - xi||^2 of the
-// row; out receives the new row (entry NV zero).
-template <int DIM, int NMAX, bool CAND>
+// sample's drift word (pair pruning; with ATOMIC_DRIFT false the row's drift
+// goes to *drift_bits instead, as the bit pattern of a non-negative float)
+// and (fp) records ||xi' - xi||^2 of the row; out receives the new row
+// (entry NV zero).
+template <int DIM, int NMAX, bool CAND, bool ATOMIC_DRIFT = true>
 __device__ __forceinline__ void xi_step_row(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, int s, int i, int x,
-                                            bool keep_prev, bool fp, float (&out)[NP]) {
+                                            bool keep_prev, bool fp, float (&out)[NP], int* drift_bits = nullptr) {
   constexpr int RS = DIM * NP;
   const Lay& L = c.L;
   float* blk = c.blk(s);
@@ -1549,7 +1210,10 @@ __device__ __forceinline__ void xi_step_row(const Cta<DIM, NMAX>& c, const Probl
       d = fmaxf(d, e);
       bad |= !(e == e);
     }
-    atomicMax(reinterpret_cast<int*>(blk + L.RF), __float_as_int(bad ? INFINITY : d));
+    if (ATOMIC_DRIFT)
+      atomicMax(reinterpret_cast<int*>(blk + L.RF), __float_as_int(bad ? INFINITY : d));
+    else
+      *drift_bits = __float_as_int(bad ? INFINITY : d);
   }
   float4* o4 = reinterpret_cast<float4*>(blk + L.C + o);
   float4* p4 = reinterpret_cast<float4*>(blk + L.EB + o);
@@ -1564,10 +1228,10 @@ __device__ __forceinline__ void xi_step_row(const Cta<DIM, NMAX>& c, const Probl
 // One iteration of f_FP on every sample of the CTA (time chunks, then the
 // lambda step and the xi step). keep_prev stores xi^k in the EB region for
 // the final residual. fp (when set) adds ||z^{k+1} - z^k||^2 per sample to FPR.
-template <int DIM, int NMAX, int PREC = 0, bool MASKS = false, bool CAND = false>
+template <int DIM, int NMAX, bool MASKS = false, bool CAND = false>
 __device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, const float* xi_bar, int it,
                               bool keep_prev, float* hist, int total_samples, bool fp, unsigned* mslot = nullptr,
-                              bool prune = false, const float* gbasis = nullptr) {
+                              bool prune = false) {
   constexpr int RS = DIM * NP;
   const Lay& L = c.L;
   const int T = pc.T, N = c.N, G = c.G, TC = L.TC;
@@ -1576,26 +1240,15 @@ __device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, 
   const float invN = 1.0f / (float)N;
   for (int t0 = 0; t0 < T; t0 += TC) {
     const int TCc = min(TC, T - t0);
-    if constexpr (PREC != 0) {
-      // the positions from the MMAs are needed only by a full pair test
-      if (!CAND || cta_refresh<DIM>(c, L, pc, prune)) {
-        tc_positions_phase<DIM, NMAX, PREC>(c.SAMP, L, c.BN, G, N, t0, TCc, pc, c.warp, c.nwarps, c.lane);
-        __syncthreads();
-      }
-      pair_phase<DIM, NMAX, true, false, CAND>(c.SAMP, L, gbasis, G, N, t0, TCc, pc, want_res, c.warp, c.nwarps,
-                                               c.lane, nullptr, prune);
-      __syncthreads();
-      tc_contract_phase<DIM, NMAX, PREC>(c.SAMP, L, c.BN, c.BT, G, N, t0, TCc, t0 == 0, pc, want_res, c.warp,
-                                         c.nwarps, c.lane);
-    } else if (MASKS && mslot != nullptr) {
+    if (MASKS && mslot != nullptr) {
       unsigned* mk = mslot + c.mask0;
-      pair_phase<DIM, NMAX, false, true, CAND>(c.SAMP, L, c.BASIS, G, N, t0, TCc, pc, want_res, c.warp, c.nwarps,
+      pair_phase<DIM, NMAX, true, CAND>(c.SAMP, L, c.BASIS, G, N, t0, TCc, pc, want_res, c.warp, c.nwarps,
                                                c.lane, mk, prune);
       __syncthreads();
       contract_phase<DIM, NMAX, true>(c.SAMP, L, c.BASIS, G, N, t0, TCc, t0 == 0, pc, want_res, c.tid, c.nthr,
                                       mk);
     } else {
-      pair_phase<DIM, NMAX, false, false, CAND>(c.SAMP, L, c.BASIS, G, N, t0, TCc, pc, want_res, c.warp,
+      pair_phase<DIM, NMAX, false, CAND>(c.SAMP, L, c.BASIS, G, N, t0, TCc, pc, want_res, c.warp,
                                                 c.nwarps, c.lane, nullptr, prune);
       __syncthreads();
       contract_phase<DIM>(c.SAMP, L, c.BASIS, G, N, t0, TCc, t0 == 0, pc, want_res, c.tid, c.nthr);
@@ -1610,7 +1263,6 @@ __device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, 
     const int s = v / (N * DIM), i = (v / DIM) % N, x = v % DIM;
     float out[NP];
     xi_step_row<DIM, NMAX, CAND>(c, pc, s, i, x, keep_prev, fp, out);
-    if constexpr (PREC != 0) cf_write_row<PREC>(c.blk(s) + L.CF, x * NMAX + i, out);
   }
   __syncthreads();
   if (fp) {
@@ -1633,33 +1285,28 @@ __device__ void write_checkpoint(const Cta<DIM, NMAX>& c, float* ckpt, int ck, l
   store_state<DIM, NMAX>(c, base, base + total_coefs, 0);
 }
 
-// PREC 0: float32 form; 1 / 2: tensor-core form with bf16 / fp16 operands.
-// MASKS (float32 form with checkpoints): the iterations of the last
-// checkpoint segment also write their activity masks for the adjoint.
-template <int DIM, int NMAX, int MAXT, int PREC, bool MASKS = false>
+// MASKS (with checkpoints): the iterations of the last checkpoint segment
+// also write their activity masks for the adjoint.
+template <int DIM, int NMAX, int MAXT, bool MASKS = false>
 __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constant__ FusedArgs A) {
   extern __shared__ float4 smem4[];
   float* sm = reinterpret_cast<float*>(smem4);
   const ProblemConsts& pc = A.pc;
   const int T = pc.T;
   constexpr bool CAND = true;   // pair pruning (the 16-bit forms too)
-  const Cta<DIM, NMAX> c(A.sc, A.n_scenes, T, A.tc, A.nq, false, sm, PREC != 0, CAND);
+  const Cta<DIM, NMAX> c(A.sc, A.n_scenes, T, A.tc, A.nq, false, sm, CAND);
   if (c.G <= 0) return;
   const Lay& L = c.L;
   const int N = c.N, G = c.G;
   const bool fp = A.fp_res2 != nullptr;
 
-  prologue<DIM, NMAX, PREC>(c, T, A.basis, A.ops, A.start, A.goal, A.start_va, A.goal_va);
+  prologue<DIM, NMAX>(c, T, A.basis, A.ops, A.start, A.goal, A.start_va, A.goal_va);
   load_state<DIM, NMAX>(c, A.xi0, A.lam0, A.xi_bar, A.xi_bar);
   for (int s = c.tid; s < G; s += c.nthr) {
     c.blk(s)[L.FPR] = 0.0f;
     if (CAND) *reinterpret_cast<int*>(c.blk(s) + L.RF) = __float_as_int(INFINITY);   // first test is full
   }
   __syncthreads();
-  if constexpr (PREC != 0) {
-    cf_prepare<DIM, NMAX, PREC>(c.SAMP, L, G, N, c.tid, c.nthr);
-    __syncthreads();
-  }
 
   // checkpoints: (xi, lambda) at iterations 0, ck, 2 ck, ...; after them a
   // tail holding every iterate of the last segment (last_ck .. K), so that
@@ -1671,8 +1318,8 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
     if (A.ckpt && it % A.ck_every == 0) write_checkpoint<DIM, NMAX>(c, A.ckpt, it / A.ck_every, A.total_coefs);
     if (tail && it >= last_ck) write_checkpoint<DIM, NMAX>(c, tail, it - last_ck, A.total_coefs);
     unsigned* ms = (MASKS && A.amask && it >= last_ck) ? A.amask + (size_t)(it - last_ck) * A.amask_slot : nullptr;
-    fwd_iteration<DIM, NMAX, PREC, MASKS, CAND>(c, pc, A.xi_bar, it, it == pc.K - 1, A.hist, A.total_samples, fp,
-                                                ms, A.prune != 0, reinterpret_cast<const float*>(A.basis));
+    fwd_iteration<DIM, NMAX, MASKS, CAND>(c, pc, A.xi_bar, it, it == pc.K - 1, A.hist, A.total_samples, fp,
+                                                ms, A.prune != 0);
   }
   if (tail) write_checkpoint<DIM, NMAX>(c, tail, pc.K - last_ck, A.total_coefs);
 
@@ -1684,8 +1331,7 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
     if (rem / RS >= N) c.blk(s)[L.EB + rem] = 0.0f;
   }
   __syncthreads();
-  const float* rbasis = PREC == 0 ? c.BASIS : reinterpret_cast<const float*>(A.basis);
-  residual_phase<DIM, NMAX>(c.SAMP, L, rbasis, G, N, T, pc, c.warp, c.nwarps, c.lane);
+  residual_phase<DIM, NMAX>(c.SAMP, L, c.BASIS, G, N, T, pc, c.warp, c.nwarps, c.lane);
   __syncthreads();
   for (int s = c.tid; s < G; s += c.nthr) {
     const float* blk = c.blk(s);
@@ -1699,9 +1345,9 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
   store_state<DIM, NMAX>(c, A.xi_out, A.lam_out, 0);
 }
 
-template <int DIM, int NMAX, int MAXT, int PREC = 0, bool MASKS = false>
+template <int DIM, int NMAX, int MAXT, bool MASKS = false>
 cudaError_t launch_t(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st) {
-  auto k = fused_fwd_kernel<DIM, NMAX, MAXT, PREC, MASKS>;
+  auto k = fused_fwd_kernel<DIM, NMAX, MAXT, MASKS>;
   if (l.warps * 32 > MAXT) return cudaErrorInvalidConfiguration;
   k<<<l.n_ctas, l.warps * 32, l.smem, st>>>(a);
   return cudaGetLastError();

@@ -186,8 +186,8 @@ struct FusedLaunch {
   int n_ctas;
   int tc, nq;   // time chunk, contraction ranges
   size_t smem;  // dynamic shared memory bytes
-  int prec;     // 0 float32 form, 1 / 2 warp-MMA form with bf16 / fp16 operands,
-                // 3 / 4 / 5 tensor-memory form with tf32 / bf16 / fp16 operands
+  int prec;     // 0 float32 form, 3 / 4 / 5 tensor-memory form with tf32 / bf16 /
+                // fp16 operands (PREC_TM_*)
 };
 // Internal form codes (FusedLaunch::prec) of the tensor-memory form.
 constexpr int PREC_TM_TF32 = 3, PREC_TM_BF16 = 4, PREC_TM_FP16 = 5;

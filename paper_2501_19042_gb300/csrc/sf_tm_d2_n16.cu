@@ -3,22 +3,35 @@
 #include "sf_tm_kernel.cuh"
 
 namespace sf {
+// a.ckpt set: the training forward (checkpoints, activity masks)
 cudaError_t launch_tm_d2_n16(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st) {
-  if (l.prec == PREC_TM_TF32) return fused_impl::launch_tm_t<2, 16, 384, 0>(a, l, st);
-  if (l.prec == PREC_TM_BF16) return fused_impl::launch_tm_t<2, 16, 384, 1>(a, l, st);
-  if (l.prec == PREC_TM_FP16) return fused_impl::launch_tm_t<2, 16, 384, 2>(a, l, st);
+  const bool train = a.ckpt != nullptr;
+  if (l.prec == PREC_TM_TF32)
+    return train ? fused_impl::launch_tm_t<2, 16, 384, 0, true>(a, l, st)
+                 : fused_impl::launch_tm_t<2, 16, 384, 0>(a, l, st);
+  if (l.prec == PREC_TM_BF16)
+    return train ? fused_impl::launch_tm_t<2, 16, 384, 1, true>(a, l, st)
+                 : fused_impl::launch_tm_t<2, 16, 384, 1>(a, l, st);
+  if (l.prec == PREC_TM_FP16)
+    return train ? fused_impl::launch_tm_t<2, 16, 384, 2, true>(a, l, st)
+                 : fused_impl::launch_tm_t<2, 16, 384, 2>(a, l, st);
   return cudaErrorInvalidValue;
 }
 // prec: the handle's sf_precision (0 float32 -> tf32 operands)
 cudaError_t prepare_tm_d2_n16(int smem, int prec) {
   const int dyn = smem - (int)TM_STATIC_SMEM_RESERVE;
-  if (prec == 1)
-    return cudaFuncSetAttribute(fused_impl::tm_fwd_kernel<2, 16, 384, 1>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-  if (prec == 2)
-    return cudaFuncSetAttribute(fused_impl::tm_fwd_kernel<2, 16, 384, 2>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-  return cudaFuncSetAttribute(fused_impl::tm_fwd_kernel<2, 16, 384, 0>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e;
+  if (prec == 1) {
+    e = cudaFuncSetAttribute(fused_impl::tm_fwd_kernel<2, 16, 384, 1>, at, dyn);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_impl::tm_fwd_kernel<2, 16, 384, 1, true>, at, dyn);
+  } else if (prec == 2) {
+    e = cudaFuncSetAttribute(fused_impl::tm_fwd_kernel<2, 16, 384, 2>, at, dyn);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_impl::tm_fwd_kernel<2, 16, 384, 2, true>, at, dyn);
+  } else {
+    e = cudaFuncSetAttribute(fused_impl::tm_fwd_kernel<2, 16, 384, 0>, at, dyn);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_impl::tm_fwd_kernel<2, 16, 384, 0, true>, at, dyn);
+  }
+  return e;
 }
 }  // namespace sf

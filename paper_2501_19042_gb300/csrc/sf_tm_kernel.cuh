@@ -192,15 +192,18 @@ __device__ __forceinline__ TmLane tm_lane(const Cta<DIM, NMAX>& c, uint32_t tbas
 
 // TMEM pass of one chunk (after its pair phase): the velocity / acceleration
 // ball rows of this lane's robot from TMEM, F^T of their residuals and of the
-// pair residuals E (chunk-buffer rows, skipped where the row's active-pair
-// flag is clear on every lane of the warp) into g, the balls' squared
-// residuals into rb.
+// pair residuals E (chunk-buffer rows whose active-pair flag is set) into g,
+// the balls' squared residuals into rb. Per 8-step block every lane first
+// evaluates its 24 conditions (velocity outside, acceleration outside, pair
+// row active, per step) into one word; a single warp-wide OR then tells
+// which of the (rare) projections and F^T updates the warp has to run.
 template <int DIM, int NMAX>
 __device__ void tm_chunk_pass(const Cta<DIM, NMAX>& c, const TmLane& q, const ProblemConsts& pc, int t0, int TCc,
-                              int TCW, const float* gbasis, float (&g)[DIM][NV], float& rb) {
+                              int TCW, const float* gbasis, float (&g)[DIM][NV], float& rb, unsigned* mk) {
   const Lay& L = c.L;
   const float* blk = c.blk(q.valid ? q.s : 0);
-  const float vm2 = pc.v_max * pc.v_max, am2 = pc.a_max * pc.a_max;
+  const float vm2 = pc.use_v ? pc.v_max * pc.v_max : INFINITY;
+  const float am2 = pc.use_a ? pc.a_max * pc.a_max : INFINITY;
   for (int bk = q.cg; bk * 8 < TCc; bk += q.ncg) {
     const int tb = bk * 8;
     uint32_t v[DIM][8], a[DIM][8];
@@ -209,32 +212,52 @@ __device__ void tm_chunk_pass(const Cta<DIM, NMAX>& c, const TmLane& q, const Pr
       tcg::ld8(q.lanebase + (uint32_t)(x * TCW + tb), v[x]);
       tcg::ld8(q.lanebase + (uint32_t)((DIM + x) * TCW + tb), a[x]);
     }
+    // the E flags of the block's steps (independent of the TMEM loads)
+    float fl[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) fl[j] = (tb + j < TCc) ? blk[L.EB + (tb + j) * L.EP + NMAX * DIM] : 0.0f;
     tcg::wait_ld();
 #pragma unroll
     for (int x = 0; x < DIM; ++x) {
       tcg::tie(v[x]);
       tcg::tie(a[x]);
     }
+    uint32_t bits = 0u;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const int tl = tb + j;
-      if (tl >= TCc) break;   // warp-uniform
-      const bool live = q.valid;
-      const float* brow = gbasis + (size_t)(t0 + tl) * BASIS_ROW;
+      float nv = 0.0f, na = 0.0f;
+#pragma unroll
+      for (int x = 0; x < DIM; ++x) {
+        const float vx = __uint_as_float(v[x][j]), ax = __uint_as_float(a[x][j]);
+        nv = fmaf(vx, vx, nv);
+        na = fmaf(ax, ax, na);
+      }
+      const bool live = q.valid && tb + j < TCc;
+      bits |= (live && nv > vm2) ? (1u << j) : 0u;
+      bits |= (live && na > am2) ? (1u << (8 + j)) : 0u;
+      bits |= (live && fl[j] != 0.0f) ? (1u << (16 + j)) : 0u;
+    }
+    const uint32_t any = __reduce_or_sync(FULL, bits);
+    if (!any) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float* brow = gbasis + (size_t)(t0 + tb + j) * BASIS_ROW;
 #pragma unroll
       for (int b = 0; b < 2; ++b) {
-        if (b == 0 ? !pc.use_v : !pc.use_a) continue;
-        float w[DIM], n2 = 0.0f;
+        const uint32_t bit = 1u << (8 * b + j);
+        if (any & bit) {
+          // lanes whose row is inside the ball take q = 0 (w = 0)
+          const bool mine = (bits & bit) != 0u;
+          float w[DIM], qb[DIM], rl = 0.0f;
 #pragma unroll
-        for (int x = 0; x < DIM; ++x) {
-          w[x] = live ? __uint_as_float(b == 0 ? v[x][j] : a[x][j]) : 0.0f;
-          n2 = fmaf(w[x], w[x], n2);
-        }
-        const bool out = n2 > (b == 0 ? vm2 : am2);
-        if (__any_sync(FULL, out)) {
-          float qb[DIM], rl = 0.0f;
+          for (int x = 0; x < DIM; ++x) w[x] = mine ? __uint_as_float(b == 0 ? v[x][j] : a[x][j]) : 0.0f;
           ball_residual<DIM>(w, b == 0 ? pc.v_max : pc.a_max, qb, rl);
           rb += rl;
+          if (mk && mine) {   // activity mask of the ball row (training forward)
+            unsigned* mball = mk + ((size_t)q.s * L.T + t0 + tb + j) * mask_words(NMAX) + mask_pair_words(NMAX);
+            const int mb = b * NMAX + q.i;
+            atomicOr(mball + (mb >> 5), 1u << (mb & 31));
+          }
           float P[NV];
           row_from(brow + (1 + b) * NP, P);
 #pragma unroll
@@ -243,12 +266,13 @@ __device__ void tm_chunk_pass(const Cta<DIM, NMAX>& c, const TmLane& q, const Pr
             for (int k = 0; k < NV; ++k) g[x][k] = fmaf(P[k], qb[x], g[x][k]);
         }
       }
-      const float* eb = blk + L.EB + tl * L.EP;
-      const bool act = live && eb[NMAX * DIM] != 0.0f;
-      if (__any_sync(FULL, act)) {
+      const uint32_t ebit = 1u << (16 + j);
+      if (any & ebit) {
+        const bool mine = (bits & ebit) != 0u;
+        const float* eb = blk + L.EB + (tb + j) * L.EP + q.i * DIM;
         float e[DIM];
 #pragma unroll
-        for (int x = 0; x < DIM; ++x) e[x] = act ? eb[q.i * DIM + x] : 0.0f;
+        for (int x = 0; x < DIM; ++x) e[x] = mine ? eb[x] : 0.0f;
         float P[NV];
         row_from(brow, P);
 #pragma unroll
@@ -262,10 +286,10 @@ __device__ void tm_chunk_pass(const Cta<DIM, NMAX>& c, const TmLane& q, const Pr
 
 // One iteration of f_FP in the tensor-memory form (the MMAs of chunk 0 are in
 // flight on entry). Ends with the xi step, which rewrites A in TMEM.
-template <int DIM, int NMAX, int FMT, bool CAND>
+template <int DIM, int NMAX, int FMT, bool CAND, bool TRAIN>
 __device__ void tm_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, int it, bool keep_prev, float* hist,
                              int total_samples, bool prune, const float* gbasis, TmShared& ts, uint32_t tabs,
-                             uint32_t& phase, int* status) {
+                             uint32_t& phase, int* status, unsigned* mk, bool fp) {
   constexpr int RS = DIM * NP;
   const Lay& L = c.L;
   const int T = pc.T, TC = L.TC, TCW = tm_tcw(TC);
@@ -281,50 +305,114 @@ __device__ void tm_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, i
   float rb = 0.0f;
   for (int ci = 0; ci < nch; ++ci) {
     const int t0 = ci * TC, TCc = min(TC, T - t0);
-    pair_phase<DIM, NMAX, false, false, CAND, true>(c.SAMP, L, gbasis, c.G, c.N, t0, TCc, pc, want_res, c.warp,
-                                                    c.nwarps, c.lane, nullptr, prune);
+    if (TRAIN && mk)
+      pair_phase<DIM, NMAX, true, CAND, true>(c.SAMP, L, gbasis, c.G, c.N, t0, TCc, pc, want_res, c.warp,
+                                                     c.nwarps, c.lane, mk, prune);
+    else
+      pair_phase<DIM, NMAX, false, CAND, true>(c.SAMP, L, gbasis, c.G, c.N, t0, TCc, pc, want_res, c.warp,
+                                                      c.nwarps, c.lane, nullptr, prune);
     __syncthreads();
     tm_wait(ts, phase, status);
-    tm_chunk_pass<DIM, NMAX>(c, q, pc, t0, TCc, TCW, gbasis, g, rb);
+    tm_chunk_pass<DIM, NMAX>(c, q, pc, t0, TCc, TCW, gbasis, g, rb, TRAIN ? mk : nullptr);
     tcg::fence_before();
     __syncthreads();
-    if (c.tid == 0 && ci + 1 < nch && !ts.abort) {
+    if (c.tid == c.nthr - 32 && ci + 1 < nch && !ts.abort) {
       tcg::fence_after();
       tm_issue<DIM, FMT>(ts.tbase, tabs, TAB, ci + 1, TC, &ts.bar);
     }
   }
-  if (q.valid) {
-    float* blk = c.blk(q.s);
-    float* pg = blk + L.PG + q.cg * NMAX * RS + q.i * RS;
+  // the warp groups' partials of F^T q, summed through TMEM: every group
+  // parks its partial ([axis][16] words) in the allocated columns (the states
+  // and A are not needed again before the xi step rewrites A), then group c
+  // adds axis c (c, c + ncg, ...) of all groups' partials in group order and
+  // writes the sum to PG
+  {
 #pragma unroll
-    for (int x = 0; x < DIM; ++x)
+    for (int x = 0; x < DIM; ++x) {
+      uint32_t part[16];
 #pragma unroll
-      for (int k = 0; k < NV; ++k) pg[x * NP + k] = g[x][k];
-    if (want_res) blk[L.RSB + q.cg * NMAX + q.i] = rb;
+      for (int k = 0; k < 16; ++k) part[k] = k < NV ? __float_as_uint(g[x][k]) : 0u;
+      tcg::st16(q.lanebase + (uint32_t)((q.cg * DIM + x) * 16), part);
+    }
+    tcg::wait_st();
   }
+  if (q.valid && want_res) c.blk(q.s)[L.RSB + q.cg * NMAX + q.i] = rb;
+  tcg::fence_before();
   __syncthreads();
-  solve_lambda_means<DIM, NMAX, CAND>(c, pc, it, hist, total_samples, false);
+  tcg::fence_after();
+  for (int x = q.cg; x < DIM; x += q.ncg) {
+    float sum[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) sum[k] = 0.0f;
+    for (int o = 0; o < q.ncg; ++o) {
+      uint32_t pa[8], pb[8];
+      tcg::ld8(q.lanebase + (uint32_t)((o * DIM + x) * 16), pa);
+      tcg::ld8(q.lanebase + (uint32_t)((o * DIM + x) * 16 + 8), pb);
+      tcg::wait_ld();
+      tcg::tie(pa);
+      tcg::tie(pb);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        sum[k] += __uint_as_float(pa[k]);
+        sum[8 + k] += __uint_as_float(pb[k]);
+      }
+    }
+    if (q.valid) {
+      float* pg = c.blk(q.s) + L.PG + q.i * RS + x * NP;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) pg[k] = sum[k];
+    }
+  }
+  tcg::fence_before();
+  __syncthreads();
+  solve_lambda_means<DIM, NMAX, CAND>(c, pc, it, hist, total_samples, TRAIN && fp);
   __syncthreads();
   // xi step, one (sample, robot) row per lane and the axes over the warp
   // groups; the new rows also go to A in TMEM
+  // drift words: the lanes of one sample reduce their rows' drift by
+  // shuffles first (a sample's rows are NMAX consecutive lanes), then one
+  // atomic per sample and warp
+  constexpr bool SEG = (NMAX % 32 == 0) || (32 % NMAX == 0);
+  constexpr int SW = NMAX < 32 ? NMAX : 32;
   for (int x = q.cg; x < DIM; x += q.ncg) {
     float out[NP];
+    int db = 0;
     if (q.valid) {
-      xi_step_row<DIM, NMAX, CAND>(c, pc, q.s, q.i, x, keep_prev, false, out);
+      if (SEG)
+        xi_step_row<DIM, NMAX, CAND, false>(c, pc, q.s, q.i, x, keep_prev, TRAIN && fp, out, &db);
+      else
+        xi_step_row<DIM, NMAX, CAND, true>(c, pc, q.s, q.i, x, keep_prev, TRAIN && fp, out);
     } else {
 #pragma unroll
       for (int k = 0; k < NP; ++k) out[k] = 0.0f;
+    }
+    if (CAND && SEG) {
+#pragma unroll
+      for (int o = SW / 2; o >= 1; o >>= 1) db = max(db, __shfl_xor_sync(FULL, db, o));
+      if ((c.lane & (SW - 1)) == 0 && q.s < c.G) atomicMax(reinterpret_cast<int*>(c.blk(q.s) + L.RF), db);
     }
     tm_write_a<DIM, FMT>(q.lanebase, TCW, x, out);
   }
   tcg::wait_st();
   tcg::fence_before();
   __syncthreads();
+  if (TRAIN && fp) {
+    // ||z^{k+1} - z^k||^2 of this iteration, added per sample
+    for (int s = c.tid; s < c.G; s += c.nthr) {
+      float* blk = c.blk(s);
+      float acc = 0.0f;
+      for (int w = 0; w < DIM * NV; ++w) acc += blk[L.FPP + w];
+      for (int w = 0; w < c.N * DIM; ++w) acc += blk[L.FPP + DIM * NV + w];
+      blk[L.FPR] += acc;
+    }
+    // FPR is read only after the last iteration's barrier
+  }
 }
 
-// FMT: MMA operand format (0 tf32, 1 bf16, 2 fp16). Forward only (no
-// checkpoints, no activity masks).
-template <int DIM, int NMAX, int MAXT, int FMT>
+// FMT: MMA operand format (0 tf32, 1 bf16, 2 fp16). TRAIN: the training
+// forward (checkpoints, the last segment's iterates and activity masks, the
+// fixed-point residual sum), as the float32 form's.
+template <int DIM, int NMAX, int MAXT, int FMT, bool TRAIN = false>
 __global__ void __launch_bounds__(MAXT, 1) tm_fwd_kernel(const __grid_constant__ FusedArgs A) {
   extern __shared__ float4 smem4[];
   __shared__ TmShared ts;
@@ -332,17 +420,17 @@ __global__ void __launch_bounds__(MAXT, 1) tm_fwd_kernel(const __grid_constant__
   const ProblemConsts& pc = A.pc;
   const int T = pc.T;
   constexpr bool CAND = true;
-  const Cta<DIM, NMAX> c(A.sc, A.n_scenes, T, A.tc, A.nq, false, sm, false, CAND, FMT);
+  const Cta<DIM, NMAX> c(A.sc, A.n_scenes, T, A.tc, A.nq, false, sm, CAND, FMT);
   if (c.G <= 0) return;
   const Lay& L = c.L;
   const int TC = L.TC, TCW = tm_tcw(TC);
   const int TAB = tm_tab_bytes(T, TC, FMT);
   const int ncols = tm_alloc_cols(tm_cols(DIM, TC, FMT));
   unsigned char* tabs = reinterpret_cast<unsigned char*>(sm);
-  const float* gbasis = reinterpret_cast<const float*>(A.basis);
+  const float* gbasis = c.BASIS;   // the float32 basis, copied to shared memory by the prologue
 
-  tm_tables<FMT>(tabs, T, TC, gbasis, c.tid, c.nthr);
-  prologue<DIM, NMAX, 3>(c, T, A.basis, A.ops, A.start, A.goal, A.start_va, A.goal_va);
+  tm_tables<FMT>(tabs, T, TC, reinterpret_cast<const float*>(A.basis), c.tid, c.nthr);   // from global memory
+  prologue<DIM, NMAX>(c, T, A.basis, A.ops, A.start, A.goal, A.start_va, A.goal_va);
   load_state<DIM, NMAX>(c, A.xi0, A.lam0, A.xi_bar, A.xi_bar);
   for (int s = c.tid; s < c.G; s += c.nthr) {
     c.blk(s)[L.FPR] = 0.0f;
@@ -378,18 +466,34 @@ __global__ void __launch_bounds__(MAXT, 1) tm_fwd_kernel(const __grid_constant__
   __syncthreads();
   uint32_t phase = 0u;
   const uint32_t tabs_addr = tcg::smem_u32(tabs);
-  if (c.tid == 0) {
+  // the MMAs are issued by lane 0 of the last warp, which the pair phase
+  // leaves idle or least loaded (its (sample, step) lanes come last)
+  const bool issuer = c.tid == c.nthr - 32;
+  if (issuer) {
     tcg::fence_after();
     tm_issue<DIM, FMT>(ts.tbase, tabs_addr, TAB, 0, TC, &ts.bar);
   }
+  // checkpoints (training): (xi, lambda) at iterations 0, ck, 2 ck, ...,
+  // then every iterate of the last segment
+  const bool fp = TRAIN && A.fp_res2 != nullptr;
+  const int n_ck = TRAIN ? (pc.K + A.ck_every - 1) / A.ck_every : 0;
+  const int last_ck = TRAIN ? (n_ck - 1) * A.ck_every : 0;
+  float* tail = (TRAIN && A.ckpt) ? A.ckpt + (size_t)n_ck * 2 * A.total_coefs : nullptr;
   for (int it = 0; it < pc.K; ++it) {
-    tm_iteration<DIM, NMAX, FMT, CAND>(c, pc, it, it == pc.K - 1, A.hist, A.total_samples, A.prune != 0, gbasis, ts,
-                                       tabs_addr, phase, A.status);
-    if (it + 1 < pc.K && c.tid == 0 && !ts.abort) {
+    unsigned* mk = nullptr;
+    if constexpr (TRAIN) {
+      if (A.ckpt && it % A.ck_every == 0) write_checkpoint<DIM, NMAX>(c, A.ckpt, it / A.ck_every, A.total_coefs);
+      if (tail && it >= last_ck) write_checkpoint<DIM, NMAX>(c, tail, it - last_ck, A.total_coefs);
+      if (A.amask && it >= last_ck) mk = A.amask + (size_t)(it - last_ck) * A.amask_slot + c.mask0;
+    }
+    tm_iteration<DIM, NMAX, FMT, CAND, TRAIN>(c, pc, it, it == pc.K - 1, A.hist, A.total_samples, A.prune != 0,
+                                              gbasis, ts, tabs_addr, phase, A.status, mk, fp);
+    if (it + 1 < pc.K && issuer && !ts.abort) {
       tcg::fence_after();
       tm_issue<DIM, FMT>(ts.tbase, tabs_addr, TAB, 0, TC, &ts.bar);
     }
   }
+  if (tail) write_checkpoint<DIM, NMAX>(c, tail, pc.K - last_ck, A.total_coefs);
   tcg::fence_after();
   __syncthreads();
   if (c.warp == 0) tcg::dealloc(ts.tbase, (uint32_t)ncols);
@@ -411,14 +515,15 @@ __global__ void __launch_bounds__(MAXT, 1) tm_fwd_kernel(const __grid_constant__
     for (int t = 0; t < T; ++t) r2 += blk[L.RS2 + t];
     const float r = sqrtf(r2);
     A.resid_out[c.gsample0 + s] = r;
+    if (fp) A.fp_res2[c.gsample0 + s] = blk[L.FPR];
     if (!isfinite(r)) atomicOr(A.status, ST_NONFINITE);
   }
   store_state<DIM, NMAX>(c, A.xi_out, A.lam_out, 0);
 }
 
-template <int DIM, int NMAX, int MAXT, int FMT>
+template <int DIM, int NMAX, int MAXT, int FMT, bool TRAIN = false>
 cudaError_t launch_tm_t(const FusedArgs& a, const FusedLaunch& l, cudaStream_t st) {
-  auto k = tm_fwd_kernel<DIM, NMAX, MAXT, FMT>;
+  auto k = tm_fwd_kernel<DIM, NMAX, MAXT, FMT, TRAIN>;
   if (l.warps * 32 > MAXT || (l.warps & 3) != 0 || l.gmax * NMAX > 128) return cudaErrorInvalidConfiguration;
   k<<<l.n_ctas, l.warps * 32, l.smem, st>>>(a);
   return cudaGetLastError();

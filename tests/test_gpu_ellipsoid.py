@@ -1,6 +1,6 @@
 """The collision spheroid with unequal semi-axes (a, a, b), a != b
 (Eq. inter_robot_con, M_a = diag(a, a, b)), on the GPU: the fused and plain
-forms in float32 and the 16-bit tensor-core forms against the FP64 oracle,
+forms in float32 and the 16-bit tensor-memory forms against the FP64 oracle,
 and the adjoint against autograd over the FP64 PyTorch unroll. For a != b
 the pair rows take the scaled-coordinate closed forms of the alpha / beta /
 d steps: e = delta outside the spheroid, the radial projection in scaled

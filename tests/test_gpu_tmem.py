@@ -174,3 +174,74 @@ def test_deterministic(sfmod):
     b = f.project(_dev(sc.xi_bar), _dev(sc.start), _dev(sc.goal), 20)
     torch.cuda.synchronize()
     assert torch.equal(a.xi, b.xi) and torch.equal(a.lam, b.lam) and torch.equal(a.residual, b.residual)
+
+
+def _torch_ref_grads(oracle_lib, sc, K, gxi, glam, gfp):
+    from torch_unroll import TorchSF
+    Pm, Pd, Pdd = oracle_lib.basis(10, sc.spec.T, sc.spec.t_final)
+    ts = TorchSF(Pm, Pd, Pdd, sc.start, sc.goal, RHO_3D, sc.spec.coll, sc.spec.coll, sc.spec.v_max, sc.spec.a_max)
+    xbv = torch.tensor(sc.xi_bar).requires_grad_(True)
+    xi, lam, fp = ts.unroll(xbv, torch.zeros_like(xbv), xbv, K, fp_weight=1.0)
+    L = (gxi * xi).sum() + (glam * lam).sum() + (gfp * fp).sum()
+    (g,) = torch.autograd.grad(L, [xbv])
+    return g, fp.detach()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
+def test_training_forward_and_adjoint(sfmod, oracle_lib, prec):
+    """The differentiable SF with the tensor-memory training forward
+    (checkpoints, activity masks and the fixed-point residual sum written by
+    the MMA form) and the float32 adjoint: dL/dxi_bar against autograd over
+    the FP64 PyTorch unroll (relative L2 <= 2e-3, the float32 adjoint's bound,
+    in every mode), the fixed-point residual against the unroll's."""
+    from paper_2501_19042_gb300.autograd import sf_unroll
+    P = sfmod
+    sc = si.scene(si.config_n16_3d(n_robots=5, n_samples=6, T=40, box=(3.0, 3.0, 1.5), min_sep=0.8), 8)
+    K = 20
+    rng = np.random.default_rng(1)
+    gxi = torch.tensor(rng.normal(size=sc.xi_bar.shape))
+    glam = torch.tensor(rng.normal(size=sc.xi_bar.shape))
+    gfp = torch.tensor(rng.uniform(0.1, 1.0, size=sc.xi_bar.shape[0]))
+    g_ref, fp_ref = _torch_ref_grads(oracle_lib, sc, K, gxi, glam, gfp)
+    f = P.SafetyFilter(dim=3, T=sc.spec.T, rho=RHO_3D, coll_a=sc.spec.coll, max_robots=8, checkpoint_every=5,
+                       precision=prec)
+    f.set_tensor_memory(True)
+    xbd = _dev(sc.xi_bar).requires_grad_(True)
+    xi, lam, fp, res = sf_unroll(f, xbd, _dev(sc.start), _dev(sc.goal), K)
+    f.sync_status()
+    np.testing.assert_allclose(fp.detach().double().cpu().numpy(), fp_ref.numpy(), rtol=2e-3, atol=1e-5)
+    L = (_dev(gxi.numpy()) * xi).sum() + (_dev(glam.numpy()) * lam).sum() + (_dev(gfp.numpy()) * fp).sum()
+    L.backward()
+    a = xbd.grad.double().cpu().reshape(6, -1)
+    b = g_ref.reshape(6, -1)
+    assert ((a - b).norm(dim=1) / b.norm(dim=1)).max().item() <= 2e-3
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_training_forward_full_size_sampled(sfmod, oracle_lib, prec):
+    """The differentiation workload (N=16, S=512, K=50, checkpoint every 10)
+    through the tensor-memory training forward and the adjoint; 2 sampled
+    samples against FP64 autograd one by one."""
+    from paper_2501_19042_gb300.autograd import sf_unroll
+    from torch_unroll import TorchSF
+    P = sfmod
+    spec = si.config_diff()
+    sc = si.scene(spec, 5)
+    K = spec.K
+    rng = np.random.default_rng(2)
+    gxi = rng.normal(size=sc.xi_bar.shape)
+    f = P.SafetyFilter(dim=3, T=spec.T, rho=RHO_3D, coll_a=spec.coll, max_robots=16, checkpoint_every=10,
+                       precision=prec)
+    f.set_tensor_memory(True)
+    xbd = _dev(sc.xi_bar).requires_grad_(True)
+    xi, lam, fp, res = sf_unroll(f, xbd, _dev(sc.start), _dev(sc.goal), K)
+    (_dev(gxi) * xi).sum().backward()
+    f.sync_status()
+    Pm, Pd, Pdd = oracle_lib.basis(10, spec.T, spec.t_final)
+    ts = TorchSF(Pm, Pd, Pdd, sc.start, sc.goal, RHO_3D, spec.coll, spec.coll, spec.v_max, spec.a_max)
+    for s in (0, 511):
+        xb = torch.tensor(sc.xi_bar[s:s + 1]).requires_grad_(True)
+        x, _, _ = ts.unroll(xb, torch.zeros_like(xb), xb, K)
+        (g,) = torch.autograd.grad((torch.tensor(gxi[s:s + 1]) * x).sum(), [xb])
+        a = xbd.grad[s:s + 1].double().cpu().reshape(-1)
+        assert ((a - g.reshape(-1)).norm() / g.norm()).item() <= 2e-3, s

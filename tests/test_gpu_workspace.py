@@ -1,5 +1,5 @@
 """The workspace block (Eq. workspace_con, F_w = I (x) P) on the GPU: parity
-of the fused and plain forms (float32, and the bf16 / fp16 tensor-core form)
+of the fused and plain forms (float32, and the bf16 / fp16 tensor-memory form)
 with the FP64 oracle on a seeded workload whose samples leave the workspace
 spheroid, and the adjoint with workspace rows against FP64 autograd."""
 import numpy as np

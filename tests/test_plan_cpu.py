@@ -1,8 +1,11 @@
 """CPU checks of the fused launch planner through ``sf_plan_launch`` (host
 logic only, no device): every chosen shape fits in the opt-in shared memory
-of a GB300 block, respects the launch bounds of the kernels and the 16-bit
-forms' constraints and takes no more samples per CTA than a scene has, and
-the bench workload gets the shape measured fastest there."""
+of a GB300 block, respects the launch bounds of the kernels and the
+tensor-memory form's constraints (16-bit precisions: warps in groups of
+four, the CTA's (sample, robot) rows within the 128 TMEM lanes, one partial
+of F^T q per warp group, the chunk's states within the 512 TMEM columns)
+and takes no more samples per CTA than a scene has, and the bench workload
+gets the shape measured fastest there."""
 import math
 
 import numpy as np
@@ -28,10 +31,10 @@ def test_bench_workload_shape(plan):
     assert (p["G"], p["warps"], p["tc"], p["nq"]) == (7, 11, 50, 3)
     assert p["smem"] <= SMEM_OPTIN
     assert math.ceil(1024 / p["G"]) <= NUM_SMS
-    # 16-bit forms: 11 warps, even chunk, one time range per 16-step block at most
+    # 16-bit (tensor-memory) forms: G=7, 12 warps in 3 groups, chunks of 50
     for prec in ("bf16", "fp16"):
         q = plan(3, 100, [16], [1024], precision=prec)
-        assert q["warps"] == 11 and q["tc"] % 2 == 0 and q["nq"] <= (q["tc"] + 15) // 16
+        assert (q["G"], q["warps"], q["tc"], q["nq"]) == (7, 12, 50, 3)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
@@ -48,12 +51,16 @@ def test_shapes_are_valid_for_random_scene_mixes(plan, prec):
         p = plan(dim, T, nr, ns, precision=prec)
         assert 1 <= p["G"] <= 64
         assert 4 <= p["warps"] <= 12
-        assert 1 <= p["tc"] <= T + (1 if prec != "fp32" else 0)
+        assert 1 <= p["tc"] <= T
         assert 1 <= p["nq"] <= p["tc"]
         assert 0 < p["smem"] <= SMEM_OPTIN
         if prec != "fp32":
-            assert p["tc"] % 2 == 0
-            assert p["nq"] <= (p["tc"] + 15) // 16
+            assert p["warps"] % 4 == 0 and p["nq"] == p["warps"] // 4
+            assert p["G"] * bucket <= 128
+            tcw = (p["tc"] + 15) // 16 * 16
+            ka = 8   # 16-bit operands: 8 columns per 16 coefficients
+            assert 2 * dim * tcw + 2 * dim * ka <= 512
+            assert p["smem"] + 256 <= SMEM_OPTIN
         # G never exceeds the largest scene (a CTA holds samples of one scene)
         assert p["G"] <= max(ns)
 
