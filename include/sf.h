@@ -22,8 +22,12 @@
  *    cudaStream_t cast to void*; NULL is the legacy default stream). No
  *    implicit host synchronisation, except where a function says so.
  *  - Device-side errors (non-finite values) are latched in a device word;
- *    sf_sync_status() synchronises the stream and returns them. No kernel of
- *    this build waits on another, so SF_ERR_TIMEOUT is not returned.
+ *    sf_sync_status() synchronises the stream and returns them. The only
+ *    device-side wait is the tensor-memory form's wait for its own MMAs
+ *    (tcgen05.commit to an mbarrier); it gives up after one second of the
+ *    GPU's global timer, stops issuing MMAs, drains (bounded) and frees its
+ *    tensor memory, and latches SF_ERR_TIMEOUT (outputs of that call are
+ *    then undefined; the context stays usable).
  *  - Layouts (row-major, float32 unless stated):
  *      coefficients (xi_bar, xi0, lambda0, xi_out, lambda_out, gradients):
  *        per sample [dim][N][nvar], nvar = order + 1 (the paper's xi vector,
@@ -53,7 +57,7 @@ typedef enum {
   SF_ERR_INVALID_ARG = 1,   /* bad size, shape, pointer or value */
   SF_ERR_CUDA = 2,          /* a CUDA runtime call failed */
   SF_ERR_OOM = 3,           /* handle-owned allocation failed */
-  SF_ERR_TIMEOUT = 4,       /* a bounded device wait ran out (reserved) */
+  SF_ERR_TIMEOUT = 4,       /* a bounded device wait ran out */
   SF_ERR_NONFINITE = 5,     /* a non-finite value reached the output */
   SF_ERR_UNSUPPORTED = 6,   /* valid request this build does not implement */
   SF_ERR_WORKSPACE = 7      /* workspace missing or too small */
@@ -211,7 +215,13 @@ typedef enum {
    * the B operand in shared memory, three-term split of tf32 operands); the
    * rest stays on the float32 lanes. 0: the float32 form, products on the
    * lanes too. 16-bit handles always use the tensor-memory form. */
-  SF_OPT_TENSOR_MEMORY = 2
+  SF_OPT_TENSOR_MEMORY = 2,
+  /* Test of the timeout path, value in microseconds (0 = off, the default):
+   * the tensor-memory form does not issue the first MMA group of each CTA
+   * and bounds every MMA wait by `value` microseconds, so the first wait runs
+   * out with nothing in flight and sf_sync_status reports SF_ERR_TIMEOUT.
+   * Outputs of such calls are undefined. No effect on the float32 form. */
+  SF_OPT_TEST_WAIT_TIMEOUT = 3
 } sf_option;
 
 /* Sets option `option` of the handle to `value` (for later calls).

@@ -29,6 +29,7 @@ struct sf_handle {
   bool use_tuned = true;
   int prune = 1;                                   // SF_OPT_PAIR_PRUNING
   int tm = 0;                                      // SF_OPT_TENSOR_MEMORY
+  int wait_test_us = 0;                            // SF_OPT_TEST_WAIT_TIMEOUT
   cudaStream_t aux[2] = {nullptr, nullptr};        // extra streams for concurrent launch groups
   cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
   float eq_pi[sf::NV * sf::NV] = {};               // QP layer operators (host copy of slot 0)
@@ -245,6 +246,8 @@ sf_status build_groups(sf_handle* h, const sf_batch* b, int K, long long S, cons
       a.total_coefs = tot;
       a.fp_res2 = rq.fp_res2;
       a.prune = h->prune ? 1 : 0;
+      a.wait_ns = 1000ull * (unsigned long long)h->wait_test_us;
+      a.skip_first_mma = h->wait_test_us > 0 ? 1 : 0;
       if (rq.ckpt && !rq.backward) {
         const long long ck = a.ck_every, nck = (K + ck - 1) / ck;
         a.amask = reinterpret_cast<unsigned*>(rq.ckpt + states_floats_aligned(nck + ck + 1, tot));
@@ -1053,6 +1056,12 @@ sf_status sf_set_option(sf_handle* h, int option, int value) {
   if (option == SF_OPT_TENSOR_MEMORY) {
     if (value != 0 && value != 1) return fail(h, SF_ERR_INVALID_ARG, "SF_OPT_TENSOR_MEMORY takes 0 or 1");
     h->tm = value;
+    return SF_OK;
+  }
+  if (option == SF_OPT_TEST_WAIT_TIMEOUT) {
+    if (value < 0 || value > 1000000)
+      return fail(h, SF_ERR_INVALID_ARG, "SF_OPT_TEST_WAIT_TIMEOUT takes 0 .. 1000000 microseconds");
+    h->wait_test_us = value;
     return SF_OK;
   }
   return fail(h, SF_ERR_INVALID_ARG, "unknown option");

@@ -111,8 +111,9 @@ FusedPlan plan_fused(int dim, int nmax, int T, const int* nr, const int* ns, int
     if (prec >= PREC_TM_TF32) {
       // tensor-memory form: G (sample, robot) rows in the 128 TMEM lanes,
       // warps in groups of four (one per lane quarter), one partial of F^T q
-      // per group, time chunks within the TMEM columns (the velocity and
-      // acceleration states of a chunk beside the coefficient operand)
+      // per group; a chunk of the pair phase is split into TMEM sub-chunks of
+      // at most 64 steps (the velocity and acceleration states of a
+      // sub-chunk beside the coefficient operand)
       if (G * nmax > 128) continue;
       const int fmt = prec - PREC_TM_TF32;
       int prev_tc = 0;
@@ -123,7 +124,10 @@ FusedPlan plan_fused(int dim, int nmax, int T, const int* nr, const int* ns, int
         if (fused_impl::tm_cols(dim, tc, fmt) > 512) continue;
         if (force_tc > 0 && tc != force_tc) continue;
         const int real_nch = (T + tc - 1) / tc;
-        const int nb = (tc + 7) / 8;
+        const int nsub = fused_impl::tm_nsub(tc);
+        const int nb = (fused_impl::tm_ts(tc) + 7) / 8;
+        // warps of lane quarters with none of the CTA's rows skip the pass
+        const int quarters = std::min(4, (G * nmax + 31) / 32);
         for (int w = 8; w <= maxw; w += 4) {
           if (force_warps > 0 && w != force_warps) continue;
           const int ncg = w / 4;
@@ -136,10 +140,11 @@ FusedPlan plan_fused(int dim, int nmax, int T, const int* nr, const int* ns, int
           // slots per step: two ball tests, the E flag, votes), issue-bound
           // over the CTA or latency-bound per warp
           const double rounds = std::ceil((double)nb / ncg);
-          const double tPass = std::max(4.0 * ncg * rounds * 8.0 * 22.0 / rate, rounds * 8.0 * 22.0 * 2.0);
+          const double tPass =
+              std::max(quarters * ncg * rounds * 8.0 * 22.0 / rate, rounds * 8.0 * 22.0 * 2.0) * nsub;
           const double a_rounds = std::ceil((double)G * tc / (32.0 * w));
           const double tPair = a_rounds * w * cA / rate;
-          const double per_iter = real_nch * (tPass + tPair) + (2.0 * real_nch + 3.0) * 400.0 +
+          const double per_iter = real_nch * (tPass + tPair) + ((1.0 + nsub) * real_nch + 3.0) * 400.0 +
                                   24.0 * G * Nbig * dim * 4.0 / rate;
           add_top(FusedPlan{G, w, tc, ncg, smem, waves * per_iter});
         }

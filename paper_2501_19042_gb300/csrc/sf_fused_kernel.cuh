@@ -63,19 +63,25 @@ constexpr float kWsDriftLimit = kWsMargin - 1e-3f;
 // per instruction, tables of 12 k per row, three 128-byte core matrices per
 // 8 rows); 1 / 2: bf16 / fp16 (K = 16, two core matrices per 8 rows).
 constexpr int TM_TABLES = 4;   // Pd, Pdd; rounded and remainder
-__host__ __device__ constexpr int tm_tcw(int tc) { return (tc + 15) / 16 * 16; }
+// A pair-phase chunk of tc steps is split into tm_nsub(tc) TMEM sub-chunks of
+// at most 64 steps (tm_ts(tc) steps, the last one shorter), whose states
+// occupy TCW = tm_tcw(tc) columns per (state, axis).
+__host__ __device__ constexpr int tm_nsub(int tc) { return (tc + 63) / 64; }
+__host__ __device__ constexpr int tm_ts(int tc) { return (tc + tm_nsub(tc) - 1) / tm_nsub(tc); }
+__host__ __device__ constexpr int tm_tcw(int tc) { return (tm_ts(tc) + 15) / 16 * 16; }
 __host__ __device__ constexpr int tm_ka(int fmt) { return fmt == 0 ? 16 : 8; }
 __host__ __device__ constexpr int tm_sbo(int fmt) { return fmt == 0 ? 384 : 256; }
-// TMEM columns: the states [2][dim][TCW], then A [dim][2][KA]
+// TMEM columns: the states of one sub-chunk [2][dim][TCW], then A [dim][2][KA]
 __host__ __device__ constexpr int tm_cols(int dim, int tc, int fmt) { return 2 * dim * tm_tcw(tc) + 2 * dim * tm_ka(fmt); }
 __host__ __device__ constexpr int tm_alloc_cols(int cols) {
   return cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
 }
-// Bytes of one B table: chunk c's rows at c * TCW, plus one zero 8-row group
-// (the tf32 form's second K step reads one core matrix past a group; the
-// coefficients' k >= 11 are zero, so any finite value there adds nothing).
+// Bytes of one B table: sub-chunk j of chunk c (global sub-chunk c nsub + j)
+// at rows (c nsub + j) TCW, plus one zero 8-row group (the tf32 form's
+// second K step reads one core matrix past a group; the coefficients'
+// k >= 11 are zero, so any finite value there adds nothing).
 __host__ __device__ constexpr int tm_tab_bytes(int T, int tc, int fmt) {
-  return ((T + tc - 1) / tc * tm_tcw(tc) / 8 + 1) * tm_sbo(fmt);
+  return ((T + tc - 1) / tc * tm_nsub(tc) * tm_tcw(tc) / 8 + 1) * tm_sbo(fmt);
 }
 
 // Shared-memory layout (floats). Head: (tensor-memory form) the MMA B
@@ -89,8 +95,9 @@ __host__ __device__ constexpr int tm_tab_bytes(int T, int tc, int fmt) {
 // iteration); RS2 [T] (pair residual per t); RSB [NQ][NMAX] (ball residual
 // partials); with pair pruning: CR [NMAX][DIM][12] (coefficients at the last
 // full pair test), CM [T][CMW] (candidate pair rows of that test), WC [T]
-// (candidate workspace rows: robots near or outside the workspace), RF (drift
-// of the coefficients since then, as the bit pattern of a non-negative float).
+// (candidate workspace rows: robots near or outside the workspace), RF (in the
+// first sample's block: the largest drift of the CTA's coefficients since
+// then, as the bit pattern of a non-negative float).
 struct Lay {
   int RS, EP, TC, NQ, NPG, PQ1, T, nmax, dim;
   int C, LAM, XIB, PG, MC, MR, EB, RS2, RSB, FPP, FPR, XB, LB, GXB, U, CW, CR, CM, WC, RF, CMW, SB;
@@ -384,9 +391,10 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
       float wkmax = 0.0f;
 #pragma unroll
       for (int x = 0; x < DIM; ++x) wkmax = fmaxf(wkmax, pc.wk[x]);
-      for (int q = 0; q < G && !refresh; ++q) {
-        const float drift = sqrtf((float)DIM) *
-                            __int_as_float(*reinterpret_cast<const int*>(SAMP + (size_t)q * L.SB + L.RF));
+      if (!refresh) {
+        // the CTA's drift word (in the first sample's block): the largest
+        // drift of any of its samples
+        const float drift = sqrtf((float)DIM) * __int_as_float(*reinterpret_cast<const int*>(SAMP + L.RF));
         refresh = !(drift < kPruneDriftLimit) || (pc.use_w && !(drift * wkmax < kWsDriftLimit));  // NaN: full
       }
       cmrow = reinterpret_cast<unsigned*>(blk + L.CM) + (size_t)t * L.CMW;
@@ -1054,11 +1062,8 @@ __device__ __forceinline__ bool cta_refresh(const Cta<DIM, NMAX>& c, const Lay& 
   float wkmax = 0.0f;
 #pragma unroll
   for (int x = 0; x < DIM; ++x) wkmax = fmaxf(wkmax, pc.wk[x]);
-  for (int q = 0; q < c.G; ++q) {
-    const float drift = sqrtf((float)DIM) * __int_as_float(*reinterpret_cast<const int*>(c.blk(q) + L.RF));
-    if (!(drift < kPruneDriftLimit) || (pc.use_w && !(drift * wkmax < kWsDriftLimit))) return true;
-  }
-  return false;
+  const float drift = sqrtf((float)DIM) * __int_as_float(*reinterpret_cast<const int*>(c.SAMP + L.RF));
+  return !(drift < kPruneDriftLimit) || (pc.use_w && !(drift * wkmax < kWsDriftLimit));
 }
 
 // Solve phase 1 of one iteration on every sample of the CTA: the lambda step
@@ -1143,7 +1148,8 @@ __device__ void solve_lambda_means(const Cta<DIM, NMAX>& c, const ProblemConsts&
         m1 = fmaf(ds[m], __shfl_sync(FULL, mr, (lane & 16) + m), m1);
       }
       if (act) blk[L.MR + x * NP + k] = m0 + m1;
-      if (CAND && act && x == 0 && k == 0) *reinterpret_cast<int*>(blk + L.RF) = 0;   // drift since the reference
+      if (CAND && act && s == 0 && x == 0 && k == 0)   // the CTA's drift since the reference
+        *reinterpret_cast<int*>(c.SAMP + L.RF) = 0;
       if (fp && act) blk[L.FPP + x * NV + k] = dl2;
       if (want_res && act && x == 0 && k == 0) {
         float r2 = 0.0f;
@@ -1211,7 +1217,7 @@ __device__ __forceinline__ void xi_step_row(const Cta<DIM, NMAX>& c, const Probl
       bad |= !(e == e);
     }
     if (ATOMIC_DRIFT)
-      atomicMax(reinterpret_cast<int*>(blk + L.RF), __float_as_int(bad ? INFINITY : d));
+      atomicMax(reinterpret_cast<int*>(c.SAMP + L.RF), __float_as_int(bad ? INFINITY : d));
     else
       *drift_bits = __float_as_int(bad ? INFINITY : d);
   }

@@ -106,6 +106,8 @@ struct FusedArgs {
   unsigned* amask;         // activity masks of the last checkpoint segment [ck_every][slot], or null
   long long amask_slot;    // words per mask slot (one iteration, all samples)
   int prune;               // float32 form: exact pair pruning on (1) or every pair tested (0)
+  unsigned long long wait_ns;   // tensor-memory form: bound of each MMA wait (0: the default)
+  int skip_first_mma;      // tensor-memory form: the first MMA group is not issued (timeout test)
   SceneDesc sc[MAX_SCENES_PER_LAUNCH];
 };
 

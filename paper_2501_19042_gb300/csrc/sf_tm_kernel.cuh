@@ -34,14 +34,16 @@
 namespace sf {
 namespace fused_impl {
 
-// Polls of an mbarrier before a wait is abandoned (a completed MMA group
-// takes a few microseconds; the limit is far above that).
-constexpr uint32_t kTmWaitLimit = 1u << 22;
+// Time after which a wait for an MMA group is abandoned, unless the launch
+// sets its own (an MMA group of a chunk completes in a few microseconds).
+constexpr uint64_t kTmWaitNs = 1000000000ull;
 
 // Shared state of the tensor-memory form (static shared memory).
 struct TmShared {
   uint64_t bar;       // MMA completion of the current chunk
+  uint64_t limit_ns;  // bound of every wait on bar
   uint32_t tbase;     // TMEM base address
+  uint32_t lost;      // parity of the phase a wait gave up on
   int abort;          // a wait ran out: no more MMAs, outputs flagged
 };
 
@@ -52,12 +54,17 @@ __device__ __forceinline__ uint32_t pack16(float lo, float hi) {
 
 // B tables: Pd and Pdd rows (m = 1, 2) of the float32 basis [T][36]
 // (global), rounded (table 2 (m - 1)) and the rounding remainder (table
-// 2 (m - 1) + 1), time step t of chunk c at row c * TCW + (t - c TC); every
-// other entry zero.
+// 2 (m - 1) + 1), time step t of sub-chunk j of chunk c at row
+// (c nsub + j) TCW + (t - c TC - j TS); every other entry zero.
 template <int FMT>
 __device__ void tm_tables(unsigned char* tb, int T, int TC, const float* gb, int tid, int nthr) {
-  const int TCW = tm_tcw(TC);
+  const int TCW = tm_tcw(TC), TS = tm_ts(TC), NSUB = tm_nsub(TC);
   const int TAB = tm_tab_bytes(T, TC, FMT);
+  // table row of time step t
+  auto row_of = [&](int t) {
+    const int ci = t / TC, tl = t - ci * TC, j = tl / TS;
+    return (ci * NSUB + j) * TCW + (tl - j * TS);
+  };
   uint32_t* w = reinterpret_cast<uint32_t*>(tb);
   for (int v = tid; v < TM_TABLES * TAB / 4; v += nthr) w[v] = 0u;
   __syncthreads();
@@ -66,7 +73,7 @@ __device__ void tm_tables(unsigned char* tb, int T, int TC, const float* gb, int
     for (int v = tid; v < T * 2 * 12; v += nthr) {
       const int t = v / 24, m = (v / 12) % 2, k = v % 12;
       const float x = gb[(size_t)t * BASIS_ROW + (1 + m) * NP + k];
-      const int ci = t / TC, row = ci * TCW + (t - ci * TC);
+      const int row = row_of(t);
       const uint32_t off = (row >> 3) * SBO + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4;
       const uint32_t h = tcg::tf32_rna(x);
       const uint32_t l = tcg::tf32_rna(x - __uint_as_float(h));
@@ -79,7 +86,7 @@ __device__ void tm_tables(unsigned char* tb, int T, int TC, const float* gb, int
       const float* row_ = gb + (size_t)t * BASIS_ROW + (1 + m) * NP;
       const float x0 = k0 < NV ? row_[k0] : 0.0f;
       const float x1 = k0 + 1 < NV ? row_[k0 + 1] : 0.0f;
-      const int ci = t / TC, row = ci * TCW + (t - ci * TC);
+      const int row = row_of(t);
       const uint32_t off = (row >> 3) * SBO + (k0 >> 3) * 128 + (row & 7) * 16 + (k0 & 7) * 2;
       *reinterpret_cast<uint32_t*>(tb + (2 * m) * TAB + off) = pack16<FMT>(x0, x1);
       *reinterpret_cast<uint32_t*>(tb + (2 * m + 1) * TAB + off) =
@@ -119,8 +126,8 @@ __device__ __forceinline__ void tm_write_a(uint32_t lanebase, int TCW, int x, co
   }
 }
 
-// Issues the MMAs of chunk ci (velocities and accelerations of every row and
-// axis) and commits them to the mbarrier. One thread.
+// Issues the MMAs of global sub-chunk ci (velocities and accelerations of
+// every row and axis) and commits them to the mbarrier. One thread.
 template <int DIM, int FMT>
 __device__ void tm_issue(uint32_t tbase, uint32_t tabs, int TAB, int ci, int TC, uint64_t* bar) {
   constexpr int KA = tm_ka(FMT);
@@ -161,8 +168,9 @@ __device__ void tm_issue(uint32_t tbase, uint32_t tabs, int TAB, int ci, int TC,
 // the timeout status and stops further MMAs.
 __device__ __forceinline__ void tm_wait(TmShared& ts, uint32_t& phase, int* status) {
   if (!ts.abort) {
-    if (!tcg::mbar_wait(&ts.bar, phase, kTmWaitLimit)) {
+    if (!tcg::mbar_wait(&ts.bar, phase, ts.limit_ns)) {
       ts.abort = 1;
+      ts.lost = phase;
       atomicOr(status, ST_TIMEOUT);
     }
   }
@@ -190,97 +198,120 @@ __device__ __forceinline__ TmLane tm_lane(const Cta<DIM, NMAX>& c, uint32_t tbas
   return q;
 }
 
-// TMEM pass of one chunk (after its pair phase): the velocity / acceleration
-// ball rows of this lane's robot from TMEM, F^T of their residuals and of the
-// pair residuals E (chunk-buffer rows whose active-pair flag is set) into g,
-// the balls' squared residuals into rb. Per 8-step block every lane first
+// Loads of one 8-step block of the TMEM pass: the lane's velocities and
+// accelerations (tcgen05.ld, completed by the caller's wait) and the
+// active-pair flags of the block's steps.
+template <int DIM, int NMAX>
+__device__ __forceinline__ void tm_block_load(const TmLane& q, const float* blk, const Lay& L, int TCW, int tb,
+                                              int TCc, int eb0, uint32_t (&v)[DIM][8], uint32_t (&a)[DIM][8],
+                                              float (&fl)[8]) {
+#pragma unroll
+  for (int x = 0; x < DIM; ++x) {
+    tcg::ld8(q.lanebase + (uint32_t)(x * TCW + tb), v[x]);
+    tcg::ld8(q.lanebase + (uint32_t)((DIM + x) * TCW + tb), a[x]);
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) fl[j] = (tb + j < TCc) ? blk[L.EB + (eb0 + tb + j) * L.EP + NMAX * DIM] : 0.0f;
+}
+
+// One 8-step block of the TMEM pass on loaded values: every lane first
 // evaluates its 24 conditions (velocity outside, acceleration outside, pair
 // row active, per step) into one word; a single warp-wide OR then tells
 // which of the (rare) projections and F^T updates the warp has to run.
 template <int DIM, int NMAX>
+__device__ __forceinline__ void tm_block(const TmLane& q, const float* blk, const Lay& L, const ProblemConsts& pc,
+                                         int t0, int tb, int TCc, int eb0, const float* gbasis, float vm2,
+                                         float am2, const uint32_t (&v)[DIM][8], const uint32_t (&a)[DIM][8],
+                                         const float (&fl)[8], float (&g)[DIM][NV], float& rb, unsigned* mk) {
+  uint32_t bj[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    float nv = 0.0f, na = 0.0f;
+#pragma unroll
+    for (int x = 0; x < DIM; ++x) {
+      const float vx = __uint_as_float(v[x][j]), ax = __uint_as_float(a[x][j]);
+      nv = fmaf(vx, vx, nv);
+      na = fmaf(ax, ax, na);
+    }
+    const bool live = q.valid && tb + j < TCc;
+    bj[j] = ((live && nv > vm2) ? (1u << j) : 0u) | ((live && na > am2) ? (1u << (8 + j)) : 0u) |
+            ((live && fl[j] != 0.0f) ? (1u << (16 + j)) : 0u);
+  }
+  // a tree of ORs (no serial chain through the steps)
+  const uint32_t bits = ((bj[0] | bj[1]) | (bj[2] | bj[3])) | ((bj[4] | bj[5]) | (bj[6] | bj[7]));
+  const uint32_t any = __reduce_or_sync(FULL, bits);
+  if (!any) return;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const float* brow = gbasis + (size_t)(t0 + tb + j) * BASIS_ROW;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const uint32_t bit = 1u << (8 * b + j);
+      if (any & bit) {
+        // lanes whose row is inside the ball take q = 0 (w = 0)
+        const bool mine = (bits & bit) != 0u;
+        float w[DIM], qb[DIM], rl = 0.0f;
+#pragma unroll
+        for (int x = 0; x < DIM; ++x) w[x] = mine ? __uint_as_float(b == 0 ? v[x][j] : a[x][j]) : 0.0f;
+        ball_residual<DIM>(w, b == 0 ? pc.v_max : pc.a_max, qb, rl);
+        rb += rl;
+        if (mk && mine) {   // activity mask of the ball row (training forward)
+          unsigned* mball = mk + ((size_t)q.s * L.T + t0 + tb + j) * mask_words(NMAX) + mask_pair_words(NMAX);
+          const int mb = b * NMAX + q.i;
+          atomicOr(mball + (mb >> 5), 1u << (mb & 31));
+        }
+        float P[NV];
+        row_from(brow + (1 + b) * NP, P);
+#pragma unroll
+        for (int x = 0; x < DIM; ++x)
+#pragma unroll
+          for (int k = 0; k < NV; ++k) g[x][k] = fmaf(P[k], qb[x], g[x][k]);
+      }
+    }
+    const uint32_t ebit = 1u << (16 + j);
+    if (any & ebit) {
+      const bool mine = (bits & ebit) != 0u;
+      const float* eb = blk + L.EB + (eb0 + tb + j) * L.EP + q.i * DIM;
+      float e[DIM];
+#pragma unroll
+      for (int x = 0; x < DIM; ++x) e[x] = mine ? eb[x] : 0.0f;
+      float P[NV];
+      row_from(brow, P);
+#pragma unroll
+      for (int x = 0; x < DIM; ++x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) g[x][k] = fmaf(P[k], e[x], g[x][k]);
+    }
+  }
+}
+
+// TMEM pass of one sub-chunk [t0, t0 + TCc) (after the pair phase of its
+// chunk, whose chunk-buffer rows start eb0 steps earlier): the velocity /
+// acceleration ball rows of this lane's robot from TMEM, F^T of their
+// residuals and of the pair residuals E (chunk-buffer rows whose
+// active-pair flag is set) into g, the balls' squared residuals into rb.
+// (Issuing a block's loads before evaluating the previous block needs a
+// second register buffer, which made the kernel spill.)
+template <int DIM, int NMAX>
 __device__ void tm_chunk_pass(const Cta<DIM, NMAX>& c, const TmLane& q, const ProblemConsts& pc, int t0, int TCc,
-                              int TCW, const float* gbasis, float (&g)[DIM][NV], float& rb, unsigned* mk) {
+                              int TCW, const float* gbasis, float (&g)[DIM][NV], float& rb, unsigned* mk,
+                              int eb0) {
   const Lay& L = c.L;
+  if (32 * (c.warp & 3) >= c.G * NMAX) return;   // a lane quarter with none of the CTA's rows
   const float* blk = c.blk(q.valid ? q.s : 0);
   const float vm2 = pc.use_v ? pc.v_max * pc.v_max : INFINITY;
   const float am2 = pc.use_a ? pc.a_max * pc.a_max : INFINITY;
   for (int bk = q.cg; bk * 8 < TCc; bk += q.ncg) {
-    const int tb = bk * 8;
     uint32_t v[DIM][8], a[DIM][8];
-#pragma unroll
-    for (int x = 0; x < DIM; ++x) {
-      tcg::ld8(q.lanebase + (uint32_t)(x * TCW + tb), v[x]);
-      tcg::ld8(q.lanebase + (uint32_t)((DIM + x) * TCW + tb), a[x]);
-    }
-    // the E flags of the block's steps (independent of the TMEM loads)
     float fl[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) fl[j] = (tb + j < TCc) ? blk[L.EB + (tb + j) * L.EP + NMAX * DIM] : 0.0f;
+    tm_block_load<DIM, NMAX>(q, blk, L, TCW, bk * 8, TCc, eb0, v, a, fl);
     tcg::wait_ld();
 #pragma unroll
     for (int x = 0; x < DIM; ++x) {
       tcg::tie(v[x]);
       tcg::tie(a[x]);
     }
-    uint32_t bits = 0u;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      float nv = 0.0f, na = 0.0f;
-#pragma unroll
-      for (int x = 0; x < DIM; ++x) {
-        const float vx = __uint_as_float(v[x][j]), ax = __uint_as_float(a[x][j]);
-        nv = fmaf(vx, vx, nv);
-        na = fmaf(ax, ax, na);
-      }
-      const bool live = q.valid && tb + j < TCc;
-      bits |= (live && nv > vm2) ? (1u << j) : 0u;
-      bits |= (live && na > am2) ? (1u << (8 + j)) : 0u;
-      bits |= (live && fl[j] != 0.0f) ? (1u << (16 + j)) : 0u;
-    }
-    const uint32_t any = __reduce_or_sync(FULL, bits);
-    if (!any) continue;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const float* brow = gbasis + (size_t)(t0 + tb + j) * BASIS_ROW;
-#pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        const uint32_t bit = 1u << (8 * b + j);
-        if (any & bit) {
-          // lanes whose row is inside the ball take q = 0 (w = 0)
-          const bool mine = (bits & bit) != 0u;
-          float w[DIM], qb[DIM], rl = 0.0f;
-#pragma unroll
-          for (int x = 0; x < DIM; ++x) w[x] = mine ? __uint_as_float(b == 0 ? v[x][j] : a[x][j]) : 0.0f;
-          ball_residual<DIM>(w, b == 0 ? pc.v_max : pc.a_max, qb, rl);
-          rb += rl;
-          if (mk && mine) {   // activity mask of the ball row (training forward)
-            unsigned* mball = mk + ((size_t)q.s * L.T + t0 + tb + j) * mask_words(NMAX) + mask_pair_words(NMAX);
-            const int mb = b * NMAX + q.i;
-            atomicOr(mball + (mb >> 5), 1u << (mb & 31));
-          }
-          float P[NV];
-          row_from(brow + (1 + b) * NP, P);
-#pragma unroll
-          for (int x = 0; x < DIM; ++x)
-#pragma unroll
-            for (int k = 0; k < NV; ++k) g[x][k] = fmaf(P[k], qb[x], g[x][k]);
-        }
-      }
-      const uint32_t ebit = 1u << (16 + j);
-      if (any & ebit) {
-        const bool mine = (bits & ebit) != 0u;
-        const float* eb = blk + L.EB + (tb + j) * L.EP + q.i * DIM;
-        float e[DIM];
-#pragma unroll
-        for (int x = 0; x < DIM; ++x) e[x] = mine ? eb[x] : 0.0f;
-        float P[NV];
-        row_from(brow, P);
-#pragma unroll
-        for (int x = 0; x < DIM; ++x)
-#pragma unroll
-          for (int k = 0; k < NV; ++k) g[x][k] = fmaf(P[k], e[x], g[x][k]);
-      }
-    }
+    tm_block<DIM, NMAX>(q, blk, L, pc, t0, bk * 8, TCc, eb0, gbasis, vm2, am2, v, a, fl, g, rb, mk);
   }
 }
 
@@ -303,6 +334,7 @@ __device__ void tm_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, i
 #pragma unroll
     for (int k = 0; k < NV; ++k) g[x][k] = 0.0f;
   float rb = 0.0f;
+  const int NSUB = tm_nsub(TC), TS = tm_ts(TC);
   for (int ci = 0; ci < nch; ++ci) {
     const int t0 = ci * TC, TCc = min(TC, T - t0);
     if (TRAIN && mk)
@@ -312,13 +344,19 @@ __device__ void tm_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, i
       pair_phase<DIM, NMAX, false, CAND, true>(c.SAMP, L, gbasis, c.G, c.N, t0, TCc, pc, want_res, c.warp,
                                                       c.nwarps, c.lane, nullptr, prune);
     __syncthreads();
-    tm_wait(ts, phase, status);
-    tm_chunk_pass<DIM, NMAX>(c, q, pc, t0, TCc, TCW, gbasis, g, rb, TRAIN ? mk : nullptr);
-    tcg::fence_before();
-    __syncthreads();
-    if (c.tid == c.nthr - 32 && ci + 1 < nch && !ts.abort) {
-      tcg::fence_after();
-      tm_issue<DIM, FMT>(ts.tbase, tabs, TAB, ci + 1, TC, &ts.bar);
+    // the chunk's TMEM sub-chunks; the MMAs of the next sub-chunk start as
+    // soon as the pass of this one has read the states
+    for (int j = 0; j < NSUB; ++j) {
+      const int s0 = j * TS, SCc = min(TS, TCc - s0);
+      tm_wait(ts, phase, status);
+      if (SCc > 0) tm_chunk_pass<DIM, NMAX>(c, q, pc, t0 + s0, SCc, TCW, gbasis, g, rb, TRAIN ? mk : nullptr, s0);
+      tcg::fence_before();
+      __syncthreads();
+      const int next = ci * NSUB + j + 1;
+      if (c.tid == c.nthr - 32 && next < nch * NSUB && !ts.abort) {
+        tcg::fence_after();
+        tm_issue<DIM, FMT>(ts.tbase, tabs, TAB, next, TC, &ts.bar);
+      }
     }
   }
   // the warp groups' partials of F^T q, summed through TMEM: every group
@@ -369,8 +407,8 @@ __device__ void tm_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, i
   __syncthreads();
   // xi step, one (sample, robot) row per lane and the axes over the warp
   // groups; the new rows also go to A in TMEM
-  // drift words: the lanes of one sample reduce their rows' drift by
-  // shuffles first (a sample's rows are NMAX consecutive lanes), then one
+  // the CTA's drift word: the lanes of one sample reduce their rows' drift
+  // by shuffles first (a sample's rows are NMAX consecutive lanes), then one
   // atomic per sample and warp
   constexpr bool SEG = (NMAX % 32 == 0) || (32 % NMAX == 0);
   constexpr int SW = NMAX < 32 ? NMAX : 32;
@@ -389,7 +427,7 @@ __device__ void tm_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, i
     if (CAND && SEG) {
 #pragma unroll
       for (int o = SW / 2; o >= 1; o >>= 1) db = max(db, __shfl_xor_sync(FULL, db, o));
-      if ((c.lane & (SW - 1)) == 0 && q.s < c.G) atomicMax(reinterpret_cast<int*>(c.blk(q.s) + L.RF), db);
+      if ((c.lane & (SW - 1)) == 0 && q.s < c.G) atomicMax(reinterpret_cast<int*>(c.SAMP + L.RF), db);
     }
     tm_write_a<DIM, FMT>(q.lanebase, TCW, x, out);
   }
@@ -443,6 +481,8 @@ __global__ void __launch_bounds__(MAXT, 1) tm_fwd_kernel(const __grid_constant__
   if (c.tid == 0) {
     tcg::mbar_init(&ts.bar, 1);
     ts.abort = 0;
+    ts.lost = 0u;
+    ts.limit_ns = A.wait_ns ? A.wait_ns : kTmWaitNs;
   }
   tcg::fence_smem_to_async();
   tcg::fence_before();
@@ -469,7 +509,7 @@ __global__ void __launch_bounds__(MAXT, 1) tm_fwd_kernel(const __grid_constant__
   // the MMAs are issued by lane 0 of the last warp, which the pair phase
   // leaves idle or least loaded (its (sample, step) lanes come last)
   const bool issuer = c.tid == c.nthr - 32;
-  if (issuer) {
+  if (issuer && !A.skip_first_mma) {   // (skipped only by the timeout test)
     tcg::fence_after();
     tm_issue<DIM, FMT>(ts.tbase, tabs_addr, TAB, 0, TC, &ts.bar);
   }
@@ -494,6 +534,9 @@ __global__ void __launch_bounds__(MAXT, 1) tm_fwd_kernel(const __grid_constant__
     }
   }
   if (tail) write_checkpoint<DIM, NMAX>(c, tail, pc.K - last_ck, A.total_coefs);
+  // after an abandoned wait the MMA group it waited for may still be running:
+  // wait for it once more (bounded) before the columns are freed
+  if (ts.abort && c.tid == 0) tcg::mbar_wait(&ts.bar, ts.lost, ts.limit_ns);
   tcg::fence_after();
   __syncthreads();
   if (c.warp == 0) tcg::dealloc(ts.tbase, (uint32_t)ncols);

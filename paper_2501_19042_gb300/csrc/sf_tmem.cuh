@@ -65,16 +65,24 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 // Bounded wait for the phase with the given parity to complete; false when
-// the limit ran out. Polls without suspending first (the MMAs of a chunk
-// are usually done or nearly done when the threads get here), then with the
-// suspending form.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+// limit_ns nanoseconds of the global timer have passed without it. Polls
+// without suspending first (the MMAs of a chunk are usually done or nearly
+// done when the threads get here), then with the suspending form.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
   for (int i = 0; i < 4096; ++i)
     if (mbar_test_wait(bar, parity)) return true;
-  for (uint32_t i = 0; i < limit; ++i)
+  const uint64_t t0 = globaltimer();
+  for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
-  return false;
+    if (globaltimer() - t0 > limit_ns) return false;
+  }
 }
 // Arrives on the mbarrier once every tcgen05 asynchronous operation issued
 // before by this thread has completed.

@@ -234,6 +234,13 @@ class SafetyFilter:
         memory (tf32 operands in float32, the handle's 16-bit type otherwise)."""
         nat.check(self._lib, self._h, self._lib.sf_set_option(self._h, 2, int(bool(on))))
 
+    def set_wait_timeout_test(self, microseconds: int):
+        """``sf_set_option(SF_OPT_TEST_WAIT_TIMEOUT)``: for testing the
+        timeout path only. Nonzero: the tensor-memory form skips its first
+        MMA group and bounds each MMA wait by this many microseconds, so the
+        next ``sync_status`` raises SF_ERR_TIMEOUT; 0 restores normal calls."""
+        nat.check(self._lib, self._h, self._lib.sf_set_option(self._h, 3, int(microseconds)))
+
     def launch_shape(self):
         out = (C.c_int * 4)()
         nat.check(self._lib, self._h, self._lib.sf_get_launch_shape(self._h, out))

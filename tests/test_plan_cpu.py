@@ -3,7 +3,7 @@ logic only, no device): every chosen shape fits in the opt-in shared memory
 of a GB300 block, respects the launch bounds of the kernels and the
 tensor-memory form's constraints (16-bit precisions: warps in groups of
 four, the CTA's (sample, robot) rows within the 128 TMEM lanes, one partial
-of F^T q per warp group, the chunk's states within the 512 TMEM columns)
+of F^T q per warp group, a sub-chunk's states within the 512 TMEM columns)
 and takes no more samples per CTA than a scene has, and the bench workload
 gets the shape measured fastest there."""
 import math
@@ -57,7 +57,9 @@ def test_shapes_are_valid_for_random_scene_mixes(plan, prec):
         if prec != "fp32":
             assert p["warps"] % 4 == 0 and p["nq"] == p["warps"] // 4
             assert p["G"] * bucket <= 128
-            tcw = (p["tc"] + 15) // 16 * 16
+            nsub = (p["tc"] + 63) // 64          # TMEM sub-chunks of <= 64 steps
+            ts = (p["tc"] + nsub - 1) // nsub
+            tcw = (ts + 15) // 16 * 16
             ka = 8   # 16-bit operands: 8 columns per 16 coefficients
             assert 2 * dim * tcw + 2 * dim * ka <= 512
             assert p["smem"] + 256 <= SMEM_OPTIN
