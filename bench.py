@@ -211,7 +211,7 @@ def run_gpu(args):
     S, K = spec.n_samples, spec.K
     f = P.SafetyFilter(dim=spec.dim, T=spec.T, rho=RHO, coll_a=spec.coll, v_max=spec.v_max, a_max=spec.a_max,
                        max_robots=spec.n_robots, t_final=spec.t_final, precision=args.precision, device=dev.index)
-    f.set_tensor_memory(args.tensor_memory)
+    f.set_tensor_memory("auto" if args.tensor_memory == 2 else bool(args.tensor_memory))
     xb = sh.xi_bar.reshape(sc.xi_bar.shape).to(dev)
     st, gl = sh.start.contiguous().to(dev), sh.goal.contiguous().to(dev)
     stream = torch.cuda.current_stream(dev)
@@ -274,7 +274,7 @@ def run_gpu(args):
     d2h = (2 * hx.numel() + S) * 4
 
     if rank == 0:
-        tm = bool(args.tensor_memory) or args.precision != "fp32"
+        tm = args.form == "fused" and f.launch_shape()["tensor_memory"]   # the form that ran
         value = world * S / (ms * 1e-3)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -285,6 +285,8 @@ def run_gpu(args):
                        "parallelism": f"contiguous sample ranges (shard_batch) on {world} GPU(s)",
                        "l2": "flushed between timed steps by a 256 MiB write outside the events",
                        "tensor_memory": tm,
+                       "form_choice": {0: "float32 lanes", 1: "tensor memory",
+                                       2: "per robot-count bucket (library default)"}[args.tensor_memory],
                        "state_products": ({"fp32": "tf32", "bf16": "bf16", "fp16": "fp16"}[args.precision]
                                           + " three-term MMAs (tcgen05, TMEM)") if tm else "float32 lanes"},
             "median_final_residual": med_res,
@@ -704,8 +706,9 @@ def main():
     ap.add_argument("--form", default="fused", choices=["fused", "plain"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"],
                     help="contraction precision of the timed forward (the metric is quoted in fp32)")
-    ap.add_argument("--tensor-memory", type=int, default=0, choices=[0, 1],
-                    help="1: coefficient-to-state products on tcgen05 tensor cores through TMEM")
+    ap.add_argument("--tensor-memory", type=int, default=2, choices=[0, 1, 2],
+                    help="1: coefficient-to-state products on tcgen05 tensor cores through TMEM; 0: on the "
+                         "float32 lanes; 2 (default): the library's choice per robot-count bucket")
     ap.add_argument("--cpu-samples", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-diff", action="store_true")

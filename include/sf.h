@@ -60,7 +60,9 @@ typedef enum {
   SF_ERR_TIMEOUT = 4,       /* a bounded device wait ran out */
   SF_ERR_NONFINITE = 5,     /* a non-finite value reached the output */
   SF_ERR_UNSUPPORTED = 6,   /* valid request this build does not implement */
-  SF_ERR_WORKSPACE = 7      /* workspace missing or too small */
+  SF_ERR_WORKSPACE = 7,     /* workspace missing or too small */
+  SF_ERR_DEBUG_CHECK = 8    /* a library built with SF_DEBUG_CHECKS found a shared-memory canary
+                               overwritten or an index out of range (the access was skipped) */
 } sf_status;
 
 /* Arithmetic of the coefficient-to-state products (velocities and
@@ -208,20 +210,28 @@ typedef enum {
    * The decision is taken per sample. No effect in the plain form and the
    * backward's recompute. */
   SF_OPT_PAIR_PRUNING = 1,
-  /* 1: the fused forward of a float32 handle (sf_project and
-   * sf_project_train) runs the velocity / acceleration products on the tensor
+  /* Form of the fused forward of a float32 handle (sf_project and
+   * sf_project_train). 1: the velocity / acceleration products on the tensor
    * cores through tensor memory (tcgen05 MMAs, the coefficient rows of a
    * CTA's samples as the A operand in TMEM, the basis rows of a time chunk as
    * the B operand in shared memory, three-term split of tf32 operands); the
    * rest stays on the float32 lanes. 0: the float32 form, products on the
-   * lanes too. 16-bit handles always use the tensor-memory form. */
+   * lanes too. 2 (the default): per robot-count bucket, the form measured
+   * faster on a GB300 (the tensor-memory form for 3D scenes of 9..16 robots,
+   * the float32 form otherwise). Both forms give outputs within rounding of
+   * each other. 16-bit handles always use the tensor-memory form. */
   SF_OPT_TENSOR_MEMORY = 2,
   /* Test of the timeout path, value in microseconds (0 = off, the default):
    * the tensor-memory form does not issue the first MMA group of each CTA
    * and bounds every MMA wait by `value` microseconds, so the first wait runs
    * out with nothing in flight and sf_sync_status reports SF_ERR_TIMEOUT.
    * Outputs of such calls are undefined. No effect on the float32 form. */
-  SF_OPT_TEST_WAIT_TIMEOUT = 3
+  SF_OPT_TEST_WAIT_TIMEOUT = 3,
+  /* Test of the debug-build checks (libraries built with SF_DEBUG_CHECKS
+   * only; SF_ERR_UNSUPPORTED otherwise). 1: the fused kernels write a wrong
+   * value into the canary word at the end of each CTA's last sample block,
+   * so sf_sync_status reports SF_ERR_DEBUG_CHECK. Outputs are unaffected. */
+  SF_OPT_TEST_CANARY = 4
 } sf_option;
 
 /* Sets option `option` of the handle to `value` (for later calls).
@@ -231,6 +241,11 @@ sf_status sf_set_option(sf_handle *h, int option, int value);
 /* Shape of the last fused launch of the handle: out[0..3] = G, warps, tc and
  * the number of time ranges of the contraction phase. */
 sf_status sf_get_launch_shape(const sf_handle *h, int *out4);
+
+/* Form of the last fused launch of the handle (the last launch group of a
+ * batch with several robot-count buckets): 1 the tensor-memory form, 0 the
+ * float32 form. */
+sf_status sf_get_launch_form(const sf_handle *h, int *tensor_memory);
 
 /* The launch shape the library's cost model picks for one fused forward
  * launch group, without a device and without a handle: n_scenes scenes of
@@ -366,7 +381,8 @@ sf_status sf_eq_project_backward(sf_handle *h, void *stream, const sf_batch *bat
                                  float *grad_in, float *grad_b);
 
 /* Synchronises `stream` and returns any device-side error latched by earlier
- * calls on the handle (SF_ERR_TIMEOUT, SF_ERR_NONFINITE), clearing it. */
+ * calls on the handle (SF_ERR_TIMEOUT, SF_ERR_DEBUG_CHECK, SF_ERR_NONFINITE,
+ * in this order of precedence), clearing it. */
 sf_status sf_sync_status(sf_handle *h, void *stream);
 
 /* Measurement, not part of the solver: throughput of the float32-lane pipes

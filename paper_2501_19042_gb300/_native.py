@@ -10,12 +10,15 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libsf_gb300.so")
+# SF_GB300_DEBUG=1 loads the debug build (canaries and index checks in the
+# fused kernels; ``build(debug=True)`` makes it)
+DEBUG = os.environ.get("SF_GB300_DEBUG") == "1"
+LIB_PATH = os.path.join(HERE, "libsf_gb300_debug.so" if DEBUG else "libsf_gb300.so")
 
 SF_OK = 0
 STATUS_NAMES = {0: "SF_OK", 1: "SF_ERR_INVALID_ARG", 2: "SF_ERR_CUDA", 3: "SF_ERR_OOM",
                 4: "SF_ERR_TIMEOUT", 5: "SF_ERR_NONFINITE", 6: "SF_ERR_UNSUPPORTED",
-                7: "SF_ERR_WORKSPACE"}
+                7: "SF_ERR_WORKSPACE", 8: "SF_ERR_DEBUG_CHECK"}
 PREC = {"fp32": 0, "bf16": 1, "fp16": 2}
 FORM = {"fused": 0, "plain": 1}
 
@@ -26,7 +29,7 @@ EXPORTS = ("sf_create", "sf_destroy", "sf_last_error", "sf_workspace_bytes", "sf
            "sf_project_train", "sf_backward_workspace_bytes", "sf_project_backward",
            "sf_autotune", "sf_graph_capture", "sf_graph_launch", "sf_graph_destroy", "sf_sync_status",
            "sf_eq_project", "sf_eq_project_backward", "sf_set_option", "sf_plan_launch",
-           "sf_lane_peaks")
+           "sf_lane_peaks", "sf_get_launch_form")
 
 
 class SfProblem(C.Structure):
@@ -96,6 +99,8 @@ def load(path: str = LIB_PATH):
         lib.sf_set_launch_shape.restype = C.c_int
         lib.sf_get_launch_shape.argtypes = [vp, C.POINTER(C.c_int)]
         lib.sf_get_launch_shape.restype = C.c_int
+        lib.sf_get_launch_form.argtypes = [vp, C.POINTER(C.c_int)]
+        lib.sf_get_launch_form.restype = C.c_int
         lib.sf_project_train.argtypes = [vp, vp, C.POINTER(SfBatch), C.c_int, vp, vp, vp, vp, vp, vp, vp]
         lib.sf_project_train.restype = C.c_int
         lib.sf_backward_workspace_bytes.argtypes = [vp, C.POINTER(SfBatch), C.c_int]

@@ -12,6 +12,7 @@
 
 #include <cuda.h>
 
+#include "sf_debug.cuh"
 #include "sf_internal.cuh"
 
 struct sf_handle {
@@ -25,11 +26,13 @@ struct sf_handle {
   unsigned long long launches = 0;
   int force_G = 0, force_warps = 0, force_tc = 0;  // launch-shape overrides (tuning)
   int last_plan[4] = {0, 0, 0, 0};                 // G, warps, tc, nq of the last fused launch
+  int last_form = 0;                               // its form: 1 tensor memory, 0 float32 lanes
   std::map<std::string, sf::FusedPlan> tuned;      // autotuned shapes per launch-group key
   bool use_tuned = true;
   int prune = 1;                                   // SF_OPT_PAIR_PRUNING
-  int tm = 0;                                      // SF_OPT_TENSOR_MEMORY
+  int tm = 2;                                      // SF_OPT_TENSOR_MEMORY (2: per bucket)
   int wait_test_us = 0;                            // SF_OPT_TEST_WAIT_TIMEOUT
+  int plant_canary = 0;                            // SF_OPT_TEST_CANARY (debug builds)
   cudaStream_t aux[2] = {nullptr, nullptr};        // extra streams for concurrent launch groups
   cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
   float eq_pi[sf::NV * sf::NV] = {};               // QP layer operators (host copy of slot 0)
@@ -56,6 +59,20 @@ struct DeviceGuard {
 sf_status fail(sf_handle* h, sf_status s, const std::string& msg) {
   if (h) h->err = msg;
   return s;
+}
+
+const char* debug_site_name(int site) {
+  switch (site) {
+    case sf::DS_PAIR_DECODE: return "pair decoded from a candidate bit";
+    case sf::DS_CHUNK_ROW: return "chunk-buffer row";
+    case sf::DS_TMEM_COL: return "TMEM column";
+    case sf::DS_TABLE: return "MMA B-table word";
+    case sf::DS_MASK: return "activity-mask word";
+    case sf::DS_OUT: return "global output index";
+    case sf::DS_CANARY_HEAD: return "canary after the shared-memory head";
+    case sf::DS_CANARY_BLOCK: return "canary at the end of a sample block";
+    default: return "unknown site";
+  }
 }
 
 sf_status cuda_fail(sf_handle* h, cudaError_t e, const char* where) {
@@ -137,13 +154,23 @@ struct FusedRequest {
 
 // Form code of a fused forward launch (FusedLaunch::prec): the tensor-memory
 // form with the handle's operand format when the option is on or the
-// precision is 16-bit (the 16-bit products exist only there), else the
-// float32 form. The training forward follows the same rule; the adjoint is
-// the float32 form's in every case.
+// precision is 16-bit (the 16-bit products exist only there), the float32
+// form when the option is off, and FORM_AUTO (float32 handles, option 2, the
+// default) to let each launch group take the form measured faster for its
+// dimension and robot-count bucket (auto_form). The training forward follows
+// the same rule; the adjoint is the float32 form's in every case.
+constexpr int FORM_AUTO = -1;
 int forward_form(const sf_handle* h) {
   const int p = h->pb.precision;
-  return (h->tm || p != SF_PREC_FP32) ? PREC_TM_TF32 + p : 0;
+  if (p != SF_PREC_FP32 || h->tm == 1) return PREC_TM_TF32 + p;
+  return h->tm == 0 ? 0 : FORM_AUTO;
 }
+// The float32 handle's form for one bucket under FORM_AUTO: the tensor-memory
+// form where it measured faster than the float32 form on a GB300 (3D,
+// T = 100, K = 200, 1024 samples of one scene: 12 and 16 robots 0.84x and
+// 0.88x the float32 form's time; 20 and 24 robots 1.02x; 4, 8, 28, 32 robots
+// and every 2D case slower).
+int auto_form(int dim, int nmax) { return (dim == 3 && nmax == 16) ? PREC_TM_TF32 : 0; }
 
 long long total_coefs(const sf_handle* h, const sf_batch* b) {
   long long c = 0;
@@ -202,6 +229,7 @@ sf_status build_groups(sf_handle* h, const sf_batch* b, int K, long long S, cons
   }
   for (int bk = 0; bk < kBuckets; ++bk) {
     const int nmax = kBucketNmax[bk];
+    const int prec = rq.backward ? 0 : rq.prec == FORM_AUTO ? auto_form(dim, nmax) : rq.prec;
     for (size_t first = 0; first < items[bk].size(); first += MAX_SCENES_PER_LAUNCH) {
       const size_t last = std::min(items[bk].size(), first + (size_t)MAX_SCENES_PER_LAUNCH);
       std::vector<int> nr, ns;
@@ -210,7 +238,7 @@ sf_status build_groups(sf_handle* h, const sf_batch* b, int K, long long S, cons
         ns.push_back(b->n_samples[items[bk][q].scene]);
       }
       LaunchGroup lg;
-      lg.key = group_key(rq.backward, rq.prec, dim, nmax, T, nr, ns);
+      lg.key = group_key(rq.backward, prec, dim, nmax, T, nr, ns);
       FusedPlan plan;
       auto hit = h->tuned.find(lg.key);
       const bool forced = h->force_G || h->force_warps || h->force_tc;
@@ -218,7 +246,7 @@ sf_status build_groups(sf_handle* h, const sf_batch* b, int K, long long S, cons
         plan = hit->second;
       } else {
         plan = plan_fused(dim, nmax, T, nr.data(), ns.data(), (int)nr.size(), h->num_sms, h->max_smem_optin,
-                          h->force_G, h->force_warps, h->force_tc, rq.backward, nullptr, 0, rq.prec);
+                          h->force_G, h->force_warps, h->force_tc, rq.backward, nullptr, 0, prec);
       }
       if (plan.G == 0) return fail(h, SF_ERR_UNSUPPORTED, "no fused launch shape fits in shared memory");
       FusedArgs& a = lg.a;
@@ -248,6 +276,7 @@ sf_status build_groups(sf_handle* h, const sf_batch* b, int K, long long S, cons
       a.prune = h->prune ? 1 : 0;
       a.wait_ns = 1000ull * (unsigned long long)h->wait_test_us;
       a.skip_first_mma = h->wait_test_us > 0 ? 1 : 0;
+      a.dbg_plant = h->plant_canary;
       if (rq.ckpt && !rq.backward) {
         const long long ck = a.ck_every, nck = (K + ck - 1) / ck;
         a.amask = reinterpret_cast<unsigned*>(rq.ckpt + states_floats_aligned(nck + ck + 1, tot));
@@ -276,13 +305,14 @@ sf_status build_groups(sf_handle* h, const sf_batch* b, int K, long long S, cons
       l.warps = plan.warps;
       l.tc = plan.tc;
       l.nq = plan.nq;
-      l.prec = rq.prec;
-      l.smem = fused_smem_bytes(dim, nmax, T, gmax, plan.tc, plan.nq, rq.backward, rq.prec);
+      l.prec = prec;
+      l.smem = fused_smem_bytes(dim, nmax, T, gmax, plan.tc, plan.nq, rq.backward, prec);
       if (l.smem > h->max_smem_optin) return fail(h, SF_ERR_UNSUPPORTED, "launch shape exceeds shared memory");
       h->last_plan[0] = plan.G;
       h->last_plan[1] = plan.warps;
       h->last_plan[2] = plan.tc;
       h->last_plan[3] = plan.nq;
+      h->last_form = (!rq.backward && prec >= PREC_TM_TF32) ? 1 : 0;
       out->push_back(lg);
     }
   }
@@ -363,7 +393,8 @@ sf_status sf_create(const sf_problem* pb, int device, sf_handle** out) {
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete h; return SF_ERR_CUDA; }
   h->num_sms = prop.multiProcessorCount;
-  h->max_smem_optin = prop.sharedMemPerBlockOptin;
+  // (debug builds: room for the static debug word of every fused kernel)
+  h->max_smem_optin = prop.sharedMemPerBlockOptin - (SF_DEBUG_CHECKS ? 16 : 0);
   double* scratch = nullptr;
   const size_t nscr = precompute_scratch_doubles(pb->T, pb->order, pb->max_robots);
   cudaError_t e = cudaMalloc(&h->basis, sizeof(float) * (size_t)pb->T * BASIS_ROW);
@@ -712,7 +743,7 @@ sf_status sf_autotune(sf_handle* h, void* stream, const sf_batch* b, int K_probe
     }
     std::vector<FusedPlan> top(n_candidates);
     plan_fused(h->pb.dim, lg.l.nmax, h->pb.T, nr.data(), ns.data(), (int)nr.size(), h->num_sms, h->max_smem_optin,
-               0, 0, 0, false, top.data(), n_candidates, rq.prec);
+               0, 0, 0, false, top.data(), n_candidates, lg.l.prec);
     float best_ms = INFINITY;
     FusedPlan best = top[0];
     for (int c = 0; c < n_candidates && e == cudaSuccess; ++c) {
@@ -734,7 +765,7 @@ sf_status sf_autotune(sf_handle* h, void* stream, const sf_batch* b, int K_probe
       t.l.warps = p.warps;
       t.l.tc = p.tc;
       t.l.nq = p.nq;
-      t.l.smem = fused_smem_bytes(h->pb.dim, t.l.nmax, h->pb.T, gmax, p.tc, p.nq, false, rq.prec);
+      t.l.smem = fused_smem_bytes(h->pb.dim, t.l.nmax, h->pb.T, gmax, p.tc, p.nq, false, t.l.prec);
       if (t.l.smem > h->max_smem_optin) continue;
       float ms_sum = 0.0f;
       for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {   // first run warms up
@@ -834,6 +865,12 @@ sf_status sf_set_launch_shape(sf_handle* h, int G, int warps, int tc) {
 sf_status sf_get_launch_shape(const sf_handle* h, int* out4) {
   if (!h || !out4) return SF_ERR_INVALID_ARG;
   for (int q = 0; q < 4; ++q) out4[q] = h->last_plan[q];
+  return SF_OK;
+}
+
+sf_status sf_get_launch_form(const sf_handle* h, int* tensor_memory) {
+  if (!h || !tensor_memory) return SF_ERR_INVALID_ARG;
+  *tensor_memory = h->last_form;
   return SF_OK;
 }
 
@@ -1054,7 +1091,7 @@ sf_status sf_set_option(sf_handle* h, int option, int value) {
     return SF_OK;
   }
   if (option == SF_OPT_TENSOR_MEMORY) {
-    if (value != 0 && value != 1) return fail(h, SF_ERR_INVALID_ARG, "SF_OPT_TENSOR_MEMORY takes 0 or 1");
+    if (value < 0 || value > 2) return fail(h, SF_ERR_INVALID_ARG, "SF_OPT_TENSOR_MEMORY takes 0, 1 or 2");
     h->tm = value;
     return SF_OK;
   }
@@ -1063,6 +1100,15 @@ sf_status sf_set_option(sf_handle* h, int option, int value) {
       return fail(h, SF_ERR_INVALID_ARG, "SF_OPT_TEST_WAIT_TIMEOUT takes 0 .. 1000000 microseconds");
     h->wait_test_us = value;
     return SF_OK;
+  }
+  if (option == SF_OPT_TEST_CANARY) {
+#if SF_DEBUG_CHECKS
+    if (value != 0 && value != 1) return fail(h, SF_ERR_INVALID_ARG, "SF_OPT_TEST_CANARY takes 0 or 1");
+    h->plant_canary = value;
+    return SF_OK;
+#else
+    return fail(h, SF_ERR_UNSUPPORTED, "SF_OPT_TEST_CANARY needs a library built with SF_DEBUG_CHECKS");
+#endif
   }
   return fail(h, SF_ERR_INVALID_ARG, "unknown option");
 }
@@ -1079,6 +1125,10 @@ sf_status sf_sync_status(sf_handle* h, void* stream) {
   if (word) {
     cudaMemset(h->status, 0, sizeof(int));
     if (word & ST_TIMEOUT) return fail(h, SF_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (word & ST_DEBUG)
+      return fail(h, SF_ERR_DEBUG_CHECK,
+                  "debug check failed at site " + std::to_string((word >> 8) & 0xFF) + " (" +
+                      debug_site_name((word >> 8) & 0xFF) + ")");
     if (word & ST_NONFINITE) return fail(h, SF_ERR_NONFINITE, "non-finite value in the output");
   }
   return SF_OK;

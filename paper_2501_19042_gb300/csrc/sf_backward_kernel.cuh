@@ -427,7 +427,9 @@ __global__ void __launch_bounds__(MAXT, 1) fused_bwd_kernel(const __grid_constan
   const Lay& L = c.L;
   const int N = c.N, G = c.G;
   const long long tot = A.total_coefs;
+  dbg_begin();
   prologue<DIM, NMAX>(c, T, A.basis, A.ops, A.start, A.goal, A.start_va, A.goal_va);
+  canary_set(c.SAMP, L.SB, G, 0);
   for (int v = c.tid; v < G * NMAX * RS; v += c.nthr) {
     const int s = v / (NMAX * RS), rem = v % (NMAX * RS);
     const int i = rem / RS, x = (rem / NP) % DIM, k = rem % NP;
@@ -484,6 +486,8 @@ __global__ void __launch_bounds__(MAXT, 1) fused_bwd_kernel(const __grid_constan
     if (A.gl0) A.gl0[g] = blk[L.LB + o];
     if (A.gxb) A.gxb[g] = blk[L.GXB + o] + (A.xi0_is_xi_bar ? blk[L.XB + o] : 0.0f);
   }
+  canary_check(c.SAMP, L.SB, G);
+  dbg_end(A.status);
 }
 
 template <int DIM, int NMAX, int MAXT>

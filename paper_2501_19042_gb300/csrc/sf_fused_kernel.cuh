@@ -28,6 +28,7 @@
 // row by row as F(xi^K - xi^{K-1}) - q(xi^{K-1}).
 // Every reduction is done in a fixed order: results are bit-reproducible.
 #pragma once
+#include "sf_debug.cuh"
 #include "sf_internal.cuh"
 #include "sf_pack16.cuh"
 
@@ -142,13 +143,13 @@ struct Lay {
     CM = CR + (cand ? nmax * RS : 0);
     WC = CM + T * CMW;
     RF = WC + (cand ? ((T + 3) / 4) * 4 : 0);
-    SB = RF + (cand ? 4 : 0);
+    SB = RF + (cand ? 4 : 0) + kCanaryWords;   // (debug builds: canary words at the end)
     // head: (tensor-memory form) the MMA B tables (Pd, Pdd; rounded and
     // remainder), then the float32 basis [T][36], the operators and beta
     basis = tmp >= 0 ? TM_TABLES * tm_tab_bytes(T, TC, tmp) / 4 : 0;
     opso = basis + T * BASIS_ROW;
     betao = opso + 4 * NV * NP;
-    head = betao + nmax * RS;
+    head = betao + nmax * RS + kCanaryWords;
   }
 };
 
@@ -365,7 +366,9 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
 #pragma unroll
       for (int x = 0; x < DIM; ++x) E[i][x] = 0.0f;
     float res2 = 0.0f;
-    float* ebw = blk + L.EB + tl * L.EP;   // this lane's row of the chunk buffer
+    // this lane's row of the chunk buffer (a row past the buffer, which a
+    // debug build reports, is redirected to row 0)
+    float* ebw = blk + L.EB + (dcheck(L.EB + (tl + 1) * L.EP <= L.RS2, DS_CHUNK_ROW) ? tl : 0) * L.EP;
     unsigned* mrow = MASKS ? mk + ((size_t)s * L.T + t) * MW : nullptr;
     if (MASKS && valid) {
 #pragma unroll
@@ -444,6 +447,7 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
             m &= m - 1;
             int i, j;
             pair_of_bit<NMAX>(idx, i, j);
+            if (!dcheck(i >= 0 && i < j && j < N, DS_PAIR_DECODE)) continue;
             float pi[DIM], pj[DIM];
             state<DIM>(Pr, Cs + i * RS, pi);
             state<DIM>(Pr, Cs + j * RS, pj);
@@ -1257,12 +1261,15 @@ __device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, 
       pair_phase<DIM, NMAX, false, CAND>(c.SAMP, L, c.BASIS, G, N, t0, TCc, pc, want_res, c.warp,
                                                 c.nwarps, c.lane, nullptr, prune);
       __syncthreads();
+      canary_check(c.SAMP, L.SB, G);
       contract_phase<DIM>(c.SAMP, L, c.BASIS, G, N, t0, TCc, t0 == 0, pc, want_res, c.tid, c.nthr);
     }
     __syncthreads();
+    canary_check(c.SAMP, L.SB, G);
   }
   solve_lambda_means<DIM, NMAX, CAND>(c, pc, it, hist, total_samples, fp);
   __syncthreads();
+  canary_check(c.SAMP, L.SB, G);
   // ---- solve phase 2: xi step, xi_i = W1 c_i + S1 r_i + (DW mean(c) +
   // DS mean(r)) + beta_i per (sample, robot, axis)
   for (int v = c.tid; v < G * N * DIM; v += c.nthr) {
@@ -1271,6 +1278,7 @@ __device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, 
     xi_step_row<DIM, NMAX, CAND>(c, pc, s, i, x, keep_prev, fp, out);
   }
   __syncthreads();
+  canary_check(c.SAMP, L.SB, G);
   if (fp) {
     for (int s = c.tid; s < G; s += c.nthr) {
       float* blk = c.blk(s);
@@ -1305,9 +1313,11 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
   const Lay& L = c.L;
   const int N = c.N, G = c.G;
   const bool fp = A.fp_res2 != nullptr;
+  dbg_begin();
 
   prologue<DIM, NMAX>(c, T, A.basis, A.ops, A.start, A.goal, A.start_va, A.goal_va);
   load_state<DIM, NMAX>(c, A.xi0, A.lam0, A.xi_bar, A.xi_bar);
+  canary_set(c.SAMP, L.SB, G, A.dbg_plant);
   for (int s = c.tid; s < G; s += c.nthr) {
     c.blk(s)[L.FPR] = 0.0f;
     if (CAND) *reinterpret_cast<int*>(c.blk(s) + L.RF) = __float_as_int(INFINITY);   // first test is full
@@ -1349,6 +1359,8 @@ __global__ void __launch_bounds__(MAXT, 1) fused_fwd_kernel(const __grid_constan
     if (!isfinite(r)) atomicOr(A.status, ST_NONFINITE);
   }
   store_state<DIM, NMAX>(c, A.xi_out, A.lam_out, 0);
+  canary_check(c.SAMP, L.SB, G);
+  dbg_end(A.status);
 }
 
 template <int DIM, int NMAX, int MAXT, bool MASKS = false>

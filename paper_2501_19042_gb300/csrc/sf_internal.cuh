@@ -61,7 +61,7 @@ __host__ __device__ constexpr int mask_words(int nmax) {
 __host__ __device__ constexpr int pair_bit(int nmax, int i, int j) { return i * nmax - i * (i + 1) / 2 + (j - i - 1); }
 
 // Bounded-wait / status words latched on the device.
-enum : int { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
+enum : int { ST_NONFINITE = 1, ST_TIMEOUT = 2, ST_DEBUG = 4 };   // ST_DEBUG: site in bits 8..15
 
 struct ProblemConsts {
   int dim, T, K;
@@ -108,6 +108,7 @@ struct FusedArgs {
   int prune;               // float32 form: exact pair pruning on (1) or every pair tested (0)
   unsigned long long wait_ns;   // tensor-memory form: bound of each MMA wait (0: the default)
   int skip_first_mma;      // tensor-memory form: the first MMA group is not issued (timeout test)
+  int dbg_plant;           // debug builds: a wrong canary word is planted (test of the checks)
   SceneDesc sc[MAX_SCENES_PER_LAUNCH];
 };
 

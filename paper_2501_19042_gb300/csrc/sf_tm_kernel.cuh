@@ -75,6 +75,7 @@ __device__ void tm_tables(unsigned char* tb, int T, int TC, const float* gb, int
       const float x = gb[(size_t)t * BASIS_ROW + (1 + m) * NP + k];
       const int row = row_of(t);
       const uint32_t off = (row >> 3) * SBO + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4;
+      if (!dcheck(off + 4 <= (uint32_t)TAB, DS_TABLE)) continue;
       const uint32_t h = tcg::tf32_rna(x);
       const uint32_t l = tcg::tf32_rna(x - __uint_as_float(h));
       *reinterpret_cast<uint32_t*>(tb + (2 * m) * TAB + off) = h;
@@ -88,6 +89,7 @@ __device__ void tm_tables(unsigned char* tb, int T, int TC, const float* gb, int
       const float x1 = k0 + 1 < NV ? row_[k0 + 1] : 0.0f;
       const int row = row_of(t);
       const uint32_t off = (row >> 3) * SBO + (k0 >> 3) * 128 + (row & 7) * 16 + (k0 & 7) * 2;
+      if (!dcheck(off + 4 <= (uint32_t)TAB, DS_TABLE)) continue;
       *reinterpret_cast<uint32_t*>(tb + (2 * m) * TAB + off) = pack16<FMT>(x0, x1);
       *reinterpret_cast<uint32_t*>(tb + (2 * m + 1) * TAB + off) =
           pack16<FMT>(x0 - tc::round16<FMT>(x0), x1 - tc::round16<FMT>(x1));
@@ -205,13 +207,19 @@ template <int DIM, int NMAX>
 __device__ __forceinline__ void tm_block_load(const TmLane& q, const float* blk, const Lay& L, int TCW, int tb,
                                               int TCc, int eb0, uint32_t (&v)[DIM][8], uint32_t (&a)[DIM][8],
                                               float (&fl)[8]) {
+  // (a block past its state's columns, which a debug build reports, is
+  // redirected to the first block)
+  if (!dcheck(tb + 8 <= TCW, DS_TMEM_COL)) tb = 0;
 #pragma unroll
   for (int x = 0; x < DIM; ++x) {
     tcg::ld8(q.lanebase + (uint32_t)(x * TCW + tb), v[x]);
     tcg::ld8(q.lanebase + (uint32_t)((DIM + x) * TCW + tb), a[x]);
   }
 #pragma unroll
-  for (int j = 0; j < 8; ++j) fl[j] = (tb + j < TCc) ? blk[L.EB + (eb0 + tb + j) * L.EP + NMAX * DIM] : 0.0f;
+  for (int j = 0; j < 8; ++j)
+    fl[j] = (tb + j < TCc && dcheck(L.EB + (eb0 + tb + j + 1) * L.EP <= L.RS2, DS_CHUNK_ROW))
+                ? blk[L.EB + (eb0 + tb + j) * L.EP + NMAX * DIM]
+                : 0.0f;
 }
 
 // One 8-step block of the TMEM pass on loaded values: every lane first
@@ -344,6 +352,7 @@ __device__ void tm_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, i
       pair_phase<DIM, NMAX, false, CAND, true>(c.SAMP, L, gbasis, c.G, c.N, t0, TCc, pc, want_res, c.warp,
                                                       c.nwarps, c.lane, nullptr, prune);
     __syncthreads();
+    canary_check(c.SAMP, L.SB, c.G);
     // the chunk's TMEM sub-chunks; the MMAs of the next sub-chunk start as
     // soon as the pass of this one has read the states
     for (int j = 0; j < NSUB; ++j) {
@@ -403,8 +412,10 @@ __device__ void tm_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, i
   }
   tcg::fence_before();
   __syncthreads();
+  canary_check(c.SAMP, L.SB, c.G);
   solve_lambda_means<DIM, NMAX, CAND>(c, pc, it, hist, total_samples, TRAIN && fp);
   __syncthreads();
+  canary_check(c.SAMP, L.SB, c.G);
   // xi step, one (sample, robot) row per lane and the axes over the warp
   // groups; the new rows also go to A in TMEM
   // the CTA's drift word: the lanes of one sample reduce their rows' drift
@@ -434,6 +445,7 @@ __device__ void tm_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, i
   tcg::wait_st();
   tcg::fence_before();
   __syncthreads();
+  canary_check(c.SAMP, L.SB, c.G);
   if (TRAIN && fp) {
     // ||z^{k+1} - z^k||^2 of this iteration, added per sample
     for (int s = c.tid; s < c.G; s += c.nthr) {
@@ -460,6 +472,7 @@ __global__ void __launch_bounds__(MAXT, 1) tm_fwd_kernel(const __grid_constant__
   constexpr bool CAND = true;
   const Cta<DIM, NMAX> c(A.sc, A.n_scenes, T, A.tc, A.nq, false, sm, CAND, FMT);
   if (c.G <= 0) return;
+  dbg_begin();
   const Lay& L = c.L;
   const int TC = L.TC, TCW = tm_tcw(TC);
   const int TAB = tm_tab_bytes(T, TC, FMT);
@@ -470,6 +483,7 @@ __global__ void __launch_bounds__(MAXT, 1) tm_fwd_kernel(const __grid_constant__
   tm_tables<FMT>(tabs, T, TC, reinterpret_cast<const float*>(A.basis), c.tid, c.nthr);   // from global memory
   prologue<DIM, NMAX>(c, T, A.basis, A.ops, A.start, A.goal, A.start_va, A.goal_va);
   load_state<DIM, NMAX>(c, A.xi0, A.lam0, A.xi_bar, A.xi_bar);
+  canary_set(c.SAMP, L.SB, c.G, A.dbg_plant);
   for (int s = c.tid; s < c.G; s += c.nthr) {
     c.blk(s)[L.FPR] = 0.0f;
     *reinterpret_cast<int*>(c.blk(s) + L.RF) = __float_as_int(INFINITY);   // the first pair test is full
@@ -562,6 +576,8 @@ __global__ void __launch_bounds__(MAXT, 1) tm_fwd_kernel(const __grid_constant__
     if (!isfinite(r)) atomicOr(A.status, ST_NONFINITE);
   }
   store_state<DIM, NMAX>(c, A.xi_out, A.lam_out, 0);
+  canary_check(c.SAMP, L.SB, G);
+  dbg_end(A.status);
 }
 
 template <int DIM, int NMAX, int MAXT, int FMT, bool TRAIN = false>

@@ -228,11 +228,14 @@ class SafetyFilter:
         rows between full tests (default on)."""
         nat.check(self._lib, self._h, self._lib.sf_set_option(self._h, 1, int(bool(on))))
 
-    def set_tensor_memory(self, on: bool):
-        """``sf_set_option(SF_OPT_TENSOR_MEMORY)``: the forward's
+    def set_tensor_memory(self, on):
+        """``sf_set_option(SF_OPT_TENSOR_MEMORY)``: True puts the forward's
         coefficient-to-state products on tcgen05 tensor cores through tensor
-        memory (tf32 operands in float32, the handle's 16-bit type otherwise)."""
-        nat.check(self._lib, self._h, self._lib.sf_set_option(self._h, 2, int(bool(on))))
+        memory (tf32 operands in float32, the handle's 16-bit type otherwise),
+        False keeps them on the float32 lanes, "auto" (the default) takes the
+        form measured faster per robot-count bucket."""
+        value = 2 if on == "auto" else int(bool(on))
+        nat.check(self._lib, self._h, self._lib.sf_set_option(self._h, 2, value))
 
     def set_wait_timeout_test(self, microseconds: int):
         """``sf_set_option(SF_OPT_TEST_WAIT_TIMEOUT)``: for testing the
@@ -244,7 +247,9 @@ class SafetyFilter:
     def launch_shape(self):
         out = (C.c_int * 4)()
         nat.check(self._lib, self._h, self._lib.sf_get_launch_shape(self._h, out))
-        return {"G": out[0], "warps": out[1], "tc": out[2], "nq": out[3]}
+        form = C.c_int(0)
+        nat.check(self._lib, self._h, self._lib.sf_get_launch_form(self._h, C.byref(form)))
+        return {"G": out[0], "warps": out[1], "tc": out[2], "nq": out[3], "tensor_memory": bool(form.value)}
 
     def checkpoint_bytes(self, xi_bar, start, goal, K, n_robots=None, n_samples=None) -> int:
         b, _keep, _, _ = self._batch(xi_bar, start, goal, n_robots, n_samples, None, None)
