@@ -157,7 +157,8 @@ struct FusedRequest {
 // precision is 16-bit (the 16-bit products exist only there), the float32
 // form when the option is off, and FORM_AUTO (float32 handles, option 2, the
 // default) to let each launch group take the form measured faster for its
-// dimension and robot-count bucket (auto_form). The training forward follows
+// dimension, robot-count bucket, K and launch shape (auto_tm_candidate,
+// kAutoTmMinG). The training forward follows
 // the same rule; the adjoint is the float32 form's in every case.
 constexpr int FORM_AUTO = -1;
 int forward_form(const sf_handle* h) {
@@ -165,12 +166,16 @@ int forward_form(const sf_handle* h) {
   if (p != SF_PREC_FP32 || h->tm == 1) return PREC_TM_TF32 + p;
   return h->tm == 0 ? 0 : FORM_AUTO;
 }
-// The float32 handle's form for one bucket under FORM_AUTO: the tensor-memory
-// form where it measured faster than the float32 form on a GB300 (3D,
-// T = 100, K = 200, 1024 samples of one scene: 12 and 16 robots 0.84x and
-// 0.88x the float32 form's time; 20 and 24 robots 1.02x; 4, 8, 28, 32 robots
-// and every 2D case slower).
-int auto_form(int dim, int nmax) { return (dim == 3 && nmax == 16) ? PREC_TM_TF32 : 0; }
+// The float32 handle's form for one launch group under FORM_AUTO: the
+// tensor-memory form where it measured faster than the float32 form on a
+// GB300, i.e. 3D scenes of 9..16 robots, K >= 100 and a launch shape of the
+// tensor-memory form with at least 6 samples per CTA (96 of the 128 TMEM
+// lanes in use). Measured, T = 100: 16 robots, K = 200: 768..2048 samples
+// 0.81..0.85x the float32 form's time, 512 samples (4 per CTA) 1.13x,
+// <= 256 samples 1.4..1.6x; K = 50: 0.97..1.06x; 12 robots, 1024 samples
+// 0.78x; 20 and 24 robots 1.02x; 4, 8, 28, 32 robots and every 2D case slower.
+bool auto_tm_candidate(int dim, int nmax, int K) { return dim == 3 && nmax == 16 && K >= 100; }
+constexpr int kAutoTmMinG = 6;
 
 long long total_coefs(const sf_handle* h, const sf_batch* b) {
   long long c = 0;
@@ -227,9 +232,17 @@ sf_status build_groups(sf_handle* h, const sf_batch* b, int K, long long S, cons
       moff += (long long)Ss * T * mask_words(kBucketNmax[bk]);
     }
   }
+  // longest processing time first: a CTA's work grows with its scene's robot
+  // count (N (N - 1) / 2 pair rows per step), and the block scheduler starts
+  // CTAs in index order as SMs free up, so the scenes of a launch are laid
+  // out by decreasing N (the outputs keep the batch's own layout)
+  for (int bk = 0; bk < kBuckets; ++bk)
+    std::stable_sort(items[bk].begin(), items[bk].end(),
+                     [&](const Item& x, const Item& y) { return b->n_robots[x.scene] > b->n_robots[y.scene]; });
   for (int bk = 0; bk < kBuckets; ++bk) {
     const int nmax = kBucketNmax[bk];
-    const int prec = rq.backward ? 0 : rq.prec == FORM_AUTO ? auto_form(dim, nmax) : rq.prec;
+    const bool auto_tm = !rq.backward && rq.prec == FORM_AUTO && auto_tm_candidate(dim, nmax, K);
+    const int prec0 = rq.backward ? 0 : rq.prec == FORM_AUTO ? (auto_tm ? PREC_TM_TF32 : 0) : rq.prec;
     for (size_t first = 0; first < items[bk].size(); first += MAX_SCENES_PER_LAUNCH) {
       const size_t last = std::min(items[bk].size(), first + (size_t)MAX_SCENES_PER_LAUNCH);
       std::vector<int> nr, ns;
@@ -238,15 +251,19 @@ sf_status build_groups(sf_handle* h, const sf_batch* b, int K, long long S, cons
         ns.push_back(b->n_samples[items[bk][q].scene]);
       }
       LaunchGroup lg;
-      lg.key = group_key(rq.backward, prec, dim, nmax, T, nr, ns);
-      FusedPlan plan;
-      auto hit = h->tuned.find(lg.key);
       const bool forced = h->force_G || h->force_warps || h->force_tc;
-      if (!forced && h->use_tuned && hit != h->tuned.end()) {
-        plan = hit->second;
-      } else {
-        plan = plan_fused(dim, nmax, T, nr.data(), ns.data(), (int)nr.size(), h->num_sms, h->max_smem_optin,
-                          h->force_G, h->force_warps, h->force_tc, rq.backward, nullptr, 0, prec);
+      auto make_plan = [&](int pr, std::string* key) {
+        *key = group_key(rq.backward, pr, dim, nmax, T, nr, ns);
+        auto hit = h->tuned.find(*key);
+        if (!forced && h->use_tuned && hit != h->tuned.end()) return hit->second;
+        return plan_fused(dim, nmax, T, nr.data(), ns.data(), (int)nr.size(), h->num_sms, h->max_smem_optin,
+                          h->force_G, h->force_warps, h->force_tc, rq.backward, nullptr, 0, pr);
+      };
+      int prec = prec0;
+      FusedPlan plan = make_plan(prec, &lg.key);
+      if (auto_tm && plan.G < kAutoTmMinG) {   // too few samples per CTA: the float32 form
+        prec = 0;
+        plan = make_plan(prec, &lg.key);
       }
       if (plan.G == 0) return fail(h, SF_ERR_UNSUPPORTED, "no fused launch shape fits in shared memory");
       FusedArgs& a = lg.a;
@@ -337,9 +354,25 @@ sf_status launch_groups(sf_handle* h, cudaStream_t st, const std::vector<LaunchG
   cudaError_t e = cudaEventRecord(h->fork, st);
   for (int q = 0; q < 2 && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(h->aux[q], h->fork, 0);
   if (e != cudaSuccess) return cuda_fail(h, e, "fork of launch groups");
+  // up to 3 groups at once: longest first, each onto the stream with the
+  // least work so far (work of a group ~ sum over its scenes of S (N^2 + 8 N))
+  std::vector<double> cost(gs.size(), 0.0);
+  std::vector<size_t> order(gs.size());
   for (size_t gi = 0; gi < gs.size(); ++gi) {
-    cudaStream_t s = gi % 3 == 0 ? st : h->aux[gi % 3 - 1];   // up to 3 groups at once
-    e = launch_group(gs[gi], rq, s);
+    order[gi] = gi;
+    for (int q = 0; q < gs[gi].a.n_scenes; ++q) {
+      const double N = gs[gi].a.sc[q].N;
+      cost[gi] += (double)gs[gi].a.sc[q].S * (N * N + 8.0 * N);
+    }
+  }
+  std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+  double load[3] = {0.0, 0.0, 0.0};
+  for (size_t gi : order) {
+    int q = 0;
+    for (int r = 1; r < 3; ++r)
+      if (load[r] < load[q]) q = r;
+    load[q] += cost[gi];
+    e = launch_group(gs[gi], rq, q == 0 ? st : h->aux[q - 1]);
     if (e != cudaSuccess) return cuda_fail(h, e, what);
     h->launches += 1;
   }

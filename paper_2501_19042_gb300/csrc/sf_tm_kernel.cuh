@@ -225,10 +225,13 @@ __device__ __forceinline__ void tm_block_load(const TmLane& q, const float* blk,
 // One 8-step block of the TMEM pass on loaded values: every lane first
 // evaluates its 24 conditions (velocity outside, acceleration outside, pair
 // row active, per step) into one word; a single warp-wide OR then tells
-// which of the (rare) projections and F^T updates the warp has to run.
+// which of the (rare) projections and F^T updates the warp has to run. Those
+// run in a loop over the set bits (one copy of the code, not one per step),
+// re-reading the step's state from TMEM (the warp takes the same bits, so
+// the warp-wide loads stay converged).
 template <int DIM, int NMAX>
 __device__ __forceinline__ void tm_block(const TmLane& q, const float* blk, const Lay& L, const ProblemConsts& pc,
-                                         int t0, int tb, int TCc, int eb0, const float* gbasis, float vm2,
+                                         int t0, int tb, int TCc, int TCW, int eb0, const float* gbasis, float vm2,
                                          float am2, const uint32_t (&v)[DIM][8], const uint32_t (&a)[DIM][8],
                                          const float (&fl)[8], float (&g)[DIM][NV], float& rb, unsigned* mk) {
   uint32_t bj[8];
@@ -247,49 +250,45 @@ __device__ __forceinline__ void tm_block(const TmLane& q, const float* blk, cons
   }
   // a tree of ORs (no serial chain through the steps)
   const uint32_t bits = ((bj[0] | bj[1]) | (bj[2] | bj[3])) | ((bj[4] | bj[5]) | (bj[6] | bj[7]));
-  const uint32_t any = __reduce_or_sync(FULL, bits);
-  if (!any) return;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
+  uint32_t any = __reduce_or_sync(FULL, bits);
+#pragma unroll 1
+  while (any) {
+    const int bit = __ffs(any) - 1;
+    any &= any - 1;
+    const int kind = bit >> 3, j = bit & 7;   // 0 velocity, 1 acceleration, 2 pair rows
+    const bool mine = (bits >> bit) & 1u;
     const float* brow = gbasis + (size_t)(t0 + tb + j) * BASIS_ROW;
+    float w[DIM];
+    if (kind < 2) {
+      uint32_t r[DIM];
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      const uint32_t bit = 1u << (8 * b + j);
-      if (any & bit) {
-        // lanes whose row is inside the ball take q = 0 (w = 0)
-        const bool mine = (bits & bit) != 0u;
-        float w[DIM], qb[DIM], rl = 0.0f;
+      for (int x = 0; x < DIM; ++x) tcg::ld1(q.lanebase + (uint32_t)((kind * DIM + x) * TCW + tb + j), r[x]);
+      tcg::wait_ld();
+      tcg::tie(r);
+      // lanes whose row is inside the ball take q = 0 (w = 0)
+      float qb[DIM], rl = 0.0f;
 #pragma unroll
-        for (int x = 0; x < DIM; ++x) w[x] = mine ? __uint_as_float(b == 0 ? v[x][j] : a[x][j]) : 0.0f;
-        ball_residual<DIM>(w, b == 0 ? pc.v_max : pc.a_max, qb, rl);
-        rb += rl;
-        if (mk && mine) {   // activity mask of the ball row (training forward)
-          unsigned* mball = mk + ((size_t)q.s * L.T + t0 + tb + j) * mask_words(NMAX) + mask_pair_words(NMAX);
-          const int mb = b * NMAX + q.i;
-          atomicOr(mball + (mb >> 5), 1u << (mb & 31));
-        }
-        float P[NV];
-        row_from(brow + (1 + b) * NP, P);
-#pragma unroll
-        for (int x = 0; x < DIM; ++x)
-#pragma unroll
-          for (int k = 0; k < NV; ++k) g[x][k] = fmaf(P[k], qb[x], g[x][k]);
+      for (int x = 0; x < DIM; ++x) w[x] = mine ? __uint_as_float(r[x]) : 0.0f;
+      ball_residual<DIM>(w, kind == 0 ? pc.v_max : pc.a_max, qb, rl);
+      rb += rl;
+      if (mk && mine) {   // activity mask of the ball row (training forward)
+        unsigned* mball = mk + ((size_t)q.s * L.T + t0 + tb + j) * mask_words(NMAX) + mask_pair_words(NMAX);
+        const int mb = kind * NMAX + q.i;
+        atomicOr(mball + (mb >> 5), 1u << (mb & 31));
       }
-    }
-    const uint32_t ebit = 1u << (16 + j);
-    if (any & ebit) {
-      const bool mine = (bits & ebit) != 0u;
+#pragma unroll
+      for (int x = 0; x < DIM; ++x) w[x] = qb[x];
+    } else {
       const float* eb = blk + L.EB + (eb0 + tb + j) * L.EP + q.i * DIM;
-      float e[DIM];
 #pragma unroll
-      for (int x = 0; x < DIM; ++x) e[x] = mine ? eb[x] : 0.0f;
-      float P[NV];
-      row_from(brow, P);
-#pragma unroll
-      for (int x = 0; x < DIM; ++x)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) g[x][k] = fmaf(P[k], e[x], g[x][k]);
+      for (int x = 0; x < DIM; ++x) w[x] = mine ? eb[x] : 0.0f;
     }
+    float P[NV];
+    row_from(brow + (kind == 2 ? 0 : (1 + kind) * NP), P);
+#pragma unroll
+    for (int x = 0; x < DIM; ++x)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) g[x][k] = fmaf(P[k], w[x], g[x][k]);
   }
 }
 
@@ -319,7 +318,7 @@ __device__ void tm_chunk_pass(const Cta<DIM, NMAX>& c, const TmLane& q, const Pr
       tcg::tie(v[x]);
       tcg::tie(a[x]);
     }
-    tm_block<DIM, NMAX>(q, blk, L, pc, t0, bk * 8, TCc, eb0, gbasis, vm2, am2, v, a, fl, g, rb, mk);
+    tm_block<DIM, NMAX>(q, blk, L, pc, t0, bk * 8, TCc, TCW, eb0, gbasis, vm2, am2, v, a, fl, g, rb, mk);
   }
 }
 

@@ -249,20 +249,23 @@ def test_training_forward_full_size_sampled(sfmod, oracle_lib, prec):
 
 def test_default_form_per_bucket(sfmod):
     """A float32 handle's default (SF_OPT_TENSOR_MEMORY = 2) takes the
-    tensor-memory form for 3D scenes of 9..16 robots and the float32 form
+    tensor-memory form for 3D scenes of 9..16 robots when K >= 100 and the
+    launch shape holds at least 6 samples per CTA, the float32 form
     otherwise; each launch gives the bits of the explicit choice."""
     P = sfmod
-    cases = [(3, 16, True), (3, 12, True), (3, 8, False), (3, 24, False), (3, 32, False), (2, 16, False)]
-    for dim, N, want in cases:
-        spec = si.config_n16_3d(n_robots=N, n_samples=20, K=20) if dim == 3 else \
-            si.config_small_2d(n_robots=N, n_samples=20, K=20, circle_radius=5.0)
+    cases = [(3, 16, 1024, 100, True), (3, 12, 1024, 100, True), (3, 16, 1024, 50, False),
+             (3, 16, 64, 100, False), (3, 8, 1024, 100, False), (3, 24, 1024, 100, False),
+             (2, 16, 1024, 100, False)]
+    for dim, N, S, K, want in cases:
+        spec = si.config_n16_3d(n_robots=N, n_samples=S) if dim == 3 else \
+            si.config_small_2d(n_robots=N, n_samples=S, circle_radius=5.0)
         sc = si.scene(spec, 9)
         args = (_dev(sc.xi_bar), _dev(sc.start), _dev(sc.goal))
         f = _filter(P, spec, RHO_3D, tm="auto")
-        out = f.project(*args, 20)
+        out = f.project(*args, K)
         f.sync_status()
-        assert f.launch_shape()["tensor_memory"] == want, (dim, N)
+        assert f.launch_shape()["tensor_memory"] == want, (dim, N, S, K)
         g = _filter(P, spec, RHO_3D, tm=want)
-        ref = g.project(*args, 20)
+        ref = g.project(*args, K)
         g.sync_status()
-        assert torch.equal(out.xi, ref.xi) and torch.equal(out.lam, ref.lam), (dim, N)
+        assert torch.equal(out.xi, ref.xi) and torch.equal(out.lam, ref.lam), (dim, N, S, K)
