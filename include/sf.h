@@ -217,11 +217,12 @@ typedef enum {
    * the B operand in shared memory, three-term split of tf32 operands); the
    * rest stays on the float32 lanes. 0: the float32 form, products on the
    * lanes too. 2 (the default): per launch group, the form measured faster
-   * on a GB300: the tensor-memory form for 3D scenes of 9..16 robots when
-   * K >= 100 and its launch shape puts at least 6 samples in a CTA (about 600
-   * or more samples of such scenes), the float32 form otherwise. Both forms
-   * give outputs within rounding of each other. 16-bit handles always use
-   * the tensor-memory form. */
+   * on a GB300: the tensor-memory form for 3D scenes of 9..24 robots when its
+   * launch shape fills at least 96 of a CTA's 128 TMEM lanes (6 samples per
+   * CTA at 9..16 robots, 4 at 17..24; about 600 or more samples of such
+   * scenes), the float32 form otherwise. Both forms give outputs within
+   * rounding of each other. 16-bit handles always use the tensor-memory
+   * form. */
   SF_OPT_TENSOR_MEMORY = 2,
   /* Test of the timeout path, value in microseconds (0 = off, the default):
    * the tensor-memory form does not issue the first MMA group of each CTA

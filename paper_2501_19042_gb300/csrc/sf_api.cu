@@ -157,8 +157,8 @@ struct FusedRequest {
 // precision is 16-bit (the 16-bit products exist only there), the float32
 // form when the option is off, and FORM_AUTO (float32 handles, option 2, the
 // default) to let each launch group take the form measured faster for its
-// dimension, robot-count bucket, K and launch shape (auto_tm_candidate,
-// kAutoTmMinG). The training forward follows
+// dimension, robot-count bucket and launch shape (auto_tm_candidate,
+// kAutoTmMinLanes). The training forward follows
 // the same rule; the adjoint is the float32 form's in every case.
 constexpr int FORM_AUTO = -1;
 int forward_form(const sf_handle* h) {
@@ -168,14 +168,15 @@ int forward_form(const sf_handle* h) {
 }
 // The float32 handle's form for one launch group under FORM_AUTO: the
 // tensor-memory form where it measured faster than the float32 form on a
-// GB300, i.e. 3D scenes of 9..16 robots, K >= 100 and a launch shape of the
-// tensor-memory form with at least 6 samples per CTA (96 of the 128 TMEM
-// lanes in use). Measured, T = 100: 16 robots, K = 200: 768..2048 samples
-// 0.81..0.85x the float32 form's time, 512 samples (4 per CTA) 1.13x,
-// <= 256 samples 1.4..1.6x; K = 50: 0.97..1.06x; 12 robots, 1024 samples
-// 0.78x; 20 and 24 robots 1.02x; 4, 8, 28, 32 robots and every 2D case slower.
-bool auto_tm_candidate(int dim, int nmax, int K) { return dim == 3 && nmax == 16 && K >= 100; }
-constexpr int kAutoTmMinG = 6;
+// GB300, i.e. 3D scenes of 9..24 robots whose tensor-memory launch shape uses
+// at least 96 of the 128 TMEM lanes of a CTA (G x NMAX >= 96: 6 samples per
+// CTA at 9..16 robots, 4 at 17..24). Measured, T = 100: 16 robots, 768..2048
+// samples 0.67..0.69x the float32 form's time at K = 200 and 0.83..0.86x at
+// K = 50, 512 samples (4 per CTA) 0.93x / 1.07x, <= 256 samples 1.2..1.4x;
+// 12 robots, 1024 samples 0.66x; 20 and 24 robots, 1024 samples 0.83x and
+// 0.88x; 4, 8, 28, 32 robots and every 2D case slower.
+bool auto_tm_candidate(int dim, int nmax) { return dim == 3 && (nmax == 16 || nmax == 24); }
+constexpr int kAutoTmMinLanes = 96;
 
 long long total_coefs(const sf_handle* h, const sf_batch* b) {
   long long c = 0;
@@ -241,7 +242,7 @@ sf_status build_groups(sf_handle* h, const sf_batch* b, int K, long long S, cons
                      [&](const Item& x, const Item& y) { return b->n_robots[x.scene] > b->n_robots[y.scene]; });
   for (int bk = 0; bk < kBuckets; ++bk) {
     const int nmax = kBucketNmax[bk];
-    const bool auto_tm = !rq.backward && rq.prec == FORM_AUTO && auto_tm_candidate(dim, nmax, K);
+    const bool auto_tm = !rq.backward && rq.prec == FORM_AUTO && auto_tm_candidate(dim, nmax);
     const int prec0 = rq.backward ? 0 : rq.prec == FORM_AUTO ? (auto_tm ? PREC_TM_TF32 : 0) : rq.prec;
     for (size_t first = 0; first < items[bk].size(); first += MAX_SCENES_PER_LAUNCH) {
       const size_t last = std::min(items[bk].size(), first + (size_t)MAX_SCENES_PER_LAUNCH);
@@ -261,7 +262,7 @@ sf_status build_groups(sf_handle* h, const sf_batch* b, int K, long long S, cons
       };
       int prec = prec0;
       FusedPlan plan = make_plan(prec, &lg.key);
-      if (auto_tm && plan.G < kAutoTmMinG) {   // too few samples per CTA: the float32 form
+      if (auto_tm && plan.G * nmax < kAutoTmMinLanes) {   // too few rows per CTA: the float32 form
         prec = 0;
         plan = make_plan(prec, &lg.key);
       }

@@ -249,12 +249,12 @@ def test_training_forward_full_size_sampled(sfmod, oracle_lib, prec):
 
 def test_default_form_per_bucket(sfmod):
     """A float32 handle's default (SF_OPT_TENSOR_MEMORY = 2) takes the
-    tensor-memory form for 3D scenes of 9..16 robots when K >= 100 and the
-    launch shape holds at least 6 samples per CTA, the float32 form
-    otherwise; each launch gives the bits of the explicit choice."""
+    tensor-memory form for 3D scenes of 9..24 robots when its launch shape
+    fills at least 96 TMEM lanes per CTA, the float32 form otherwise; each
+    launch gives the bits of the explicit choice."""
     P = sfmod
-    cases = [(3, 16, 1024, 100, True), (3, 12, 1024, 100, True), (3, 16, 1024, 50, False),
-             (3, 16, 64, 100, False), (3, 8, 1024, 100, False), (3, 24, 1024, 100, False),
+    cases = [(3, 16, 1024, 50, True), (3, 12, 1024, 100, True), (3, 20, 1024, 50, True),
+             (3, 16, 64, 100, False), (3, 8, 1024, 100, False), (3, 32, 256, 50, False),
              (2, 16, 1024, 100, False)]
     for dim, N, S, K, want in cases:
         spec = si.config_n16_3d(n_robots=N, n_samples=S) if dim == 3 else \
