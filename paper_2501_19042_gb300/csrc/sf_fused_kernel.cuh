@@ -415,8 +415,81 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
         for (int v = tl; v < NMAX * RS; v += TCc) blk[L.CR + v] = Cs[v];
     }
     bool e_in_row = false;
+    // pair rows (bits in pair_bit order) and workspace robots (bits) whose
+    // projection is applied into the lane's row of the chunk buffer: the
+    // recorded candidates, or the active rows that a full test found (N <= 16)
+    unsigned wsel[(PW + 3) / 4 * 4];
+    unsigned wsm = 0u;
+    bool apply = false;
     if (CAND && !__any_sync(FULL, refresh)) {
       // candidate path: no warp-wide votes below, lanes run their own lists
+      apply = true;
+      const uint4* c4 = reinterpret_cast<const uint4*>(cmrow);
+#pragma unroll
+      for (int q = 0; q < (PW + 3) / 4; ++q) {
+        const uint4 v = c4[q];
+        wsel[4 * q] = v.x; wsel[4 * q + 1] = v.y; wsel[4 * q + 2] = v.z; wsel[4 * q + 3] = v.w;
+      }
+      if (pc.use_w) wsm = reinterpret_cast<const unsigned*>(blk + L.WC)[t];
+    } else if (NMAX <= 16) {
+      // full test: scaled positions of all robots in registers, every pair
+      // row and workspace row tested branch-free; the active ones are then
+      // applied by the same loop as the candidates (one copy of the
+      // projection code). Lanes past the chunk get far-apart dummies so that
+      // none of their rows tests active.
+      apply = true;
+      float p[NMAX][DIM];
+#pragma unroll
+      for (int i = 0; i < NMAX; ++i) {
+        if (i < N) {
+          state<DIM>(Pr, Cs + i * RS, p[i]);
+#pragma unroll
+          for (int x = 0; x < DIM; ++x) p[i][x] *= (x == 2 ? pc.inv_b : pc.inv_a);
+        } else {
+#pragma unroll
+          for (int x = 0; x < DIM; ++x) p[i][x] = 0.0f;
+        }
+        if (!valid) p[i][0] = 4096.0f * (float)i;
+      }
+      unsigned cmr[PW];
+#pragma unroll
+      for (int q = 0; q < PW; ++q) {
+        cmr[q] = 0u;
+        wsel[q] = 0u;
+      }
+#pragma unroll
+      for (int i = 0; i < NMAX; ++i)
+#pragma unroll
+        for (int j = 0; j < NMAX; ++j)
+          if (j > i && j < N) {
+            const float s2 = scaled_d2<DIM>(p[i], p[j]);
+            const int b = pair_bit(NMAX, i, j);
+            wsel[b >> 5] |= (s2 < 1.0f) ? (1u << (b & 31)) : 0u;
+            if (CAND) cmr[b >> 5] |= (s2 < kPruneCandS2) ? (1u << (b & 31)) : 0u;
+          }
+      if (CAND && rec) {
+#pragma unroll
+        for (int q = 0; q < PW; ++q) cmrow[q] = cmr[q];
+      }
+      // workspace rows of every robot (Eq. workspace_con)
+      if (pc.use_w) {
+        unsigned wsc = 0u;
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i)
+          if (i < N) {
+            float s2 = 0.0f;
+#pragma unroll
+            for (int x = 0; x < DIM; ++x) {
+              const float w = fmaf(p[i][x], pc.wk[x], -pc.wo[x]);
+              s2 = fmaf(w, w, s2);
+            }
+            wsm |= (s2 > 1.0f) ? (1u << i) : 0u;
+            if (CAND) wsc |= (s2 > kWsCandS2) ? (1u << i) : 0u;
+          }
+        if (CAND && rec) reinterpret_cast<unsigned*>(blk + L.WC)[t] = wsc;
+      }
+    }
+    if (apply) {
       e_in_row = true;
       // FLAG: the row is cleared (16-byte stores) only when the lane meets
       // its first active row; a row whose flag stays clear is never read
@@ -432,16 +505,9 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
       if (valid) {
         if (!FLAG)
           for (int q = 0; q < N * DIM; ++q) ebw[q] = 0.0f;
-        unsigned w[(PW + 3) / 4 * 4];
-        const uint4* c4 = reinterpret_cast<const uint4*>(cmrow);
-#pragma unroll
-        for (int q = 0; q < (PW + 3) / 4; ++q) {
-          const uint4 v = c4[q];
-          w[4 * q] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w;
-        }
 #pragma unroll
         for (int q = 0; q < PW; ++q) {
-          unsigned m = w[q];
+          unsigned m = wsel[q];
           while (m) {
             const int idx = q * 32 + __ffs(m) - 1;
             m &= m - 1;
@@ -471,8 +537,8 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
             }
           }
         }
-        if (pc.use_w) {   // workspace rows of the robots recorded near the boundary
-          unsigned m = reinterpret_cast<const unsigned*>(blk + L.WC)[t];
+        if (pc.use_w) {   // workspace rows of the selected robots
+          unsigned m = wsm;
           while (m) {
             const int i = __ffs(m) - 1;
             m &= m - 1;
@@ -495,83 +561,6 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
           }
         }
         if (FLAG) ebw[NMAX * DIM] = zeroed ? 1.0f : 0.0f;
-      }
-    } else if (NMAX <= 16) {
-      // scaled positions of all robots in registers; lanes past the chunk get
-      // far-apart dummies so that none of their rows tests active
-      float p[NMAX][DIM];
-#pragma unroll
-      for (int i = 0; i < NMAX; ++i) {
-        if (i < N) {
-          state<DIM>(Pr, Cs + i * RS, p[i]);
-#pragma unroll
-          for (int x = 0; x < DIM; ++x) p[i][x] *= (x == 2 ? pc.inv_b : pc.inv_a);
-        } else {
-#pragma unroll
-          for (int x = 0; x < DIM; ++x) p[i][x] = 0.0f;
-        }
-        if (!valid) p[i][0] = 4096.0f * (float)i;
-      }
-      // a row of pairs (i, j > i) is tested without branches; only a row that
-      // is active on some lane of the warp is walked pair by pair. Candidate
-      // rows (pruning) are collected branch-free in registers.
-      unsigned cmr[PW];
-#pragma unroll
-      for (int q = 0; q < PW; ++q) cmr[q] = 0u;
-#pragma unroll
-      for (int i = 0; i < NMAX; ++i) {
-        if (i + 1 < N) {
-          bool row = false;
-#pragma unroll
-          for (int j = 0; j < NMAX; ++j)
-            if (j > i && j < N) {
-              const float s2 = scaled_d2<DIM>(p[i], p[j]);
-              row |= s2 < 1.0f;
-              if (CAND) {
-                const int b = pair_bit(NMAX, i, j);
-                cmr[b >> 5] |= (s2 < kPruneCandS2) ? (1u << (b & 31)) : 0u;
-              }
-            }
-          if (__any_sync(FULL, row)) {
-#pragma unroll
-            for (int j = 0; j < NMAX; ++j)
-              if (j > i && j < N) {
-                const bool act = scaled_d2<DIM>(p[i], p[j]) < 1.0f;
-                if (__any_sync(FULL, act)) {
-                  mark(i, j, act);
-                  pair_apply_scaled<DIM>(p[i], p[j], E[i], E[j], pc, res2);
-                }
-              }
-          }
-        }
-      }
-      if (CAND && rec) {
-#pragma unroll
-        for (int q = 0; q < PW; ++q) cmrow[q] = cmr[q];
-      }
-      // workspace rows of every robot (Eq. workspace_con): q = e - p pulls a
-      // position outside the spheroid back to its surface
-      if (pc.use_w) {
-        bool outw = false;
-        unsigned wsc = 0u;
-#pragma unroll
-        for (int i = 0; i < NMAX; ++i)
-          if (i < N) {
-            float s2 = 0.0f;
-#pragma unroll
-            for (int x = 0; x < DIM; ++x) {
-              const float w = fmaf(p[i][x], pc.wk[x], -pc.wo[x]);
-              s2 = fmaf(w, w, s2);
-            }
-            outw |= valid && s2 > 1.0f;
-            if (CAND) wsc |= (s2 > kWsCandS2) ? (1u << i) : 0u;
-          }
-        if (CAND && rec) reinterpret_cast<unsigned*>(blk + L.WC)[t] = wsc;
-        if (__any_sync(FULL, outw)) {
-#pragma unroll
-          for (int i = 0; i < NMAX; ++i)
-            if (i < N) ws_row<DIM, NMAX, MASKS>(p[i], E[i], valid, i, pc, res2, mrow);
-        }
       }
     } else {
       // scaled positions staged once in the lane's own row of the chunk
