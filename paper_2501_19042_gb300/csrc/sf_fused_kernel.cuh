@@ -360,11 +360,6 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
     const float* Cs = blk + L.C;
     float Pr[NV];
     row_from(BASIS + (size_t)t * BASIS_ROW, Pr);
-    float E[NMAX][DIM];
-#pragma unroll
-    for (int i = 0; i < NMAX; ++i)
-#pragma unroll
-      for (int x = 0; x < DIM; ++x) E[i][x] = 0.0f;
     float res2 = 0.0f;
     // this lane's row of the chunk buffer (a row past the buffer, which a
     // debug build reports, is redirected to row 0)
@@ -414,7 +409,6 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
       if (t0 == 0)
         for (int v = tl; v < NMAX * RS; v += TCc) blk[L.CR + v] = Cs[v];
     }
-    bool e_in_row = false;
     // pair rows (bits in pair_bit order) and workspace robots (bits) whose
     // projection is applied into the lane's row of the chunk buffer: the
     // recorded candidates, or the active rows that a full test found (N <= 16)
@@ -488,9 +482,73 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
           }
         if (CAND && rec) reinterpret_cast<unsigned*>(blk + L.WC)[t] = wsc;
       }
+    } else {
+      // full test, N > 16: scaled positions staged once in the lane's own
+      // row of the chunk buffer (overwritten by E when the active rows are
+      // applied below), robots in blocks of 8 reloaded from there, each
+      // later robot tested against a block in one group; active rows as bits
+      apply = true;
+#pragma unroll
+      for (int q = 0; q < PW; ++q) wsel[q] = 0u;
+#pragma unroll
+      for (int i = 0; i < NMAX; ++i) {
+        if (i < N) {
+          float pi[DIM];
+          state<DIM>(Pr, Cs + i * RS, pi);
+          if (valid)
+#pragma unroll
+            for (int x = 0; x < DIM; ++x) ebw[i * DIM + x] = pi[x] * (x == 2 ? pc.inv_b : pc.inv_a);
+        }
+      }
+      auto sel = [&](int i, int j, float s2) {
+        const int b = pair_bit(NMAX, i, j);
+        wsel[b >> 5] |= (s2 < 1.0f) ? (1u << (b & 31)) : 0u;
+        cand(i, j, s2);
+      };
+#pragma unroll
+      for (int I0 = 0; I0 < NMAX; I0 += 8) {
+        if (I0 < N) {
+          float pI[8][DIM];
+#pragma unroll
+          for (int a = 0; a < 8; ++a) {
+#pragma unroll
+            for (int x = 0; x < DIM; ++x) pI[a][x] = (valid && I0 + a < N) ? ebw[(I0 + a) * DIM + x] : 0.0f;
+            if (!valid) pI[a][0] = 4096.0f * (float)(I0 + a);
+          }
+#pragma unroll
+          for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 8; ++b)
+              if (b > a && I0 + b < N) sel(I0 + a, I0 + b, scaled_d2<DIM>(pI[a], pI[b]));
+#pragma unroll
+          for (int j = 0; j < NMAX; ++j) {
+            if (j >= I0 + 8 && j < N) {
+              float pj[DIM];
+#pragma unroll
+              for (int x = 0; x < DIM; ++x) pj[x] = valid ? ebw[j * DIM + x] : 0.0f;
+              if (!valid) pj[0] = 4096.0f * (float)j;
+#pragma unroll
+              for (int a = 0; a < 8; ++a) sel(I0 + a, j, scaled_d2<DIM>(pI[a], pj));
+            }
+          }
+        }
+      }
+      if (pc.use_w) {
+        unsigned wsc = 0u;
+        for (int i = 0; i < N; ++i) {
+          float s2 = 0.0f;
+#pragma unroll
+          for (int x = 0; x < DIM; ++x) {
+            const float w = fmaf(valid ? ebw[i * DIM + x] : 0.0f, pc.wk[x], -pc.wo[x]);
+            s2 = fmaf(w, w, s2);
+          }
+          if (valid && s2 > 1.0f) wsm |= 1u << i;
+          if (CAND && s2 > kWsCandS2) wsc |= 1u << i;
+        }
+        if (CAND && rec) reinterpret_cast<unsigned*>(blk + L.WC)[t] = wsc;
+      }
     }
     if (apply) {
-      e_in_row = true;
       // FLAG: the row is cleared (16-byte stores) only when the lane meets
       // its first active row; a row whose flag stays clear is never read
       bool zeroed = !FLAG;
@@ -562,133 +620,8 @@ __device__ void pair_phase(float* SAMP, const Lay& L, const float* BASIS, int G,
         }
         if (FLAG) ebw[NMAX * DIM] = zeroed ? 1.0f : 0.0f;
       }
-    } else {
-      // scaled positions staged once in the lane's own row of the chunk
-      // buffer (which later receives E); robots in blocks of 8 reloaded
-      // from there, each later robot tested against a block in one group
-#pragma unroll
-      for (int i = 0; i < NMAX; ++i) {
-        if (i < N) {
-          float pi[DIM];
-          state<DIM>(Pr, Cs + i * RS, pi);
-          if (valid)
-#pragma unroll
-            for (int x = 0; x < DIM; ++x) ebw[i * DIM + x] = pi[x] * (x == 2 ? pc.inv_b : pc.inv_a);
-        }
-      }
-#pragma unroll
-      for (int I0 = 0; I0 < NMAX; I0 += 8) {
-        if (I0 < N) {
-          float pI[8][DIM];
-#pragma unroll
-          for (int a = 0; a < 8; ++a) {
-#pragma unroll
-            for (int x = 0; x < DIM; ++x) pI[a][x] = (valid && I0 + a < N) ? ebw[(I0 + a) * DIM + x] : 0.0f;
-            if (!valid) pI[a][0] = 4096.0f * (float)(I0 + a);
-          }
-          bool blkrow = false;
-#pragma unroll
-          for (int a = 0; a < 8; ++a)
-#pragma unroll
-            for (int b = 0; b < 8; ++b)
-              if (b > a && I0 + b < N) {
-                const float s2 = scaled_d2<DIM>(pI[a], pI[b]);
-                blkrow |= s2 < 1.0f;
-                cand(I0 + a, I0 + b, s2);
-              }
-          if (__any_sync(FULL, blkrow)) {
-#pragma unroll
-            for (int a = 0; a < 8; ++a)
-#pragma unroll
-              for (int b = 0; b < 8; ++b)
-                if (b > a && I0 + b < N) {
-                  const bool act = scaled_d2<DIM>(pI[a], pI[b]) < 1.0f;
-                  if (__any_sync(FULL, act)) {
-                    mark(I0 + a, I0 + b, act);
-                    pair_apply_scaled<DIM>(pI[a], pI[b], E[I0 + a], E[I0 + b], pc, res2);
-                  }
-                }
-          }
-#pragma unroll
-          for (int j = 0; j < NMAX; ++j) {
-            if (j >= I0 + 8 && j < N) {
-              float pj[DIM];
-#pragma unroll
-              for (int x = 0; x < DIM; ++x) pj[x] = valid ? ebw[j * DIM + x] : 0.0f;
-              if (!valid) pj[0] = 4096.0f * (float)j;
-              bool grp = false;
-#pragma unroll
-              for (int a = 0; a < 8; ++a) {
-                const float s2 = scaled_d2<DIM>(pI[a], pj);
-                grp |= s2 < 1.0f;
-                cand(I0 + a, j, s2);
-              }
-              if (__any_sync(FULL, grp)) {
-#pragma unroll
-                for (int a = 0; a < 8; ++a) {
-                  const bool act = scaled_d2<DIM>(pI[a], pj) < 1.0f;
-                  if (__any_sync(FULL, act)) {
-                    mark(I0 + a, j, act);
-                    pair_apply_scaled<DIM>(pI[a], pj, E[I0 + a], E[j], pc, res2);
-                  }
-                }
-              }
-            }
-          }
-        }
-      }
-      if (pc.use_w) {
-        bool outw = false;
-        unsigned wsc = 0u;
-        for (int i = 0; i < N; ++i) {
-          float s2 = 0.0f;
-#pragma unroll
-          for (int x = 0; x < DIM; ++x) {
-            const float w = fmaf(valid ? ebw[i * DIM + x] : 0.0f, pc.wk[x], -pc.wo[x]);
-            s2 = fmaf(w, w, s2);
-          }
-          outw |= valid && s2 > 1.0f;
-          if (CAND && s2 > kWsCandS2) wsc |= 1u << i;
-        }
-        if (CAND && rec) reinterpret_cast<unsigned*>(blk + L.WC)[t] = wsc;
-        if (__any_sync(FULL, outw)) {
-#pragma unroll
-          for (int i = 0; i < NMAX; ++i)
-            if (i < N) {
-              float pi[DIM];
-#pragma unroll
-              for (int x = 0; x < DIM; ++x) pi[x] = valid ? ebw[i * DIM + x] : 0.0f;
-              ws_row<DIM, NMAX, MASKS>(pi, E[i], valid, i, pc, res2, mrow);
-            }
-        }
-      }
     }
-    if (valid) {
-      float* eb = blk + L.EB + tl * L.EP;
-      if (e_in_row) {
-        // candidate path: E (and with FLAG the row's flag) is already in the row
-      } else if (FLAG) {
-        // whole row in 16-byte stores (E of robots >= N is zero); the row
-        // stride is a multiple of 4 floats, scalar stores would conflict
-        float Ef[NMAX * DIM];
-#pragma unroll
-        for (int i = 0; i < NMAX; ++i)
-#pragma unroll
-          for (int x = 0; x < DIM; ++x) Ef[i * DIM + x] = E[i][x];
-        float4* e4 = reinterpret_cast<float4*>(eb);
-#pragma unroll
-        for (int q = 0; q < NMAX * DIM / 4; ++q)
-          e4[q] = make_float4(Ef[4 * q], Ef[4 * q + 1], Ef[4 * q + 2], Ef[4 * q + 3]);
-        eb[NMAX * DIM] = res2 > 0.0f ? 1.0f : 0.0f;
-      } else {
-#pragma unroll
-        for (int i = 0; i < NMAX; ++i)
-          if (i < N)
-#pragma unroll
-            for (int x = 0; x < DIM; ++x) eb[i * DIM + x] = E[i][x];
-      }
-      if (want_res) blk[L.RS2 + t] = res2;
-    }
+    if (valid && want_res) blk[L.RS2 + t] = res2;
   }
 }
 
