@@ -38,7 +38,7 @@ UNIT = "samples/s"
 # precision), from ncu captures of the current kernels (summaries under
 # profiles/); a kernel changed since its capture has no entry
 FWD_TRAFFIC = {
-    ("fused", True, "fp32"): (2467328, "ncu --set full of tm_fwd_kernel<3,16,384,tf32> on this workload, "
+    ("fused", True, "fp32"): (2394368, "ncu --set full of tm_fwd_kernel<3,16,384,tf32> on this workload, "
                                         "one launch (summary under profiles/)"),
 }
 DTYPES = {"fp32": "f32", "bf16": "f32 (bf16 tensor products)", "fp16": "f32 (fp16 tensor products)"}
