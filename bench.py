@@ -41,6 +41,12 @@ FWD_TRAFFIC = {
     ("fused", True, "fp32"): (2394368, "ncu --set full of tm_fwd_kernel<3,16,384,tf32> on this workload, "
                                         "one launch (summary under profiles/)"),
 }
+# warp-instructions executed by one launch of the fused kernel on the bench
+# workload (smsp__inst_executed.sum of the same ncu captures), for the
+# executed-instruction fraction beside the algorithmic one
+FWD_EXECUTED = {
+    ("fused", True, "fp32"): 1341586834,
+}
 DTYPES = {"fp32": "f32", "bf16": "f32 (bf16 tensor products)", "fp16": "f32 (fp16 tensor products)"}
 
 
@@ -99,6 +105,16 @@ def roofline(spec, S, K, ms, tm, precision, form, lane, dev):
     if cap is not None:
         out["traffic"] = cap[0]
         out["traffic_source"] = cap[1]
+    inst = FWD_EXECUTED.get((form, tm, precision))
+    if inst is not None and dev is not None:
+        # issue slots: 4 schedulers per SM, one warp-instruction each per
+        # cycle, at the clock the FMA microbenchmark ran at
+        import torch
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        slots = sec * sms * 4 * lane["lane_mhz"] * 1e6
+        out["executed"] = {"warp_instructions_per_launch": inst, "issue_frac": inst / slots,
+                           "source": "smsp__inst_executed.sum of one ncu capture of this kernel on this workload; "
+                                     "issue_frac = that count / (launch time x SMs x 4 x lane clock)"}
     mufu = mufu_per_sample_iter(N, T) * S * K / sec / 1e12
     out["mufu"] = {"achieved": mufu, "peak": lane["mufu_per_s"] / 1e12, "unit": "Tops/s",
                    "frac": mufu / (lane["mufu_per_s"] / 1e12), "ops_per_sample_iteration": mufu_per_sample_iter(N, T)}
