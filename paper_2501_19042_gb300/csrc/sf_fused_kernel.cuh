@@ -1096,24 +1096,17 @@ __device__ void solve_lambda_means(const Cta<DIM, NMAX>& c, const ProblemConsts&
 // goes to *drift_bits instead, as the bit pattern of a non-negative float)
 // and (fp) records ||xi' - xi||^2 of the row; out receives the new row
 // (entry NV zero).
+// The xi step of one row from its operands in registers: cc the row's
+// coefficients, r its right-hand side rho g + lambda' + xi_bar, mt the mean
+// term of its (sample, axis).
 template <int DIM, int NMAX, bool CAND, bool ATOMIC_DRIFT = true>
-__device__ __forceinline__ void xi_step_row(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, int s, int i, int x,
-                                            bool keep_prev, bool fp, float (&out)[NP], int* drift_bits = nullptr) {
+__device__ __forceinline__ void xi_step_core(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, int s, int i, int x,
+                                             bool keep_prev, bool fp, const float (&cc)[NP], const float (&r)[NP],
+                                             const float (&mt)[NP], float (&out)[NP], int* drift_bits) {
   constexpr int RS = DIM * NP;
   const Lay& L = c.L;
   float* blk = c.blk(s);
   const int o = i * RS + x * NP;
-  float cc[NP], r[NP], mt[NP];
-  const float4* c4 = reinterpret_cast<const float4*>(blk + L.C + o);
-  const float4* r4 = reinterpret_cast<const float4*>(blk + L.PG + o);
-  const float4* mt4 = reinterpret_cast<const float4*>(blk + L.MR + x * NP);
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    const float4 a = c4[q], b = r4[q], e = mt4[q];
-    cc[4 * q] = a.x; cc[4 * q + 1] = a.y; cc[4 * q + 2] = a.z; cc[4 * q + 3] = a.w;
-    r[4 * q] = b.x; r[4 * q + 1] = b.y; r[4 * q + 2] = b.z; r[4 * q + 3] = b.w;
-    mt[4 * q] = e.x; mt[4 * q + 1] = e.y; mt[4 * q + 2] = e.z; mt[4 * q + 3] = e.w;
-  }
   float dx2 = 0.0f;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
@@ -1155,6 +1148,27 @@ __device__ __forceinline__ void xi_step_row(const Cta<DIM, NMAX>& c, const Probl
     o4[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
   }
   if (fp) blk[L.FPP + DIM * NV + i * DIM + x] = dx2;
+}
+
+template <int DIM, int NMAX, bool CAND, bool ATOMIC_DRIFT = true>
+__device__ __forceinline__ void xi_step_row(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, int s, int i, int x,
+                                            bool keep_prev, bool fp, float (&out)[NP], int* drift_bits = nullptr) {
+  constexpr int RS = DIM * NP;
+  const Lay& L = c.L;
+  float* blk = c.blk(s);
+  const int o = i * RS + x * NP;
+  float cc[NP], r[NP], mt[NP];
+  const float4* c4 = reinterpret_cast<const float4*>(blk + L.C + o);
+  const float4* r4 = reinterpret_cast<const float4*>(blk + L.PG + o);
+  const float4* mt4 = reinterpret_cast<const float4*>(blk + L.MR + x * NP);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const float4 a = c4[q], b = r4[q], e = mt4[q];
+    cc[4 * q] = a.x; cc[4 * q + 1] = a.y; cc[4 * q + 2] = a.z; cc[4 * q + 3] = a.w;
+    r[4 * q] = b.x; r[4 * q + 1] = b.y; r[4 * q + 2] = b.z; r[4 * q + 3] = b.w;
+    mt[4 * q] = e.x; mt[4 * q + 1] = e.y; mt[4 * q + 2] = e.z; mt[4 * q + 3] = e.w;
+  }
+  xi_step_core<DIM, NMAX, CAND, ATOMIC_DRIFT>(c, pc, s, i, x, keep_prev, fp, cc, r, mt, out, drift_bits);
 }
 
 // One iteration of f_FP on every sample of the CTA (time chunks, then the

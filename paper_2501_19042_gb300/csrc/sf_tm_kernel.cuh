@@ -382,64 +382,218 @@ __device__ void tm_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, i
     }
     tcg::wait_st();
   }
+  constexpr bool SEG = (NMAX % 32 == 0) || (32 % NMAX == 0);
+  constexpr int SW = NMAX < 32 ? NMAX : 32;
+  // one-pass solve for samples of at most 16 robots (the robot sums of a
+  // 32-lane segment cost more shuffles than they save: 44.8 against 44.1 ms
+  // on the 32-robot workload)
+  constexpr bool ONEPASS = 32 % NMAX == 0 && NMAX <= 16;
   if (q.valid && want_res) c.blk(q.s)[L.RSB + q.cg * NMAX + q.i] = rb;
+  // (one-pass solve: every pair test of this iteration has read the drift
+  // word, the xi step below raises it again)
+  if (CAND && ONEPASS && c.tid == 0) *reinterpret_cast<int*>(c.SAMP + L.RF) = 0;
   tcg::fence_before();
   __syncthreads();
   tcg::fence_after();
-  for (int x = q.cg; x < DIM; x += q.ncg) {
-    float sum[16];
+  if constexpr (ONEPASS) {
+    // One pass per (row, axis) lane: the groups' partials summed from TMEM,
+    // the lambda step (minus-sign reading of Eq. lambda_step), r = rho g +
+    // lambda' + xi_bar, the sample's robot means by shuffles over its NMAX
+    // consecutive lanes, the mean term DW mean(c) + DS mean(r) formed for
+    // one k per lane and gathered by shuffles, then the xi step (Eq. xi_step)
+    // from registers. No shared-memory round trip of g, r or the means.
+    const int j = c.lane & (SW - 1);           // the lane's place in its sample's segment
+    const int segbase = c.lane & ~(SW - 1);
+    const float rho = pc.rho;
+    const float invN = 1.0f / (float)c.N;
+    float* blk = c.blk(q.s < c.G ? q.s : 0);   // (rows are read and written only by valid lanes)
+    for (int x = q.cg; x < DIM; x += q.ncg) {
+      float g[16];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) sum[k] = 0.0f;
-    for (int o = 0; o < q.ncg; ++o) {
-      uint32_t pa[8], pb[8];
-      tcg::ld8(q.lanebase + (uint32_t)((o * DIM + x) * 16), pa);
-      tcg::ld8(q.lanebase + (uint32_t)((o * DIM + x) * 16 + 8), pb);
-      tcg::wait_ld();
-      tcg::tie(pa);
-      tcg::tie(pb);
+      for (int k = 0; k < 16; ++k) g[k] = 0.0f;
+      for (int o = 0; o < q.ncg; ++o) {
+        uint32_t pa[8], pb[8];
+        tcg::ld8(q.lanebase + (uint32_t)((o * DIM + x) * 16), pa);
+        tcg::ld8(q.lanebase + (uint32_t)((o * DIM + x) * 16 + 8), pb);
+        tcg::wait_ld();
+        tcg::tie(pa);
+        tcg::tie(pb);
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        sum[k] += __uint_as_float(pa[k]);
-        sum[8 + k] += __uint_as_float(pb[k]);
+        for (int k = 0; k < 8; ++k) {
+          g[k] += __uint_as_float(pa[k]);
+          g[8 + k] += __uint_as_float(pb[k]);
+        }
+      }
+      const int o = q.i * RS + x * NP;
+      float cc[NP], r[NP], mt[NP];
+      float dl2 = 0.0f;
+      if (q.valid) {
+        float lo[NP], xb[NP];
+        const float4* c4 = reinterpret_cast<const float4*>(blk + L.C + o);
+        const float4* l4 = reinterpret_cast<const float4*>(blk + L.LAM + o);
+        const float4* b4 = reinterpret_cast<const float4*>(blk + L.XIB + o);
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const float4 a = c4[u], l = l4[u], b = b4[u];
+          cc[4 * u] = a.x; cc[4 * u + 1] = a.y; cc[4 * u + 2] = a.z; cc[4 * u + 3] = a.w;
+          lo[4 * u] = l.x; lo[4 * u + 1] = l.y; lo[4 * u + 2] = l.z; lo[4 * u + 3] = l.w;
+          xb[4 * u] = b.x; xb[4 * u + 1] = b.y; xb[4 * u + 2] = b.z; xb[4 * u + 3] = b.w;
+        }
+        float ln[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          if (k < NV) {
+            const float lam = fmaf(rho, g[k], lo[k]);
+            dl2 = fmaf(lam - lo[k], lam - lo[k], dl2);
+            ln[k] = lam;
+            r[k] = fmaf(rho, g[k], lam) + xb[k];
+          } else {
+            ln[k] = lo[k];
+            r[k] = 0.0f;
+          }
+        }
+        float4* lw = reinterpret_cast<float4*>(blk + L.LAM + o);
+#pragma unroll
+        for (int u = 0; u < 3; ++u) lw[u] = make_float4(ln[4 * u], ln[4 * u + 1], ln[4 * u + 2], ln[4 * u + 3]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) cc[k] = r[k] = 0.0f;
+      }
+      // robot sums of c and r over the sample's segment (rows beyond N and
+      // lanes beyond the CTA's samples add zero)
+      float sc[NV], sr[NV];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        sc[k] = cc[k];
+        sr[k] = r[k];
+      }
+#pragma unroll
+      for (int w = SW / 2; w >= 1; w >>= 1)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+          sc[k] += __shfl_xor_sync(FULL, sc[k], w);
+          sr[k] += __shfl_xor_sync(FULL, sr[k], w);
+        }
+      // the mean term, one k (two when the segment has fewer than NV lanes)
+      // per lane, then gathered
+      float v0 = 0.0f, v1 = 0.0f;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = j + h * SW;
+        if (h == 1 && SW >= NV) break;
+        float dw[NV], ds[NV];
+        row_from(c.OPS + OPS_DW + (k < NV ? k : 0) * NP, dw);
+        row_from(c.OPS + OPS_DS + (k < NV ? k : 0) * NP, ds);
+        float m0 = 0.0f, m1 = 0.0f;
+#pragma unroll
+        for (int m = 0; m < NV; ++m) {
+          m0 = fmaf(dw[m], sc[m] * invN, m0);
+          m1 = fmaf(ds[m], sr[m] * invN, m1);
+        }
+        if (h == 0) v0 = m0 + m1;
+        else v1 = m0 + m1;
+      }
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        if (k < NV) {
+          const float a0 = __shfl_sync(FULL, v0, segbase + (k % SW));
+          const float a1 = (SW < NV) ? __shfl_sync(FULL, v1, segbase + (k % SW)) : 0.0f;
+          mt[k] = k < SW ? a0 : a1;
+        } else {
+          mt[k] = 0.0f;
+        }
+      }
+      if (TRAIN && fp) {   // ||lambda' - lambda||^2 of the sample's rows, in its FPP slots of this axis
+#pragma unroll
+        for (int w = SW / 2; w >= 1; w >>= 1) dl2 += __shfl_xor_sync(FULL, dl2, w);
+        if (q.s < c.G)
+          for (int k = j; k < NV; k += SW) blk[L.FPP + x * NV + k] = k == 0 ? dl2 : 0.0f;
+      }
+      if (want_res && x == 0 && j == 0 && q.s < c.G) {   // history entry of the sample
+        float r2 = 0.0f;
+        for (int t = 0; t < T; ++t) r2 += blk[L.RS2 + t];
+        for (int gq = 0; gq < L.NQ; ++gq)
+          for (int i = 0; i < c.N; ++i) r2 += blk[L.RSB + gq * NMAX + i];
+        hist[(size_t)it * total_samples + c.gsample0 + q.s] = sqrtf(r2);
+      }
+      float out[NP];
+      int db = 0;
+      if (q.valid)
+        xi_step_core<DIM, NMAX, CAND, false>(c, pc, q.s, q.i, x, keep_prev, TRAIN && fp, cc, r, mt, out, &db);
+      if (CAND) {
+#pragma unroll
+        for (int w = SW / 2; w >= 1; w >>= 1) db = max(db, __shfl_xor_sync(FULL, db, w));
+        if (j == 0 && q.s < c.G) atomicMax(reinterpret_cast<int*>(c.SAMP + L.RF), db);
       }
     }
-    if (q.valid) {
-      float* pg = c.blk(q.s) + L.PG + q.i * RS + x * NP;
-#pragma unroll
-      for (int k = 0; k < NV; ++k) pg[k] = sum[k];
+    // the new rows to A in TMEM, once no warp reads its partials from columns
+    // that A covers
+    if (2 * TCW < 16 * q.ncg) {
+      tcg::fence_before();
+      __syncthreads();
+      tcg::fence_after();
     }
-  }
-  tcg::fence_before();
-  __syncthreads();
-  canary_check(c.SAMP, L.SB, c.G);
-  solve_lambda_means<DIM, NMAX, CAND>(c, pc, it, hist, total_samples, TRAIN && fp);
-  __syncthreads();
-  canary_check(c.SAMP, L.SB, c.G);
-  // xi step, one (sample, robot) row per lane and the axes over the warp
-  // groups; the new rows also go to A in TMEM
-  // the CTA's drift word: the lanes of one sample reduce their rows' drift
-  // by shuffles first (a sample's rows are NMAX consecutive lanes), then one
-  // atomic per sample and warp
-  constexpr bool SEG = (NMAX % 32 == 0) || (32 % NMAX == 0);
-  constexpr int SW = NMAX < 32 ? NMAX : 32;
+    for (int x = q.cg; x < DIM; x += q.ncg) {
+      float row[NP];
+      const float* cr = blk + L.C + q.i * RS + x * NP;
+#pragma unroll
+      for (int k = 0; k < NP; ++k) row[k] = (q.valid && k < NV) ? cr[k] : 0.0f;
+      tm_write_a<DIM, FMT>(q.lanebase, TCW, x, row);
+    }
+  } else {
   for (int x = q.cg; x < DIM; x += q.ncg) {
-    float out[NP];
-    int db = 0;
-    if (q.valid) {
-      if (SEG)
-        xi_step_row<DIM, NMAX, CAND, false>(c, pc, q.s, q.i, x, keep_prev, TRAIN && fp, out, &db);
-      else
-        xi_step_row<DIM, NMAX, CAND, true>(c, pc, q.s, q.i, x, keep_prev, TRAIN && fp, out);
-    } else {
-#pragma unroll
-      for (int k = 0; k < NP; ++k) out[k] = 0.0f;
+      float sum[16];
+  #pragma unroll
+      for (int k = 0; k < 16; ++k) sum[k] = 0.0f;
+      for (int o = 0; o < q.ncg; ++o) {
+        uint32_t pa[8], pb[8];
+        tcg::ld8(q.lanebase + (uint32_t)((o * DIM + x) * 16), pa);
+        tcg::ld8(q.lanebase + (uint32_t)((o * DIM + x) * 16 + 8), pb);
+        tcg::wait_ld();
+        tcg::tie(pa);
+        tcg::tie(pb);
+  #pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          sum[k] += __uint_as_float(pa[k]);
+          sum[8 + k] += __uint_as_float(pb[k]);
+        }
+      }
+      if (q.valid) {
+        float* pg = c.blk(q.s) + L.PG + q.i * RS + x * NP;
+  #pragma unroll
+        for (int k = 0; k < NV; ++k) pg[k] = sum[k];
+      }
     }
-    if (CAND && SEG) {
-#pragma unroll
-      for (int o = SW / 2; o >= 1; o >>= 1) db = max(db, __shfl_xor_sync(FULL, db, o));
-      if ((c.lane & (SW - 1)) == 0 && q.s < c.G) atomicMax(reinterpret_cast<int*>(c.SAMP + L.RF), db);
-    }
+    tcg::fence_before();
+    __syncthreads();
+    canary_check(c.SAMP, L.SB, c.G);
+    solve_lambda_means<DIM, NMAX, CAND>(c, pc, it, hist, total_samples, TRAIN && fp);
+    __syncthreads();
+    canary_check(c.SAMP, L.SB, c.G);
+    // xi step, one (sample, robot) row per lane and the axes over the warp
+    // groups; the new rows also go to A in TMEM
+    // the CTA's drift word: the lanes of one sample reduce their rows' drift
+    // by shuffles first (a sample's rows are NMAX consecutive lanes), then one
+    // atomic per sample and warp
+    for (int x = q.cg; x < DIM; x += q.ncg) {
+      float out[NP];
+      int db = 0;
+      if (q.valid) {
+        if (SEG)
+          xi_step_row<DIM, NMAX, CAND, false>(c, pc, q.s, q.i, x, keep_prev, TRAIN && fp, out, &db);
+        else
+          xi_step_row<DIM, NMAX, CAND, true>(c, pc, q.s, q.i, x, keep_prev, TRAIN && fp, out);
+      } else {
+  #pragma unroll
+        for (int k = 0; k < NP; ++k) out[k] = 0.0f;
+      }
+      if (CAND && SEG) {
+  #pragma unroll
+        for (int o = SW / 2; o >= 1; o >>= 1) db = max(db, __shfl_xor_sync(FULL, db, o));
+        if ((c.lane & (SW - 1)) == 0 && q.s < c.G) atomicMax(reinterpret_cast<int*>(c.SAMP + L.RF), db);
+      }
     tm_write_a<DIM, FMT>(q.lanebase, TCW, x, out);
+    }
   }
   tcg::wait_st();
   tcg::fence_before();
