@@ -1171,6 +1171,144 @@ __device__ __forceinline__ void xi_step_row(const Cta<DIM, NMAX>& c, const Probl
   xi_step_core<DIM, NMAX, CAND, ATOMIC_DRIFT>(c, pc, s, i, x, keep_prev, fp, cc, r, mt, out, drift_bits);
 }
 
+// One-pass solve of the float32 form for samples of at most 16 robots: one
+// lane per (sample, axis, robot), the robots of a (sample, axis) on NMAX
+// consecutive lanes. Each lane sums its row's partials of F^T q, takes the
+// lambda step (minus-sign reading of Eq. lambda_step) and r = rho g + lambda'
+// + xi_bar, the robot sums of c and r by shuffles over its segment, one k of
+// the mean term DW mean(c) + DS mean(r) (gathered by shuffles), and then the
+// xi step (Eq. xi_step) from registers. The drift word must have been reset
+// before (no pair test of this iteration reads it afterwards).
+template <int DIM, int NMAX, bool CAND>
+__device__ void solve_onepass(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, int it, bool keep_prev,
+                              float* hist, int total_samples, bool fp) {
+  static_assert(32 % NMAX == 0 && NMAX <= 16, "one-pass solve: robots of a sample within one warp");
+  constexpr int RS = DIM * NP;
+  constexpr int SW = NMAX;
+  const Lay& L = c.L;
+  const int T = pc.T, N = c.N, G = c.G;
+  const float rho = pc.rho;
+  const float invN = 1.0f / (float)N;
+  const bool want_res = hist != nullptr;
+  const int nL = G * DIM * NMAX;
+  const int j = c.lane & (SW - 1);
+  const int segbase = c.lane & ~(SW - 1);
+  for (int base = c.warp * 32; base < nL; base += c.nwarps * 32) {
+    const int u = base + c.lane;
+    const int sx = u / NMAX;                 // (sample, axis) of the segment
+    const int s = sx / DIM, x = sx - s * DIM, i = j;
+    const bool in_cta = u < nL;
+    const bool valid = in_cta && i < N;
+    float* blk = c.blk(in_cta ? s : 0);
+    const int o = i * RS + x * NP;
+    float cc[NP], r[NP], mt[NP];
+    float dl2 = 0.0f;
+    if (valid) {
+      float lo[NP], xb[NP], g[NP];
+      const float4* c4 = reinterpret_cast<const float4*>(blk + L.C + o);
+      const float4* l4 = reinterpret_cast<const float4*>(blk + L.LAM + o);
+      const float4* b4 = reinterpret_cast<const float4*>(blk + L.XIB + o);
+      const float4* g4 = reinterpret_cast<const float4*>(blk + L.PG + o);
+#pragma unroll
+      for (int w = 0; w < 3; ++w) {
+        const float4 a = c4[w], l = l4[w], b = b4[w], e = g4[w];
+        cc[4 * w] = a.x; cc[4 * w + 1] = a.y; cc[4 * w + 2] = a.z; cc[4 * w + 3] = a.w;
+        lo[4 * w] = l.x; lo[4 * w + 1] = l.y; lo[4 * w + 2] = l.z; lo[4 * w + 3] = l.w;
+        xb[4 * w] = b.x; xb[4 * w + 1] = b.y; xb[4 * w + 2] = b.z; xb[4 * w + 3] = b.w;
+        g[4 * w] = e.x; g[4 * w + 1] = e.y; g[4 * w + 2] = e.z; g[4 * w + 3] = e.w;
+      }
+      for (int q = 1; q < L.NPG; ++q) {
+        const float4* p4 = reinterpret_cast<const float4*>(blk + L.PQ1 + (q - 1) * NMAX * RS + o);
+#pragma unroll
+        for (int w = 0; w < 3; ++w) {
+          const float4 e = p4[w];
+          g[4 * w] += e.x; g[4 * w + 1] += e.y; g[4 * w + 2] += e.z; g[4 * w + 3] += e.w;
+        }
+      }
+      float ln[NP];
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        if (k < NV) {
+          const float lam = fmaf(rho, g[k], lo[k]);
+          dl2 = fmaf(lam - lo[k], lam - lo[k], dl2);
+          ln[k] = lam;
+          r[k] = fmaf(rho, g[k], lam) + xb[k];
+        } else {
+          ln[k] = lo[k];
+          r[k] = 0.0f;
+        }
+      }
+      float4* lw = reinterpret_cast<float4*>(blk + L.LAM + o);
+#pragma unroll
+      for (int w = 0; w < 3; ++w) lw[w] = make_float4(ln[4 * w], ln[4 * w + 1], ln[4 * w + 2], ln[4 * w + 3]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < NP; ++k) cc[k] = r[k] = 0.0f;
+    }
+    float sc[NV], sr[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      sc[k] = cc[k];
+      sr[k] = r[k];
+    }
+#pragma unroll
+    for (int w = SW / 2; w >= 1; w >>= 1)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        sc[k] += __shfl_xor_sync(FULL, sc[k], w);
+        sr[k] += __shfl_xor_sync(FULL, sr[k], w);
+      }
+    float v0 = 0.0f, v1 = 0.0f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = j + h * SW;
+      if (h == 1 && SW >= NV) break;
+      float dw[NV], ds[NV];
+      row_from(c.OPS + OPS_DW + (k < NV ? k : 0) * NP, dw);
+      row_from(c.OPS + OPS_DS + (k < NV ? k : 0) * NP, ds);
+      float m0 = 0.0f, m1 = 0.0f;
+#pragma unroll
+      for (int m = 0; m < NV; ++m) {
+        m0 = fmaf(dw[m], sc[m] * invN, m0);
+        m1 = fmaf(ds[m], sr[m] * invN, m1);
+      }
+      if (h == 0) v0 = m0 + m1;
+      else v1 = m0 + m1;
+    }
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      if (k < NV) {
+        const float a0 = __shfl_sync(FULL, v0, segbase + (k % SW));
+        const float a1 = (SW < NV) ? __shfl_sync(FULL, v1, segbase + (k % SW)) : 0.0f;
+        mt[k] = k < SW ? a0 : a1;
+      } else {
+        mt[k] = 0.0f;
+      }
+    }
+    if (fp) {   // ||lambda' - lambda||^2 of the segment's rows, in the FPP slots of its axis
+#pragma unroll
+      for (int w = SW / 2; w >= 1; w >>= 1) dl2 += __shfl_xor_sync(FULL, dl2, w);
+      if (in_cta)
+        for (int k = j; k < NV; k += SW) blk[L.FPP + x * NV + k] = k == 0 ? dl2 : 0.0f;
+    }
+    if (want_res && in_cta && x == 0 && j == 0) {   // history entry of the sample
+      float r2 = 0.0f;
+      for (int t = 0; t < T; ++t) r2 += blk[L.RS2 + t];
+      for (int q = 0; q < L.NQ; ++q)
+        for (int i2 = 0; i2 < N; ++i2) r2 += blk[L.RSB + q * NMAX + i2];
+      hist[(size_t)it * total_samples + c.gsample0 + s] = sqrtf(r2);
+    }
+    float out[NP];
+    int db = 0;
+    if (valid) xi_step_core<DIM, NMAX, CAND, false>(c, pc, s, i, x, keep_prev, fp, cc, r, mt, out, &db);
+    if (CAND) {
+#pragma unroll
+      for (int w = SW / 2; w >= 1; w >>= 1) db = max(db, __shfl_xor_sync(FULL, db, w));
+      if (j == 0 && in_cta) atomicMax(reinterpret_cast<int*>(c.SAMP + L.RF), db);
+    }
+  }
+}
+
 // One iteration of f_FP on every sample of the CTA (time chunks, then the
 // lambda step and the xi step). keep_prev stores xi^k in the EB region for
 // the final residual. fp (when set) adds ||z^{k+1} - z^k||^2 per sample to FPR.
@@ -1200,18 +1338,26 @@ __device__ void fwd_iteration(const Cta<DIM, NMAX>& c, const ProblemConsts& pc, 
       canary_check(c.SAMP, L.SB, G);
       contract_phase<DIM>(c.SAMP, L, c.BASIS, G, N, t0, TCc, t0 == 0, pc, want_res, c.tid, c.nthr);
     }
+    // one-pass solve: the drift word is reset once every pair test of the
+    // iteration has read it (the barrier below orders it before the xi step)
+    if (CAND && 32 % NMAX == 0 && NMAX <= 16 && t0 + TC >= T && c.tid == 0)
+      *reinterpret_cast<int*>(c.SAMP + L.RF) = 0;
     __syncthreads();
     canary_check(c.SAMP, L.SB, G);
   }
-  solve_lambda_means<DIM, NMAX, CAND>(c, pc, it, hist, total_samples, fp);
-  __syncthreads();
-  canary_check(c.SAMP, L.SB, G);
-  // ---- solve phase 2: xi step, xi_i = W1 c_i + S1 r_i + (DW mean(c) +
-  // DS mean(r)) + beta_i per (sample, robot, axis)
-  for (int v = c.tid; v < G * N * DIM; v += c.nthr) {
-    const int s = v / (N * DIM), i = (v / DIM) % N, x = v % DIM;
-    float out[NP];
-    xi_step_row<DIM, NMAX, CAND>(c, pc, s, i, x, keep_prev, fp, out);
+  if constexpr (32 % NMAX == 0 && NMAX <= 16) {
+    solve_onepass<DIM, NMAX, CAND>(c, pc, it, keep_prev, hist, total_samples, fp);
+  } else {
+    solve_lambda_means<DIM, NMAX, CAND>(c, pc, it, hist, total_samples, fp);
+    __syncthreads();
+    canary_check(c.SAMP, L.SB, G);
+    // ---- solve phase 2: xi step, xi_i = W1 c_i + S1 r_i + (DW mean(c) +
+    // DS mean(r)) + beta_i per (sample, robot, axis)
+    for (int v = c.tid; v < G * N * DIM; v += c.nthr) {
+      const int s = v / (N * DIM), i = (v / DIM) % N, x = v % DIM;
+      float out[NP];
+      xi_step_row<DIM, NMAX, CAND>(c, pc, s, i, x, keep_prev, fp, out);
+    }
   }
   __syncthreads();
   canary_check(c.SAMP, L.SB, G);
